@@ -1,0 +1,963 @@
+/*
+ * hweno_oracle.c -- plain, slow CPU FP64 restatement of the moment-based
+ * multi-resolution HWENO scheme (Li, Shu, Qiu, arXiv 2201.12193).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: only tests/, __graft_entry__.smoke() and the cpu_baseline /
+ * reference legs of bench.py use it.  It shares no code, header, table or
+ * constant generator with the CUDA library.
+ *
+ * Every step follows the paper's order and notation and is written for a
+ * reader checking it against the paper by eye:
+ *   - polynomials q_1..q_4 are solved from their moment conditions
+ *     (Sec. 2.1 Step 1.1, eq. (q); Sec. 2.2 Steps 1.1.1-1.1.4, eqs.
+ *     (2D-q1)-(2D-q4), the 2D ones as least squares with the target-cell
+ *     average imposed exactly);
+ *   - p_l from q_l by eq. (p) / (2D-p) with the linear weights of
+ *     eq. (linear-weight) built from any positive gbar[4];
+ *   - beta_l by integrating squared derivatives exactly (eq. (beta),
+ *     (2D-beta)); beta_1 by eqs. (q1-LR)-(beta1) / (2D-q1-1234)-(2D-beta1);
+ *   - WENO-Z weights eq. (non-linear-weight), (tau4); point values by
+ *     eq. (re-p), (re-u), (2D-re-p), (2D-re-u);
+ *   - KXRCF eq. (KXRCF) with eq. (line-integral-average) in 1D and
+ *     eq. (KXRCF_) with eq. (line-integral-average_) in 2D (Remarks 2, 3);
+ *   - the first-moment modification from the quartic p_0 of eq. (p0),
+ *     solved here (the printed constants of eq. (vi) are a test pin);
+ *   - HLLC flux eqs. (f_HLLC), (COEF), (uLR_); Gauss-Lobatto quadrature
+ *     eqs. (F), (integral1)-(integral3); semi-discrete forms eqs.
+ *     (1D-equ-int-approximation), (2D-equ-int-approximation);
+ *   - SSP Runge-Kutta eq. (Runge-Kutta).
+ *
+ * Readings of points the paper leaves open (each one also used by the GPU
+ * path) are marked "Reading:" where they are applied.
+ *
+ * State layout (same as the library boundary): m[var][moment][j][i], FP64,
+ * moment 0 = cell average, 1 = first moment in x, 2 = first moment in y.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_EINVAL (-1)
+#define ORC_ENONPHYSICAL (-3)
+
+typedef struct {
+  int dim;          /* 1 or 2 */
+  int nx, ny;       /* cells; ny = 1 when dim == 1 */
+  double dx, dy;    /* mesh sizes */
+  int eq;           /* 0 linear advection, 1 Burgers, 2 Euler */
+  double adv_a, adv_b; /* advection speeds (f = a u, g = b u) */
+  double gamma;     /* ratio of specific heats (Euler) */
+  int indicator;    /* 0 none (HWENO6), 1 KXRCF (M5-I), 2 all cells (M5-NI) */
+  double gbar[4];   /* positive linear-weight seeds, eq. (linear-weight) */
+  int bc[4];        /* x-lo, x-hi, y-lo, y-hi: 0 periodic, 1 transmissive */
+} orc_cfg;
+
+/* ------------------------------------------------------------------ */
+/* small dense linear algebra                                          */
+/* ------------------------------------------------------------------ */
+
+/* Gaussian elimination with partial pivoting in long double.
+ * A is n x n row-major (destroyed); B is n x nrhs row-major, overwritten
+ * with the solution.  Returns 0, or -1 if A is singular. */
+static int solve_ld(int n, long double *A, long double *B, int nrhs) {
+  for (int col = 0; col < n; ++col) {
+    int piv = col;
+    long double best = fabsl(A[col * n + col]);
+    for (int r = col + 1; r < n; ++r) {
+      long double v = fabsl(A[r * n + col]);
+      if (v > best) { best = v; piv = r; }
+    }
+    if (best == 0.0L) return -1;
+    if (piv != col) {
+      for (int k = 0; k < n; ++k) {
+        long double t = A[col * n + k]; A[col * n + k] = A[piv * n + k]; A[piv * n + k] = t;
+      }
+      for (int k = 0; k < nrhs; ++k) {
+        long double t = B[col * nrhs + k]; B[col * nrhs + k] = B[piv * nrhs + k]; B[piv * nrhs + k] = t;
+      }
+    }
+    for (int r = col + 1; r < n; ++r) {
+      long double f = A[r * n + col] / A[col * n + col];
+      if (f == 0.0L) continue;
+      for (int k = col; k < n; ++k) A[r * n + k] -= f * A[col * n + k];
+      for (int k = 0; k < nrhs; ++k) B[r * nrhs + k] -= f * B[col * nrhs + k];
+    }
+  }
+  for (int col = n - 1; col >= 0; --col) {
+    for (int k = 0; k < nrhs; ++k) {
+      long double s = B[col * nrhs + k];
+      for (int c2 = col + 1; c2 < n; ++c2) s -= A[col * n + c2] * B[c2 * nrhs + k];
+      B[col * nrhs + k] = s / A[col * n + col];
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* polynomials in scaled cell coordinates                              */
+/* xi = (x - x_i)/dx, eta = (y - y_j)/dy; the target cell is           */
+/* [-1/2,1/2]^2, neighbour (ox,oy) is [ox-1/2,ox+1/2]x[oy-1/2,oy+1/2]. */
+/* A polynomial is c[a][b] (coefficient of xi^a eta^b), a+b <= 5.      */
+/* ------------------------------------------------------------------ */
+
+#define PMAX 6
+typedef struct { double c[PMAX][PMAX]; } poly2;
+
+/* integral of s^n over [o-1/2, o+1/2] */
+static long double mono_int(int n, int o) {
+  long double hi = (long double)o + 0.5L, lo = (long double)o - 0.5L;
+  return (powl(hi, n + 1) - powl(lo, n + 1)) / (long double)(n + 1);
+}
+
+/* Moment condition kinds: 0 cell average, 1 first moment in x, 2 in y.
+ * For a neighbour cell k with centre offset (ox,oy) the normalised moments
+ * of eq. (1D-moment)/(2D-moment) become, in scaled coordinates,
+ *   avg = int int u,   v = int int u (xi - ox),   w = int int u (eta - oy). */
+static long double mono_moment(int kind, int a, int b, int ox, int oy) {
+  long double ix = mono_int(a, ox), iy = mono_int(b, oy);
+  if (kind == 1) ix = mono_int(a + 1, ox) - (long double)ox * mono_int(a, ox);
+  if (kind == 2) iy = mono_int(b + 1, oy) - (long double)oy * mono_int(b, oy);
+  return ix * iy;
+}
+
+typedef struct { int kind, ox, oy; } cond_t;
+
+/* A reconstruction level: its unknown monomials and its conditions. */
+typedef struct {
+  int deg;               /* polynomial degree */
+  int nmono;             /* number of monomials */
+  int ma[21], mb[21];    /* exponents of each monomial */
+  int ncond;
+  cond_t cond[23];
+  double M[21][23];      /* coefficient = M . data  */
+} level_t;
+
+static void level_monomials(level_t *L, int dim, int deg) {
+  L->deg = deg; L->nmono = 0;
+  for (int t = 0; t <= deg; ++t)
+    for (int b = 0; b <= t; ++b) {
+      int a = t - b;
+      if (dim == 1 && b != 0) continue;
+      L->ma[L->nmono] = a; L->mb[L->nmono] = b; L->nmono++;
+    }
+}
+
+/* Solve the level's conditions for M.
+ * 1D: the systems are square (eq. (q)).
+ * 2D: the first condition (target-cell average) is imposed exactly and the
+ * others are matched in the least-squares sense (Step 1.1.4 text, after
+ * Hu and Shu): minimise |A_r x - b_r|^2 subject to c^T x = b_c, via the
+ * KKT system  [A_r^T A_r  c; c^T 0] [x; lam] = [A_r^T b_r; b_c].
+ * Reading: the rows are unweighted in the normalised (scaled) form. */
+static int level_solve(level_t *L, int dim) {
+  int n = L->nmono, m = L->ncond;
+  long double A[23][21];
+  for (int r = 0; r < m; ++r)
+    for (int k = 0; k < n; ++k)
+      A[r][k] = mono_moment(L->cond[r].kind, L->ma[k], L->mb[k], L->cond[r].ox, L->cond[r].oy);
+  if (dim == 1 || m == n) {
+    if (m != n) return -1;
+    long double *S = calloc((size_t)n * n, sizeof(long double));
+    long double *B = calloc((size_t)n * m, sizeof(long double));
+    for (int r = 0; r < n; ++r) for (int k = 0; k < n; ++k) S[r * n + k] = A[r][k];
+    for (int r = 0; r < n; ++r) B[r * m + r] = 1.0L;
+    int rc = solve_ld(n, S, B, m);
+    for (int k = 0; k < n; ++k) for (int r = 0; r < m; ++r) L->M[k][r] = (double)B[k * m + r];
+    free(S); free(B);
+    return rc;
+  }
+  int N = n + 1;
+  long double *K = calloc((size_t)N * N, sizeof(long double));
+  long double *B = calloc((size_t)N * m, sizeof(long double));
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      long double s = 0.0L;
+      for (int r = 1; r < m; ++r) s += A[r][i] * A[r][k];
+      K[i * N + k] = s;
+    }
+  for (int i = 0; i < n; ++i) { K[i * N + n] = A[0][i]; K[n * N + i] = A[0][i]; }
+  for (int i = 0; i < n; ++i)
+    for (int r = 1; r < m; ++r) B[i * m + r] = A[r][i];
+  B[n * m + 0] = 1.0L;
+  int rc = solve_ld(N, K, B, m);
+  for (int k = 0; k < n; ++k) for (int r = 0; r < m; ++r) L->M[k][r] = (double)B[k * m + r];
+  free(K); free(B);
+  return rc;
+}
+
+/* The reconstruction tables (built once per dimension). */
+typedef struct {
+  int ready;
+  level_t q[5];   /* q[2], q[3], q[4] used */
+  double mod[5];  /* p_0 modification: weights of (ubar_{-1}, ubar_0, ubar_{+1}, vbar_{-1}, vbar_{+1}) */
+} tables_t;
+
+static tables_t T1, T2;
+
+/* 2D stencil labels of the paper's table (Step 1): 1..9 <-> (ox, oy) */
+static const int LBL_OX[10] = {0, -1, 0, 1, -1, 0, 1, -1, 0, 1};
+static const int LBL_OY[10] = {0, -1, -1, -1, 0, 0, 0, 1, 1, 1};
+
+static void add_cond(level_t *L, int kind, int ox, int oy) {
+  L->cond[L->ncond].kind = kind; L->cond[L->ncond].ox = ox; L->cond[L->ncond].oy = oy; L->ncond++;
+}
+
+/* Quartic p_0 of eq. (p0) and the modified first moment of eq. (vi):
+ * vbar_i = int_{-1/2}^{1/2} p_0(xi) xi dxi.  Conditions: averages on
+ * cells -1, 0, +1 and first moments on cells -1, +1. */
+static int build_modification(double out[5]) {
+  level_t P;
+  memset(&P, 0, sizeof P);
+  level_monomials(&P, 1, 4);
+  add_cond(&P, 0, -1, 0); add_cond(&P, 0, 0, 0); add_cond(&P, 0, 1, 0);
+  add_cond(&P, 1, -1, 0); add_cond(&P, 1, 1, 0);
+  if (level_solve(&P, 1)) return -1;
+  for (int r = 0; r < 5; ++r) {
+    long double s = 0.0L;
+    for (int k = 0; k < P.nmono; ++k) s += (long double)P.M[k][r] * mono_moment(1, P.ma[k], 0, 0, 0);
+    out[r] = (double)s;
+  }
+  return 0;
+}
+
+static int build_tables(int dim) {
+  tables_t *T = dim == 1 ? &T1 : &T2;
+  if (T->ready) return 0;
+  memset(T, 0, sizeof *T);
+  if (dim == 1) {
+    /* eq. (q): q2 on averages of i-1,i,i+1; q3 adds vbar_i; q4 adds vbar_{i-1}, vbar_{i+1}. */
+    level_t *L;
+    L = &T->q[2]; level_monomials(L, 1, 2);
+    add_cond(L, 0, 0, 0); add_cond(L, 0, -1, 0); add_cond(L, 0, 1, 0);
+    L = &T->q[3]; level_monomials(L, 1, 3);
+    add_cond(L, 0, 0, 0); add_cond(L, 0, -1, 0); add_cond(L, 0, 1, 0); add_cond(L, 1, 0, 0);
+    L = &T->q[4]; level_monomials(L, 1, 5);
+    add_cond(L, 0, 0, 0); add_cond(L, 0, -1, 0); add_cond(L, 0, 1, 0);
+    add_cond(L, 1, -1, 0); add_cond(L, 1, 0, 0); add_cond(L, 1, 1, 0);
+  } else {
+    /* eqs. (2D-q2)-(2D-q4); the first condition is always the target average (label 5). */
+    level_t *L;
+    L = &T->q[2]; level_monomials(L, 2, 2);
+    add_cond(L, 0, 0, 0);
+    for (int k = 1; k <= 9; ++k) if (k != 5) add_cond(L, 0, LBL_OX[k], LBL_OY[k]);
+    L = &T->q[3]; level_monomials(L, 2, 3);
+    add_cond(L, 0, 0, 0);
+    for (int k = 1; k <= 9; ++k) if (k != 5) add_cond(L, 0, LBL_OX[k], LBL_OY[k]);
+    add_cond(L, 1, 0, 0); add_cond(L, 2, 0, 0);
+    L = &T->q[4]; level_monomials(L, 2, 5);
+    add_cond(L, 0, 0, 0);
+    for (int k = 1; k <= 9; ++k) if (k != 5) add_cond(L, 0, LBL_OX[k], LBL_OY[k]);
+    { static const int kx[7] = {1, 3, 4, 5, 6, 7, 9};
+      for (int t = 0; t < 7; ++t) add_cond(L, 1, LBL_OX[kx[t]], LBL_OY[kx[t]]); }
+    { static const int ky[7] = {1, 2, 3, 5, 7, 8, 9};
+      for (int t = 0; t < 7; ++t) add_cond(L, 2, LBL_OX[ky[t]], LBL_OY[ky[t]]); }
+  }
+  for (int l = 2; l <= 4; ++l)
+    if (level_solve(&T->q[l], dim)) return -1;
+  if (build_modification(T->mod)) return -1;
+  T->ready = 1;
+  return 0;
+}
+
+/* Build a polynomial from a level's coefficients and a gathered data vector. */
+static void level_poly(const level_t *L, const double *data, poly2 *p) {
+  memset(p, 0, sizeof *p);
+  for (int k = 0; k < L->nmono; ++k) {
+    double s = 0.0;
+    for (int r = 0; r < L->ncond; ++r) s += L->M[k][r] * data[r];
+    p->c[L->ma[k]][L->mb[k]] = s;
+  }
+}
+
+static double poly_eval(const poly2 *p, double xi, double eta) {
+  double s = 0.0, xa = 1.0;
+  for (int a = 0; a < PMAX; ++a, xa *= xi) {
+    double yb = 1.0;
+    for (int b = 0; a + b < PMAX; ++b, yb *= eta) s += p->c[a][b] * xa * yb;
+  }
+  return s;
+}
+
+/* d^ax/dxi^ax d^ay/deta^ay of p */
+static void poly_deriv(const poly2 *p, int ax, int ay, poly2 *d) {
+  memset(d, 0, sizeof *d);
+  for (int a = ax; a < PMAX; ++a)
+    for (int b = ay; a + b < PMAX; ++b) {
+      double f = 1.0;
+      for (int t = 0; t < ax; ++t) f *= (double)(a - t);
+      for (int t = 0; t < ay; ++t) f *= (double)(b - t);
+      d->c[a - ax][b - ay] = f * p->c[a][b];
+    }
+}
+
+/* exact integral of p^2 over the target cell [-1/2,1/2]^2 (or [-1/2,1/2] in 1D):
+ * int_{-1/2}^{1/2} s^n ds = 0 for odd n and 2^{-n}/(n+1) for even n. */
+static double poly_sq_int(const poly2 *p) {
+  double in0[2 * PMAX];
+  for (int n = 0; n < 2 * PMAX; ++n) in0[n] = (n % 2) ? 0.0 : ldexp(1.0, -n) / (double)(n + 1);
+  double s = 0.0;
+  for (int a = 0; a < PMAX; ++a) for (int b = 0; a + b < PMAX; ++b) {
+    if (p->c[a][b] == 0.0) continue;
+    for (int a2 = 0; a2 < PMAX; ++a2) for (int b2 = 0; a2 + b2 < PMAX; ++b2) {
+      if (p->c[a2][b2] == 0.0) continue;
+      s += p->c[a][b] * p->c[a2][b2] * in0[a + a2] * in0[b + b2];
+    }
+  }
+  return s;
+}
+
+/* ------------------------------------------------------------------ */
+/* The reconstruction of one variable in one cell (Step 1)             */
+/* ------------------------------------------------------------------ */
+
+static const double EPS_W = 1e-10; /* epsilon of eqs. (w1_-LR), (non-linear-weight) */
+
+/* Diagnostic switch, oracle only (never used by the library): 0 = beta_l of
+ * p_l as eq. (beta) states (the scheme); 1 = beta_l of q_l, the variant under
+ * which the expansion beta_l = u'^2 dx^2 + O(dx^4) of Remark 1 holds for every
+ * l.  Used by a test that documents the difference. */
+static int g_beta_from_q = 0;
+void orc_set_beta_source(int from_q) { g_beta_from_q = from_q ? 1 : 0; }
+
+/* Gauss-Lobatto nodes and weights of eq. (F) */
+static double gl_node(int k) {
+  switch (k) {
+    case 0: return -0.5;
+    case 1: return -sqrt(5.0) / 10.0;
+    case 2: return sqrt(5.0) / 10.0;
+    default: return 0.5;
+  }
+}
+static double gl_weight(int k) { return (k == 0 || k == 3) ? 1.0 / 12.0 : 5.0 / 12.0; }
+
+/* Linear weights of eq. (linear-weight): gamma_{l1,l2} = gbar_{l1} / sum_{l<=l2} gbar_l */
+static double lin_weight(const double gbar[4], int l1, int l2) {
+  double s = 0.0;
+  for (int l = 1; l <= l2; ++l) s += gbar[l - 1];
+  return gbar[l1 - 1] / s;
+}
+
+typedef struct {
+  double vals[16];   /* 1D: 4 GL values; 2D: value at (xi_k, eta_l) stored at [k*4+l] */
+  double beta[5];    /* beta_1..beta_4 at [1..4] */
+  double omega[5];   /* omega_{l,4} at [1..4] */
+} recon_out;
+
+/* Data of one variable around a cell:
+ *   1D: ub[3] (cells -1,0,+1), vb[3];
+ *   2D: ub[9], vb[9], wb[9] indexed by paper label-1 (0..8). */
+typedef struct { double ub[9], vb[9], wb[9]; } stencil_t;
+
+static double st_get(const stencil_t *s, int dim, int kind, int ox, int oy) {
+  int idx = dim == 1 ? ox + 1 : (oy + 1) * 3 + (ox + 1);
+  return kind == 0 ? s->ub[idx] : kind == 1 ? s->vb[idx] : s->wb[idx];
+}
+
+static void recon_cell(int dim, double dx, double dy, const double gbar[4],
+                       const stencil_t *st, recon_out *out) {
+  const tables_t *T = dim == 1 ? &T1 : &T2;
+  poly2 q[5], p[5];
+  /* Step 1.1: q_1 .. q_4 */
+  memset(&q[1], 0, sizeof q[1]);
+  q[1].c[0][0] = st_get(st, dim, 0, 0, 0);
+  for (int l = 2; l <= 4; ++l) {
+    const level_t *L = &T->q[l];
+    double data[23];
+    for (int r = 0; r < L->ncond; ++r) data[r] = st_get(st, dim, L->cond[r].kind, L->cond[r].ox, L->cond[r].oy);
+    level_poly(L, data, &q[l]);
+  }
+  /* eq. (p) / (2D-p): p_1 = q_1, p_l2 = q_l2/gamma_{l2,l2} - sum_{l<l2} gamma_{l,l2}/gamma_{l2,l2} p_l */
+  p[1] = q[1];
+  for (int l2 = 2; l2 <= 4; ++l2) {
+    double gll = lin_weight(gbar, l2, l2);
+    for (int a = 0; a < PMAX; ++a) for (int b = 0; b < PMAX; ++b) {
+      double s = q[l2].c[a][b] / gll;
+      for (int l = 1; l < l2; ++l) s -= lin_weight(gbar, l, l2) / gll * p[l].c[a][b];
+      p[l2].c[a][b] = s;
+    }
+  }
+  /* Step 1.2: beta_l2 for l2 = 2,3,4 (eq. (beta) / (2D-beta)), kappa = 2,3,5.
+   * In scaled coordinates dx^{2a-1} int (d^a p/dx^a)^2 dx = int (d^a p/dxi^a)^2 dxi; in 2D
+   * |I|^{|a|-1} int (D^a p)^2 dxdy = (dx/dy)^{ay-ax} int int (D^a p)^2 dxi deta.
+   * Reading: each multi-index (ax, ay) with 1 <= |a| <= kappa is counted once. */
+  static const int kappa[5] = {0, 0, 2, 3, 5};
+  for (int l2 = 2; l2 <= 4; ++l2) {
+    double b = 0.0;
+    for (int t = 1; t <= kappa[l2]; ++t)
+      for (int ay = 0; ay <= (dim == 2 ? t : 0); ++ay) {
+        int ax = t - ay;
+        poly2 d;
+        poly_deriv(g_beta_from_q ? &q[l2] : &p[l2], ax, ay, &d);
+        double w = (dim == 2) ? pow(dx / dy, (double)(ay - ax)) : 1.0;
+        b += w * poly_sq_int(&d);
+      }
+    out->beta[l2] = b;
+  }
+  /* beta_1 */
+  if (dim == 1) {
+    double um = st->ub[0], u0 = st->ub[1], up = st->ub[2];
+    double b1L = (u0 - um) * (u0 - um);               /* eq. (beta1-LR) */
+    double b1R = (up - u0) * (up - u0);
+    double tau1 = fabs(b1R - b1L) * fabs(b1R - b1L);  /* eq. (tau1) */
+    double wLb = 0.5 * (1.0 + tau1 / (b1L + EPS_W));  /* eq. (w1_-LR) */
+    double wRb = 0.5 * (1.0 + tau1 / (b1R + EPS_W));
+    double wL = wLb / (wLb + wRb), wR = wRb / (wLb + wRb); /* eq. (w1-LR) */
+    double g = wL * (u0 - um) + wR * (up - u0);      /* eq. (beta1) */
+    out->beta[1] = g * g;
+  } else {
+    /* eqs. (2D-q1-1234): linear polynomials through the L-shaped triples; a
+     * linear a + b xi + c eta through labels 5 and its two neighbours has
+     * b, c equal to undivided differences. */
+    double u5 = st->ub[4], u4 = st->ub[3], u6 = st->ub[5], u2 = st->ub[1], u8 = st->ub[7];
+    double bx[4] = {u5 - u4, u6 - u5, u6 - u5, u5 - u4};
+    double by[4] = {u8 - u5, u8 - u5, u5 - u2, u5 - u2};
+    double b1k[4], wb[4], ws = 0.0, tau1s = 0.0;
+    for (int k = 0; k < 4; ++k) b1k[k] = bx[k] * bx[k] + by[k] * by[k]; /* eq. (2D-beta1-1234) */
+    /* eq. (2D-tau1); Reading: the sum runs over the 6 unordered pairs k < l */
+    for (int k = 0; k < 4; ++k) for (int l = k + 1; l < 4; ++l) tau1s += fabs(b1k[k] - b1k[l]);
+    double tau1 = (tau1s / 6.0) * (tau1s / 6.0);
+    for (int k = 0; k < 4; ++k) { wb[k] = 0.25 * (1.0 + tau1 / (b1k[k] + EPS_W)); ws += wb[k]; }
+    double gx = 0.0, gy = 0.0;
+    for (int k = 0; k < 4; ++k) { gx += wb[k] / ws * bx[k]; gy += wb[k] / ws * by[k]; }
+    /* eq. (2D-beta1): |I| (d q/dx)^2 + |I| (d q/dy)^2 with d/dx = (1/dx) d/dxi */
+    out->beta[1] = (dy / dx) * gx * gx + (dx / dy) * gy * gy;
+  }
+  /* eqs. (tau4), (non-linear-weight) */
+  double tau4 = 0.0;
+  for (int l = 1; l <= 3; ++l) tau4 += fabs(out->beta[4] - out->beta[l]);
+  tau4 = (tau4 / 3.0) * (tau4 / 3.0);
+  double wbar[5], wsum = 0.0;
+  for (int l = 1; l <= 4; ++l) {
+    wbar[l] = lin_weight(gbar, l, 4) * (1.0 + tau4 / (out->beta[l] + EPS_W));
+    wsum += wbar[l];
+  }
+  for (int l = 1; l <= 4; ++l) out->omega[l] = wbar[l] / wsum;
+  /* eq. (re-p): u_i = sum omega_l p_l, evaluated at the GL points (eq. (re-u), (2D-re-u)) */
+  poly2 u;
+  memset(&u, 0, sizeof u);
+  for (int l = 1; l <= 4; ++l)
+    for (int a = 0; a < PMAX; ++a) for (int b = 0; b < PMAX; ++b) u.c[a][b] += out->omega[l] * p[l].c[a][b];
+  if (dim == 1) {
+    for (int k = 0; k < 4; ++k) out->vals[k] = poly_eval(&u, gl_node(k), 0.0);
+  } else {
+    for (int k = 0; k < 4; ++k) for (int l = 0; l < 4; ++l) out->vals[k * 4 + l] = poly_eval(&u, gl_node(k), gl_node(l));
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* Boundary images                                                    */
+/* ------------------------------------------------------------------ */
+/* Reading: a ghost cell is, throughout a stage, the image of an interior
+ * cell: periodic = wrap; transmissive = mirror about the boundary face, so
+ * the mirrored direction's first moment changes sign and its point values
+ * are reversed in that direction.  Ghost flags and modified moments are those
+ * of the image cell. */
+typedef struct { int i, j, sx, sy; } image_t;
+
+static image_t cell_image(const orc_cfg *c, int i, int j) {
+  image_t r = {i, j, 1, 1};
+  if (i < 0 || i >= c->nx) {
+    int side = i < 0 ? 0 : 1;
+    if (c->bc[side] == 0) { r.i = ((i % c->nx) + c->nx) % c->nx; }
+    else { r.i = i < 0 ? -1 - i : 2 * c->nx - 1 - i; r.sx = -1; }
+  }
+  if (c->dim == 2 && (j < 0 || j >= c->ny)) {
+    int side = j < 0 ? 2 : 3;
+    if (c->bc[side] == 0) { r.j = ((j % c->ny) + c->ny) % c->ny; }
+    else { r.j = j < 0 ? -1 - j : 2 * c->ny - 1 - j; r.sy = -1; }
+  }
+  return r;
+}
+
+static int nvars(const orc_cfg *c) { return c->eq == 2 ? (c->dim == 1 ? 3 : 4) : 1; }
+static int nmoms(const orc_cfg *c) { return c->dim == 1 ? 2 : 3; }
+static size_t ncell(const orc_cfg *c) { return (size_t)c->nx * (size_t)(c->dim == 1 ? 1 : c->ny); }
+
+static double *MOM(const orc_cfg *c, double *m, int var, int mom, int i, int j) {
+  return m + (((size_t)var * nmoms(c) + mom) * ncell(c) + (size_t)j * c->nx + i);
+}
+
+/* moment of any (possibly ghost) cell */
+static double mom_at(const orc_cfg *c, const double *m, int var, int mom, int i, int j) {
+  image_t im = cell_image(c, i, j);
+  double v = *MOM(c, (double *)m, var, mom, im.i, im.j);
+  if (mom == 1) v *= im.sx;
+  if (mom == 2) v *= im.sy;
+  return v;
+}
+
+/* GL values array G[cell][var][16]; value of any (possibly ghost) cell at node (k,l) */
+static double gl_at(const orc_cfg *c, const double *G, int var, int i, int j, int k, int l) {
+  image_t im = cell_image(c, i, j);
+  if (im.sx < 0) k = 3 - k;
+  if (im.sy < 0) l = 3 - l;
+  size_t cell = (size_t)im.j * c->nx + im.i;
+  int nv = nvars(c);
+  return G[(cell * nv + var) * 16 + (c->dim == 1 ? k : k * 4 + l)];
+}
+
+/* ------------------------------------------------------------------ */
+/* Physics                                                            */
+/* ------------------------------------------------------------------ */
+
+/* physical flux in direction dir (0 = x, 1 = y) of a state u[nv] */
+static void phys_flux(const orc_cfg *c, const double *u, int dir, double *f) {
+  if (c->eq == 0) { f[0] = (dir == 0 ? c->adv_a : c->adv_b) * u[0]; return; }
+  if (c->eq == 1) { f[0] = 0.5 * u[0] * u[0]; return; }
+  double g = c->gamma;
+  if (c->dim == 1) {
+    double rho = u[0], mu = u[1] / rho, E = u[2];
+    double p = (g - 1.0) * (E - 0.5 * rho * mu * mu);
+    f[0] = rho * mu; f[1] = rho * mu * mu + p; f[2] = mu * (E + p);
+    return;
+  }
+  double rho = u[0], mu = u[1] / rho, nu = u[2] / rho, E = u[3];
+  double p = (g - 1.0) * (E - 0.5 * rho * (mu * mu + nu * nu));
+  if (dir == 0) { f[0] = rho * mu; f[1] = rho * mu * mu + p; f[2] = rho * mu * nu; f[3] = mu * (E + p); }
+  else          { f[0] = rho * nu; f[1] = rho * mu * nu; f[2] = rho * nu * nu + p; f[3] = nu * (E + p); }
+}
+
+/* velocity used by KXRCF (Remarks 2 and 3): f'(u) / g'(u) for scalars,
+ * mu = (rho mu)/rho or nu for Euler. */
+static double kx_velocity(const orc_cfg *c, const double *u, int dir) {
+  if (c->eq == 0) return dir == 0 ? c->adv_a : c->adv_b;
+  if (c->eq == 1) return u[0];
+  return u[1 + dir] / u[0];
+}
+
+/* HLLC flux, eqs. (f_HLLC), (COEF), (uLR_), in direction dir.
+ * Reading (2D): the rotated 1D flux with the tangential velocity carried in
+ * the star state.  Reading (branches): 0<=sL -> fL; else 0<=s* -> f*L; else
+ * 0<=sR -> f*R; else fR.  p*, s* literal, no clamp. */
+static void hllc(const orc_cfg *c, const double *uL, const double *uR, int dir, double *F) {
+  double g = c->gamma;
+  int two = c->dim == 2;
+  int in = 1 + dir, it = 2 - dir;   /* momentum components: normal / tangential (2D) */
+  int iE = two ? 3 : 2;
+  double rL = uL[0], rR = uR[0];
+  double mL = uL[in] / rL, mR = uR[in] / rR;
+  double tL = two ? uL[it] / rL : 0.0, tR = two ? uR[it] / rR : 0.0;
+  double EL = uL[iE], ER = uR[iE];
+  double pL = (g - 1.0) * (EL - 0.5 * rL * (mL * mL + tL * tL));
+  double pR = (g - 1.0) * (ER - 0.5 * rR * (mR * mR + tR * tR));
+  double cL = sqrt(g * pL / rL), cR = sqrt(g * pR / rR);
+  double rs = 0.5 * (rL + rR), cs = 0.5 * (cL + cR);
+  double ps = 0.5 * (pL + pR + (mL - mR) * (cs * rs));
+  double ss = 0.5 * (mL + mR + (pL - pR) / (cs * rs));
+  double coefL = ps <= pL ? 1.0 : sqrt(1.0 + (g + 1.0) * (ps / pL - 1.0) / (2.0 * g));
+  double coefR = ps <= pR ? 1.0 : sqrt(1.0 + (g + 1.0) * (ps / pR - 1.0) / (2.0 * g));
+  double sL = mL - cL * coefL, sR = mR + cR * coefR;
+  int nv = nvars(c);
+  double fL[4], fR[4];
+  phys_flux(c, uL, dir, fL);
+  phys_flux(c, uR, dir, fR);
+  if (0.0 <= sL) { for (int v = 0; v < nv; ++v) F[v] = fL[v]; return; }
+  const double *uK; const double *fK; double sK, rK, mK, tK, EK, pK;
+  if (0.0 <= ss) { uK = uL; fK = fL; sK = sL; rK = rL; mK = mL; tK = tL; EK = EL; pK = pL; }
+  else if (0.0 <= sR) { uK = uR; fK = fR; sK = sR; rK = rR; mK = mR; tK = tR; EK = ER; pK = pR; }
+  else { for (int v = 0; v < nv; ++v) F[v] = fR[v]; return; }
+  double fac = rK * (sK - mK) / (sK - ss);
+  double us[4];
+  us[0] = fac;
+  us[in] = fac * ss;
+  if (two) us[it] = fac * tK;
+  us[iE] = fac * (EK / rK + (ss - mK) * (ss + pK / (rK * (sK - mK))));
+  for (int v = 0; v < nv; ++v) F[v] = fK[v] + sK * (us[v] - uK[v]);
+}
+
+/* Reading: scalar laws use the local Lax-Friedrichs flux with
+ * alpha = max(|f'(uL)|, |f'(uR)|) (upwind for linear advection). */
+static void llf(const orc_cfg *c, const double *uL, const double *uR, int dir, double *F) {
+  double fL, fR;
+  phys_flux(c, uL, dir, &fL);
+  phys_flux(c, uR, dir, &fR);
+  double aL = fabs(kx_velocity(c, uL, dir)), aR = fabs(kx_velocity(c, uR, dir));
+  double al = aL > aR ? aL : aR;
+  F[0] = 0.5 * (fL + fR) - 0.5 * al * (uR[0] - uL[0]);
+}
+
+static void num_flux(const orc_cfg *c, const double *uL, const double *uR, int dir, double *F) {
+  if (c->eq == 2) hllc(c, uL, uR, dir, F); else llf(c, uL, uR, dir, F);
+}
+
+/* ------------------------------------------------------------------ */
+/* One evaluation of L(U) with the troubled-cell steps (Steps 1-3)    */
+/* ------------------------------------------------------------------ */
+
+static void gather_stencil(const orc_cfg *c, const double *m, int var, int i, int j, stencil_t *st) {
+  if (c->dim == 1) {
+    for (int o = -1; o <= 1; ++o) {
+      st->ub[o + 1] = mom_at(c, m, var, 0, i + o, 0);
+      st->vb[o + 1] = mom_at(c, m, var, 1, i + o, 0);
+    }
+    return;
+  }
+  for (int oy = -1; oy <= 1; ++oy)
+    for (int ox = -1; ox <= 1; ++ox) {
+      int idx = (oy + 1) * 3 + (ox + 1);
+      st->ub[idx] = mom_at(c, m, var, 0, i + ox, j + oy);
+      st->vb[idx] = mom_at(c, m, var, 1, i + ox, j + oy);
+      st->wb[idx] = mom_at(c, m, var, 2, i + ox, j + oy);
+    }
+}
+
+static void reconstruct_all(const orc_cfg *c, const double *m, double *G, const unsigned char *only) {
+  int nv = nvars(c), ny = c->dim == 1 ? 1 : c->ny;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < c->nx; ++i) {
+      size_t cell = (size_t)j * c->nx + i;
+      if (only && !only[cell]) continue;
+      for (int v = 0; v < nv; ++v) {
+        stencil_t st; recon_out ro;
+        gather_stencil(c, m, v, i, j, &st);
+        recon_cell(c->dim, c->dx, c->dy, c->gbar, &st, &ro);
+        memcpy(&G[(cell * nv + v) * 16], ro.vals, sizeof ro.vals);
+      }
+    }
+}
+
+/* KXRCF value aleph for cell (i,j) from the pass-1 point values (eq. (KXRCF),
+ * (line-integral-average); eq. (KXRCF_), (line-integral-average_)).
+ * Readings: sf is the Heaviside step (sf(s) = 1 iff s > 0); the face velocity
+ * is the average of both sides' velocities (GL-weighted along a 2D face);
+ * the indicator variable is u (scalar) or rho (Euler); h = dx; l = 5 so
+ * h^{(l+1)/3} = h^2; ||u|| = max |value| over the cell's GL points;
+ * an empty inflow boundary or a zero norm gives aleph = 0. */
+static double kxrcf_aleph(const orc_cfg *c, const double *G, int i, int j) {
+  int nv = nvars(c);
+  double u[4], un[4];
+  double h = c->dx;
+  if (c->dim == 1) {
+    /* face velocities */
+    for (int v = 0; v < nv; ++v) { un[v] = gl_at(c, G, v, i - 1, 0, 3, 0); u[v] = gl_at(c, G, v, i, 0, 0, 0); }
+    double vl = 0.5 * (kx_velocity(c, un, 0) + kx_velocity(c, u, 0));
+    for (int v = 0; v < nv; ++v) { u[v] = gl_at(c, G, v, i, 0, 3, 0); un[v] = gl_at(c, G, v, i + 1, 0, 0, 0); }
+    double vr = 0.5 * (kx_velocity(c, u, 0) + kx_velocity(c, un, 0));
+    double jl = gl_at(c, G, 0, i, 0, 0, 0) - gl_at(c, G, 0, i - 1, 0, 3, 0);
+    double jr = gl_at(c, G, 0, i, 0, 3, 0) - gl_at(c, G, 0, i + 1, 0, 0, 0);
+    double s = jl * (vl > 0.0 ? 1.0 : 0.0) + jr * (-vr > 0.0 ? 1.0 : 0.0);
+    double nrm = 0.0;
+    for (int k = 0; k < 4; ++k) { double a = fabs(gl_at(c, G, 0, i, 0, k, 0)); if (a > nrm) nrm = a; }
+    if (nrm == 0.0) return 0.0;
+    return fabs(s) / (h * h * nrm);
+  }
+  double vxl = 0.0, vxr = 0.0, vyb = 0.0, vyt = 0.0;
+  for (int l = 0; l < 4; ++l) {
+    for (int v = 0; v < nv; ++v) { un[v] = gl_at(c, G, v, i - 1, j, 3, l); u[v] = gl_at(c, G, v, i, j, 0, l); }
+    vxl += gl_weight(l) * 0.5 * (kx_velocity(c, un, 0) + kx_velocity(c, u, 0));
+    for (int v = 0; v < nv; ++v) { u[v] = gl_at(c, G, v, i, j, 3, l); un[v] = gl_at(c, G, v, i + 1, j, 0, l); }
+    vxr += gl_weight(l) * 0.5 * (kx_velocity(c, u, 0) + kx_velocity(c, un, 0));
+  }
+  for (int k = 0; k < 4; ++k) {
+    for (int v = 0; v < nv; ++v) { un[v] = gl_at(c, G, v, i, j - 1, k, 3); u[v] = gl_at(c, G, v, i, j, k, 0); }
+    vyb += gl_weight(k) * 0.5 * (kx_velocity(c, un, 1) + kx_velocity(c, u, 1));
+    for (int v = 0; v < nv; ++v) { u[v] = gl_at(c, G, v, i, j, k, 3); un[v] = gl_at(c, G, v, i, j + 1, k, 0); }
+    vyt += gl_weight(k) * 0.5 * (kx_velocity(c, u, 1) + kx_velocity(c, un, 1));
+  }
+  double s = 0.0, len = 0.0;
+  if (vxl > 0.0) {
+    for (int l = 0; l < 4; ++l) s += c->dy * gl_weight(l) * (gl_at(c, G, 0, i, j, 0, l) - gl_at(c, G, 0, i - 1, j, 3, l));
+    len += c->dy;
+  }
+  if (-vxr > 0.0) {
+    for (int l = 0; l < 4; ++l) s += c->dy * gl_weight(l) * (gl_at(c, G, 0, i, j, 3, l) - gl_at(c, G, 0, i + 1, j, 0, l));
+    len += c->dy;
+  }
+  if (vyb > 0.0) {
+    for (int k = 0; k < 4; ++k) s += c->dx * gl_weight(k) * (gl_at(c, G, 0, i, j, k, 0) - gl_at(c, G, 0, i, j - 1, k, 3));
+    len += c->dx;
+  }
+  if (-vyt > 0.0) {
+    for (int k = 0; k < 4; ++k) s += c->dx * gl_weight(k) * (gl_at(c, G, 0, i, j, k, 3) - gl_at(c, G, 0, i, j + 1, k, 0));
+    len += c->dx;
+  }
+  double nrm = 0.0;
+  for (int k = 0; k < 4; ++k) for (int l = 0; l < 4; ++l) { double a = fabs(gl_at(c, G, 0, i, j, k, l)); if (a > nrm) nrm = a; }
+  if (len == 0.0 || nrm == 0.0) return 0.0;
+  return fabs(s) / len / (h * h * nrm);
+}
+
+static int finite_state(const orc_cfg *c, const double *m) {
+  size_t n = (size_t)nvars(c) * nmoms(c) * ncell(c);
+  for (size_t t = 0; t < n; ++t) if (!isfinite(m[t])) return 0;
+  return 1;
+}
+
+/*
+ * One evaluation of the spatial operator with the troubled-cell steps.
+ *   U     : stage input (not modified)
+ *   Umod  : out, U with the first moments of troubled cells replaced (Step 2.2)
+ *   Lout  : out, L(Umod) in the state layout
+ *   mask  : out, troubled flags per cell (may be NULL)
+ *   aleph : out, KXRCF values per cell (may be NULL)
+ */
+int orc_rhs(const orc_cfg *c, const double *U, double *Umod, double *Lout,
+            unsigned char *mask, double *aleph) {
+  if (build_tables(c->dim)) return ORC_EINVAL;
+  int nv = nvars(c), nm = nmoms(c), ny = c->dim == 1 ? 1 : c->ny;
+  size_t nc = ncell(c), nstate = (size_t)nv * nm * nc;
+  double *G = malloc(nc * nv * 16 * sizeof(double));
+  unsigned char *flag = calloc(nc, 1);
+  /* Step 1: pass-1 point values in every cell */
+  reconstruct_all(c, U, G, NULL);
+  /* Step 2.1: troubled cells */
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < c->nx; ++i) {
+      size_t cell = (size_t)j * c->nx + i;
+      double a = 0.0;
+      if (c->indicator == 1) a = kxrcf_aleph(c, G, i, j);
+      if (aleph) aleph[cell] = a;
+      flag[cell] = c->indicator == 2 ? 1 : (c->indicator == 1 && a > 1.0);
+    }
+  /* Step 2.2: modify first moments of troubled cells (eq. (vi), applied
+   * dimension by dimension in 2D).  Reading: every new value is computed
+   * from the pre-modification moments (Jacobi). */
+  memcpy(Umod, U, nstate * sizeof(double));
+  const double *w = c->dim == 1 ? T1.mod : T2.mod;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < c->nx; ++i) {
+      size_t cell = (size_t)j * c->nx + i;
+      if (!flag[cell]) continue;
+      for (int v = 0; v < nv; ++v) {
+        *MOM(c, Umod, v, 1, i, j) = w[0] * mom_at(c, U, v, 0, i - 1, j) + w[1] * mom_at(c, U, v, 0, i, j)
+                                  + w[2] * mom_at(c, U, v, 0, i + 1, j)
+                                  + w[3] * mom_at(c, U, v, 1, i - 1, j) + w[4] * mom_at(c, U, v, 1, i + 1, j);
+        if (c->dim == 2)
+          *MOM(c, Umod, v, 2, i, j) = w[0] * mom_at(c, U, v, 0, i, j - 1) + w[1] * mom_at(c, U, v, 0, i, j)
+                                    + w[2] * mom_at(c, U, v, 0, i, j + 1)
+                                    + w[3] * mom_at(c, U, v, 2, i, j - 1) + w[4] * mom_at(c, U, v, 2, i, j + 1);
+      }
+    }
+  /* Step 2.3: re-reconstruct the troubled cells from the modified moments */
+  reconstruct_all(c, Umod, G, flag);
+  /* Step 3: fluxes, quadrature, semi-discrete right-hand sides */
+  memset(Lout, 0, nstate * sizeof(double));
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < c->nx; ++i) {
+      double uL[4], uR[4], fh[4], fp[4];
+      if (c->dim == 1) {
+        double fm[4], fpl[4], F[4] = {0, 0, 0, 0};
+        for (int v = 0; v < nv; ++v) { uL[v] = gl_at(c, G, v, i - 1, 0, 3, 0); uR[v] = gl_at(c, G, v, i, 0, 0, 0); }
+        num_flux(c, uL, uR, 0, fm);
+        for (int v = 0; v < nv; ++v) { uL[v] = gl_at(c, G, v, i, 0, 3, 0); uR[v] = gl_at(c, G, v, i + 1, 0, 0, 0); }
+        num_flux(c, uL, uR, 0, fpl);
+        for (int k = 0; k < 4; ++k) {           /* eq. (F) */
+          double u[4];
+          for (int v = 0; v < nv; ++v) u[v] = gl_at(c, G, v, i, 0, k, 0);
+          phys_flux(c, u, 0, fp);
+          for (int v = 0; v < nv; ++v) F[v] += gl_weight(k) * fp[v];
+        }
+        for (int v = 0; v < nv; ++v) {          /* eq. (1D-equ-int-approximation) */
+          *MOM(c, Lout, v, 0, i, 0) = -(fpl[v] - fm[v]) / c->dx;
+          *MOM(c, Lout, v, 1, i, 0) = -(fpl[v] + fm[v]) / (2.0 * c->dx) + F[v] / c->dx;
+        }
+        continue;
+      }
+      /* 2D: face integrals by eq. (integral2)/(integral3), cell integrals by eq. (integral1) */
+      double Fx_p[4] = {0}, Fx_m[4] = {0}, Fx_pe[4] = {0}, Fx_me[4] = {0};
+      double Gy_p[4] = {0}, Gy_m[4] = {0}, Gy_px[4] = {0}, Gy_mx[4] = {0};
+      double Fc[4] = {0}, Gc[4] = {0};
+      for (int l = 0; l < 4; ++l) {
+        double wl = gl_weight(l), eta = gl_node(l);
+        for (int v = 0; v < nv; ++v) { uL[v] = gl_at(c, G, v, i, j, 3, l); uR[v] = gl_at(c, G, v, i + 1, j, 0, l); }
+        num_flux(c, uL, uR, 0, fh);
+        for (int v = 0; v < nv; ++v) { Fx_p[v] += wl * fh[v]; Fx_pe[v] += wl * eta * fh[v]; }
+        for (int v = 0; v < nv; ++v) { uL[v] = gl_at(c, G, v, i - 1, j, 3, l); uR[v] = gl_at(c, G, v, i, j, 0, l); }
+        num_flux(c, uL, uR, 0, fh);
+        for (int v = 0; v < nv; ++v) { Fx_m[v] += wl * fh[v]; Fx_me[v] += wl * eta * fh[v]; }
+      }
+      for (int k = 0; k < 4; ++k) {
+        double wk = gl_weight(k), xi = gl_node(k);
+        for (int v = 0; v < nv; ++v) { uL[v] = gl_at(c, G, v, i, j, k, 3); uR[v] = gl_at(c, G, v, i, j + 1, k, 0); }
+        num_flux(c, uL, uR, 1, fh);
+        for (int v = 0; v < nv; ++v) { Gy_p[v] += wk * fh[v]; Gy_px[v] += wk * xi * fh[v]; }
+        for (int v = 0; v < nv; ++v) { uL[v] = gl_at(c, G, v, i, j - 1, k, 3); uR[v] = gl_at(c, G, v, i, j, k, 0); }
+        num_flux(c, uL, uR, 1, fh);
+        for (int v = 0; v < nv; ++v) { Gy_m[v] += wk * fh[v]; Gy_mx[v] += wk * xi * fh[v]; }
+      }
+      for (int k = 0; k < 4; ++k)
+        for (int l = 0; l < 4; ++l) {
+          double u[4], fx[4], gy[4];
+          for (int v = 0; v < nv; ++v) u[v] = gl_at(c, G, v, i, j, k, l);
+          phys_flux(c, u, 0, fx);
+          phys_flux(c, u, 1, gy);
+          for (int v = 0; v < nv; ++v) {
+            Fc[v] += gl_weight(k) * gl_weight(l) * fx[v];
+            Gc[v] += gl_weight(k) * gl_weight(l) * gy[v];
+          }
+        }
+      for (int v = 0; v < nv; ++v) {            /* eq. (2D-equ-int-approximation) */
+        *MOM(c, Lout, v, 0, i, j) = -(Fx_p[v] - Fx_m[v]) / c->dx - (Gy_p[v] - Gy_m[v]) / c->dy;
+        *MOM(c, Lout, v, 1, i, j) = -(Fx_p[v] + Fx_m[v]) / (2.0 * c->dx) + Fc[v] / c->dx
+                                    - (Gy_px[v] - Gy_mx[v]) / c->dy;
+        *MOM(c, Lout, v, 2, i, j) = -(Fx_pe[v] - Fx_me[v]) / c->dx
+                                    - (Gy_p[v] + Gy_m[v]) / (2.0 * c->dy) + Gc[v] / c->dy;
+      }
+    }
+  if (mask) memcpy(mask, flag, nc);
+  free(G);
+  free(flag);
+  return finite_state(c, Lout) ? ORC_OK : ORC_ENONPHYSICAL;
+}
+
+/*
+ * One SSP-RK3 step, eq. (Runge-Kutta), in place on m.
+ * Reading: the modified moments of Step 2.2 replace the stage input and are
+ * the ones the Runge-Kutta combination uses (so stage 1 also modifies U^n).
+ * masks (may be NULL): 3 x ncell troubled flags of the three stages.
+ */
+int orc_step(const orc_cfg *c, double *m, double dt, unsigned char *masks) {
+  size_t nc = ncell(c), n = (size_t)nvars(c) * nmoms(c) * nc;
+  double *Un = malloc(n * sizeof(double)), *U1 = malloc(n * sizeof(double));
+  double *U2 = malloc(n * sizeof(double)), *Um = malloc(n * sizeof(double)), *L = malloc(n * sizeof(double));
+  int rc = orc_rhs(c, m, Un, L, masks ? masks : NULL, NULL);
+  if (rc == ORC_OK) {
+    for (size_t t = 0; t < n; ++t) U1[t] = Un[t] + dt * L[t];
+    rc = orc_rhs(c, U1, Um, L, masks ? masks + nc : NULL, NULL);
+  }
+  if (rc == ORC_OK) {
+    for (size_t t = 0; t < n; ++t) U2[t] = 0.75 * Un[t] + 0.25 * Um[t] + 0.25 * dt * L[t];
+    rc = orc_rhs(c, U2, Um, L, masks ? masks + 2 * nc : NULL, NULL);
+  }
+  if (rc == ORC_OK) {
+    for (size_t t = 0; t < n; ++t) U1[t] = Un[t] / 3.0 + 2.0 / 3.0 * Um[t] + 2.0 / 3.0 * dt * L[t];
+    if (!finite_state(c, U1)) rc = ORC_ENONPHYSICAL;
+    else memcpy(m, U1, n * sizeof(double));
+  }
+  free(Un); free(U1); free(U2); free(Um); free(L);
+  return rc;
+}
+
+/* Reading of the CFL rule (CFL 0.6 in Sec. 3, formula not printed):
+ *   1D dt = cfl dx / max(|f'(ubar)|) or max(|mu|+c) from cell averages;
+ *   2D dt = cfl / (max(a_x)/dx + max(a_y)/dy). */
+double orc_max_dt(const orc_cfg *c, const double *m, double cfl) {
+  int nv = nvars(c), ny = c->dim == 1 ? 1 : c->ny;
+  double ax = 0.0, ay = 0.0;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < c->nx; ++i) {
+      double u[4];
+      for (int v = 0; v < nv; ++v) u[v] = *MOM(c, (double *)m, v, 0, i, j);
+      double sx, sy = 0.0;
+      if (c->eq == 0) { sx = fabs(c->adv_a); sy = fabs(c->adv_b); }
+      else if (c->eq == 1) { sx = fabs(u[0]); sy = fabs(u[0]); }
+      else {
+        double rho = u[0], mu = u[1] / rho, nu = c->dim == 2 ? u[2] / rho : 0.0, E = u[nv - 1];
+        double p = (c->gamma - 1.0) * (E - 0.5 * rho * (mu * mu + nu * nu));
+        double cs = sqrt(c->gamma * p / rho);
+        sx = fabs(mu) + cs; sy = fabs(nu) + cs;
+      }
+      if (sx > ax) ax = sx;
+      if (sy > ay) ay = sy;
+    }
+  if (c->dim == 1) return cfl * c->dx / ax;
+  return cfl / (ax / c->dx + ay / c->dy);
+}
+
+/* ------------------------------------------------------------------ */
+/* Exposed pieces, for the pins                                        */
+/* ------------------------------------------------------------------ */
+
+/* The five weights of the modified first moment derived from p_0. */
+int orc_modification_weights(double out[5]) {
+  return build_modification(out);
+}
+
+/* Reconstruct one variable of one cell.
+ * data: 1D -> 6 values (ubar_{-1,0,1}, vbar_{-1,0,1});
+ *       2D -> 27 values (ubar[9], vbar[9], wbar[9], each in paper label order 1..9).
+ * vals: 4 (1D) or 16 (2D, [k*4+l]); beta[4], omega[4]: l = 1..4. */
+int orc_recon_cell(int dim, double dx, double dy, const double gbar[4], const double *data,
+                   double *vals, double *beta, double *omega) {
+  if (build_tables(dim)) return ORC_EINVAL;
+  stencil_t st;
+  memset(&st, 0, sizeof st);
+  if (dim == 1) { for (int t = 0; t < 3; ++t) { st.ub[t] = data[t]; st.vb[t] = data[3 + t]; } }
+  else { for (int t = 0; t < 9; ++t) { st.ub[t] = data[t]; st.vb[t] = data[9 + t]; st.wb[t] = data[18 + t]; } }
+  recon_out ro;
+  recon_cell(dim, dx, dy, gbar, &st, &ro);
+  memcpy(vals, ro.vals, (dim == 1 ? 4 : 16) * sizeof(double));
+  for (int l = 0; l < 4; ++l) { if (beta) beta[l] = ro.beta[l + 1]; if (omega) omega[l] = ro.omega[l + 1]; }
+  return ORC_OK;
+}
+
+/* Polynomial q_l (l = 1..4) of one cell: writes its monomial coefficients
+ * coef[a*6+b] (xi^a eta^b) from the same data layout as orc_recon_cell.
+ * With lin == 2, writes p_l of eq. (p) instead; with lin == 1, the
+ * linear-weight polynomial sum_l gamma_{l,4} p_l (omega = gamma). */
+int orc_poly(int dim, int level, int lin, const double gbar[4], const double *data, double coef[36]) {
+  if (build_tables(dim)) return ORC_EINVAL;
+  stencil_t st;
+  memset(&st, 0, sizeof st);
+  if (dim == 1) { for (int t = 0; t < 3; ++t) { st.ub[t] = data[t]; st.vb[t] = data[3 + t]; } }
+  else { for (int t = 0; t < 9; ++t) { st.ub[t] = data[t]; st.vb[t] = data[9 + t]; st.wb[t] = data[18 + t]; } }
+  const tables_t *T = dim == 1 ? &T1 : &T2;
+  poly2 q[5], p[5];
+  memset(q, 0, sizeof q);
+  q[1].c[0][0] = st_get(&st, dim, 0, 0, 0);
+  for (int l = 2; l <= 4; ++l) {
+    const level_t *L = &T->q[l];
+    double d[23];
+    for (int r = 0; r < L->ncond; ++r) d[r] = st_get(&st, dim, L->cond[r].kind, L->cond[r].ox, L->cond[r].oy);
+    level_poly(L, d, &q[l]);
+  }
+  poly2 out;
+  if (!lin) {
+    if (level < 1 || level > 4) return ORC_EINVAL;
+    out = q[level];
+  } else {
+    p[1] = q[1];
+    for (int l2 = 2; l2 <= 4; ++l2) {
+      double gll = lin_weight(gbar, l2, l2);
+      for (int a = 0; a < PMAX; ++a) for (int b = 0; b < PMAX; ++b) {
+        double s = q[l2].c[a][b] / gll;
+        for (int l = 1; l < l2; ++l) s -= lin_weight(gbar, l, l2) / gll * p[l].c[a][b];
+        p[l2].c[a][b] = s;
+      }
+    }
+    memset(&out, 0, sizeof out);
+    if (lin == 2) {
+      if (level < 1 || level > 4) return ORC_EINVAL;
+      out = p[level];
+    } else {
+      for (int l = 1; l <= 4; ++l)
+        for (int a = 0; a < PMAX; ++a) for (int b = 0; b < PMAX; ++b) out.c[a][b] += lin_weight(gbar, l, 4) * p[l].c[a][b];
+    }
+  }
+  for (int a = 0; a < PMAX; ++a) for (int b = 0; b < PMAX; ++b) coef[a * 6 + b] = out.c[a][b];
+  return ORC_OK;
+}
+
+/* Solution matrix of level l (coef = M . data in the level's own condition
+ * order), for comparing with independently derived tables.
+ * Writes nmono*ncond values row-major and the exponent and condition lists. */
+int orc_level_matrix(int dim, int level, int *nmono, int *ncond, int *ma, int *mb,
+                     int *ckind, int *cox, int *coy, double *M) {
+  if (build_tables(dim) || level < 2 || level > 4) return ORC_EINVAL;
+  const level_t *L = dim == 1 ? &T1.q[level] : &T2.q[level];
+  *nmono = L->nmono; *ncond = L->ncond;
+  for (int k = 0; k < L->nmono; ++k) { ma[k] = L->ma[k]; mb[k] = L->mb[k]; }
+  for (int r = 0; r < L->ncond; ++r) { ckind[r] = L->cond[r].kind; cox[r] = L->cond[r].ox; coy[r] = L->cond[r].oy; }
+  for (int k = 0; k < L->nmono; ++k) for (int r = 0; r < L->ncond; ++r) M[k * L->ncond + r] = L->M[k][r];
+  return ORC_OK;
+}
+
+/* Numerical flux between two states (for the HLLC / LLF pins). */
+void orc_num_flux(const orc_cfg *c, const double *uL, const double *uR, int dir, double *F) {
+  num_flux(c, uL, uR, dir, F);
+}
+
+void orc_phys_flux(const orc_cfg *c, const double *u, int dir, double *f) { phys_flux(c, u, dir, f); }
+
+/* Conservation totals: sum over cells of ubar * dx * dy, per variable. */
+void orc_totals(const orc_cfg *c, const double *m, double *sums) {
+  int nv = nvars(c), ny = c->dim == 1 ? 1 : c->ny;
+  double area = c->dx * (c->dim == 1 ? 1.0 : c->dy);
+  for (int v = 0; v < nv; ++v) {
+    long double s = 0.0L;
+    for (int j = 0; j < ny; ++j) for (int i = 0; i < c->nx; ++i) s += *MOM(c, (double *)m, v, 0, i, j);
+    sums[v] = (double)(s * area);
+  }
+}
