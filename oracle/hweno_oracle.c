@@ -618,9 +618,14 @@ static void reconstruct_all(const orc_cfg *c, const double *m, double *G, const 
     }
 }
 
+/* Reading: a face is inflow when its velocity exceeds KX_VDEAD (absolute, in
+ * the problem's velocity units): a fluid exactly at rest has face velocities
+ * that are pure rounding noise, whose sign must not decide the indicator. */
+#define KX_VDEAD 1e-12
+
 /* KXRCF value aleph for cell (i,j) from the pass-1 point values (eq. (KXRCF),
  * (line-integral-average); eq. (KXRCF_), (line-integral-average_)).
- * Readings: sf is the Heaviside step (sf(s) = 1 iff s > 0); the face velocity
+ * Readings: sf is the Heaviside step (sf(s) = 1 iff s > KX_VDEAD); the face velocity
  * is the average of both sides' velocities (GL-weighted along a 2D face);
  * the indicator variable is u (scalar) or rho (Euler); h = dx; l = 5 so
  * h^{(l+1)/3} = h^2; ||u|| = max |value| over the cell's GL points;
@@ -637,7 +642,7 @@ static double kxrcf_aleph(const orc_cfg *c, const double *G, int i, int j) {
     double vr = 0.5 * (kx_velocity(c, u, 0) + kx_velocity(c, un, 0));
     double jl = gl_at(c, G, 0, i, 0, 0, 0) - gl_at(c, G, 0, i - 1, 0, 3, 0);
     double jr = gl_at(c, G, 0, i, 0, 3, 0) - gl_at(c, G, 0, i + 1, 0, 0, 0);
-    double s = jl * (vl > 0.0 ? 1.0 : 0.0) + jr * (-vr > 0.0 ? 1.0 : 0.0);
+    double s = jl * (vl > KX_VDEAD ? 1.0 : 0.0) + jr * (-vr > KX_VDEAD ? 1.0 : 0.0);
     double nrm = 0.0;
     for (int k = 0; k < 4; ++k) { double a = fabs(gl_at(c, G, 0, i, 0, k, 0)); if (a > nrm) nrm = a; }
     if (nrm == 0.0) return 0.0;
@@ -657,19 +662,19 @@ static double kxrcf_aleph(const orc_cfg *c, const double *G, int i, int j) {
     vyt += gl_weight(k) * 0.5 * (kx_velocity(c, u, 1) + kx_velocity(c, un, 1));
   }
   double s = 0.0, len = 0.0;
-  if (vxl > 0.0) {
+  if (vxl > KX_VDEAD) {
     for (int l = 0; l < 4; ++l) s += c->dy * gl_weight(l) * (gl_at(c, G, 0, i, j, 0, l) - gl_at(c, G, 0, i - 1, j, 3, l));
     len += c->dy;
   }
-  if (-vxr > 0.0) {
+  if (-vxr > KX_VDEAD) {
     for (int l = 0; l < 4; ++l) s += c->dy * gl_weight(l) * (gl_at(c, G, 0, i, j, 3, l) - gl_at(c, G, 0, i + 1, j, 0, l));
     len += c->dy;
   }
-  if (vyb > 0.0) {
+  if (vyb > KX_VDEAD) {
     for (int k = 0; k < 4; ++k) s += c->dx * gl_weight(k) * (gl_at(c, G, 0, i, j, k, 0) - gl_at(c, G, 0, i, j - 1, k, 3));
     len += c->dx;
   }
-  if (-vyt > 0.0) {
+  if (-vyt > KX_VDEAD) {
     for (int k = 0; k < 4; ++k) s += c->dx * gl_weight(k) * (gl_at(c, G, 0, i, j, k, 3) - gl_at(c, G, 0, i, j + 1, k, 0));
     len += c->dx;
   }

@@ -557,3 +557,30 @@ def test_shock_tube_converges_to_exact_riemann(orc, golden, name):
     if name == "lax":
         lax = golden["lax_problem"]
         assert list(p.meta["left"]) == lax["left"] and list(p.meta["right"]) == lax["right"]
+
+
+# ------------------------------------------------------------- linear stability (a property of the scheme)
+
+def test_linear_spectrum_and_ssp_rk3_limit(orc):
+    """Jacobian of L for linear advection at tiny amplitude (the weights sit at
+    their linear values): no eigenvalue in the right half plane (the upwind
+    flux is dissipative or neutral), and SSP-RK3 keeps |R(dt lambda)| <= 1 up to
+    CFL ~ 0.569 only.  The paper's CFL 0.6 is just beyond: its largest
+    amplification is ~1.17 per step, which rounding noise excites."""
+    N = 48
+    dx = 2 * math.pi / N
+    cfg = orc.make_cfg(1, N, dx=dx, eq="advection", adv=(1.0, 0.0), indicator="none")
+    amp, n = 1e-9, 2 * N
+    A = np.zeros((n, n))
+    for k in range(n):
+        U = np.zeros(n)
+        U[k] = amp
+        A[:, k] = orc.rhs(cfg, U.reshape(1, 2, 1, N))[1].reshape(-1) / amp
+    lam = np.linalg.eigvals(A) * dx
+    assert lam.real.max() < 1e-12
+
+    def amp_max(cfl):
+        z = cfl * lam
+        return np.abs(1 + z + z * z / 2 + z ** 3 / 6).max()
+    assert amp_max(0.56) <= 1.0 + 1e-12
+    assert 1.15 < amp_max(0.6) < 1.2
