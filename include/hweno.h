@@ -1,0 +1,156 @@
+/*
+ * hweno.h -- C ABI of the GB300 (sm_103a) implementation of the moment-based
+ * multi-resolution HWENO scheme of J. Li, C.-W. Shu and J. Qiu,
+ * "Moment-based multi-resolution HWENO scheme for hyperbolic conservation
+ * laws" (arXiv 2201.12193).  Section, equation and table names below are the
+ * paper's.
+ *
+ * What one step computes (Sec. 2.1 for 1D, Sec. 2.2 for 2D): for every cell
+ * and every conserved variable, point values at the Gauss-Lobatto points are
+ * reconstructed from the zeroth and first moments of the 3-cell / 3x3-cell
+ * stencil (Step 1: nested central polynomials q_1..q_4, WENO-Z weights of
+ * eq. (non-linear-weight) with any positive linear weights); troubled cells
+ * are found with the KXRCF indicator (eq. (KXRCF) / (KXRCF_)) and their first
+ * moments replaced by eq. (vi) (Step 2); HLLC (Euler, eq. (f_HLLC)) or local
+ * Lax-Friedrichs (scalar laws) fluxes and the Gauss-Lobatto quadratures of
+ * eq. (F) / (integral1)-(integral3) give L(U) of eq. (1D-equ-int-approximation)
+ * / (2D-equ-int-approximation), advanced by the SSP Runge-Kutta method of
+ * eq. (Runge-Kutta) (Step 3).
+ *
+ * State layout everywhere: FP64 m[var][moment][j][i], contiguous in i, no
+ * padding, j of size 1 in 1D.  Variables: (u) for scalar laws; (rho, rho*mu, E)
+ * for 1D Euler; (rho, rho*mu, rho*nu, E) for 2D Euler.  Moments (eq. (1D-moment)
+ * / (2D-moment)): 0 = cell average, 1 = first moment in x ((x-x_i)/dx
+ * weighted), 2 = first moment in y (2D only).  count arguments are element
+ * counts nvar * nmom * ny * nx and must match exactly.
+ *
+ * Ownership: the library allocates and frees all device memory it uses for a
+ * handle; every pointer passed in belongs to the caller.  Device pointers
+ * must be on the handle's device.  Errors never cross the ABI as exceptions:
+ * each call returns an hweno_status and hweno_last_error() describes it.
+ * A handle is not thread-safe; use one handle per host thread.
+ *
+ * Streams: work is enqueued on the handle's stream (hweno_set_stream; default
+ * the legacy default stream).  hweno_step is asynchronous.  hweno_max_dt,
+ * hweno_get_moments (host destination), hweno_troubled_mask, hweno_totals and
+ * hweno_sync synchronise the stream; they also report a non-physical state
+ * left by the last step (HWENO_ENONPHYSICAL), after which the state has been
+ * rolled back to the one before that step.
+ */
+#ifndef HWENO_H
+#define HWENO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hweno_s* hweno_t;
+
+typedef enum {
+  HWENO_OK = 0,
+  HWENO_EINVAL = -1,        /* bad argument (size, pointer, grid, count) */
+  HWENO_ECUDA = -2,         /* a CUDA runtime call failed */
+  HWENO_ENONPHYSICAL = -3,  /* non-finite value, rho <= 0 or p <= 0 after a step */
+  HWENO_ETIMEOUT = -4,      /* a bounded device wait gave up */
+  HWENO_ESTATE = -5,        /* call out of order (e.g. no moments set) */
+  HWENO_ENOMEM = -6         /* device allocation failed */
+} hweno_status;
+
+typedef enum { HWENO_ADVECTION = 0, HWENO_BURGERS = 1, HWENO_EULER = 2 } hweno_eq;
+typedef enum { HWENO_BC_PERIODIC = 0, HWENO_BC_TRANSMISSIVE = 1 } hweno_bc_kind;
+typedef enum { HWENO_IND_NONE = 0, HWENO_IND_KXRCF = 1, HWENO_IND_ALL = 2 } hweno_indicator;
+
+/* Uniform mesh and scheme options.
+ *   dim 1 or 2; nx, ny >= 4 (ny ignored in 1D); 2D cells must be square
+ *   (dx == dy to 1e-12 relative) because the smoothness indicators of
+ *   eq. (2D-beta), eq. (2D-beta1) and h of eq. (KXRCF_) are stated for them.
+ *   eq: advection (f = adv_a u, g = adv_b u), Burgers (f = g = u^2/2) or Euler.
+ *   precision: 0 = FP64 throughout; 1 = FP32 reconstruction, indicator, flux
+ *   and quadrature with FP64 state, FP64 Runge-Kutta accumulation and FP64
+ *   differences of the face fluxes in the cell-average equation.
+ *   indicator: HWENO_IND_KXRCF is the scheme (HWENO6-M5-I); NONE gives HWENO6
+ *   (no modification); ALL gives HWENO6-M5-NI (every cell modified) (Sec. 3).
+ *   gamma_bar: positive linear-weight seeds of eq. (linear-weight)
+ *   (gamma_{l1,l2} = gamma_bar[l1-1] / sum_{l<=l2} gamma_bar[l-1]); the paper
+ *   uses {1, 10, 100, 1000}.
+ *   beta_of_q: 0 = smoothness indicators of p_l as eq. (beta) states (default);
+ *   1 = of q_l (the variant for which Remark 1's expansion holds for every l). */
+typedef struct {
+  int dim;
+  int nx, ny;
+  double x0, x1, y0, y1;
+  int eq;
+  double adv_a, adv_b;
+  int precision;
+  int indicator;
+  double gamma_bar[4];
+  int beta_of_q;
+} hweno_grid;
+
+/* Boundary kinds of the four sides.  Periodic sides must come in pairs.
+ * Transmissive = the mirror image about the boundary face (the cell average
+ * and the tangential first moment are copied, the normal first moment changes
+ * sign); ghost cells are images of interior cells throughout a stage. */
+typedef struct { int xlo, xhi, ylo, yhi; } hweno_bc;
+
+/* Create a solver.  gamma: ratio of specific heats (Euler; ignored otherwise).
+ * Allocates all device buffers on the current device.  Returns EINVAL for a bad
+ * grid, ENOMEM if allocation fails.  *out is NULL on failure. */
+hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gamma, hweno_t* out);
+
+/* Release everything the handle owns (waits for its stream first). */
+void hweno_destroy(hweno_t h);
+
+/* Use cuda_stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream). */
+hweno_status hweno_set_stream(hweno_t h, void* cuda_stream);
+
+/* Copy moments in (on_device = 0: pageable or pinned host; 1: device pointer). */
+hweno_status hweno_set_moments(hweno_t h, const double* m, size_t count, int on_device);
+
+/* Copy the current moments out (synchronises when the destination is host memory). */
+hweno_status hweno_get_moments(hweno_t h, double* m, size_t count, int on_device);
+
+/* One SSP-RK3 step of size dt (three stages, eq. (Runge-Kutta)); asynchronous.
+ * Reading: the first moments modified in troubled cells replace the stage
+ * input and enter the Runge-Kutta combination. */
+hweno_status hweno_step(hweno_t h, double dt);
+
+/* dt for the next step from the cell averages (CFL rule of Sec. 3, formula not
+ * printed there; reading): 1D dt = cfl dx / max(|f'|) or max(|mu| + c);
+ * 2D dt = cfl / (max(a_x)/dx + max(a_y)/dy).  Synchronises. */
+hweno_status hweno_max_dt(hweno_t h, double cfl, double* dt_out);
+
+/* Troubled-cell flags of the three stages of the last step, [3][ny][nx] bytes
+ * (0/1), host memory.  Synchronises. */
+hweno_status hweno_troubled_mask(hweno_t h, unsigned char* mask, size_t count);
+
+/* Conservation totals sum(ubar) * dx * dy per variable (FP64), host array of
+ * nvar doubles.  Synchronises. */
+hweno_status hweno_totals(hweno_t h, double* sums);
+
+/* Wait for the handle's stream; report a non-physical last step. */
+hweno_status hweno_sync(hweno_t h);
+
+/* One evaluation of the spatial operator with the troubled-cell steps on a
+ * caller-given state (all device pointers, state layout):
+ *   U    in : stage input;
+ *   Umod out: U with the first moments of troubled cells replaced (eq. (vi));
+ *   L    out: L(Umod);
+ *   mask out: troubled flags [ny][nx] bytes;
+ *   aleph out (may be NULL): KXRCF values [ny][nx] doubles.
+ * Asynchronous on the handle's stream. */
+hweno_status hweno_rhs(hweno_t h, const double* U, double* Umod, double* L, unsigned char* mask, double* aleph);
+
+/* Message of the last error on this handle (never NULL). */
+const char* hweno_last_error(hweno_t h);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int hweno_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HWENO_H */

@@ -1,0 +1,232 @@
+// One-dimensional stage pipeline of the moment-based multi-resolution HWENO
+// scheme (Sec. 2.1 of Li, Shu & Qiu, arXiv 2201.12193) on sm_103a.
+//
+// Same four steps per Runge-Kutta stage as the 2D pipeline:
+//   rec1d    Step 1: 3-cell moments -> 4 Gauss-Lobatto values (eq. (re-u))
+//   flag1d   Step 2.1/2.2: KXRCF (eq. (KXRCF), (line-integral-average)) and
+//            the modified first moment of eq. (vi) in troubled cells
+//   rec1d*   Step 2.3: troubled cells again from the modified moments
+//   update1d Step 3: HLLC/LLF fluxes, quadrature of eq. (F), L(U) of
+//            eq. (1D-equ-int-approximation), SSP-RK3 (eq. (Runge-Kutta)).
+#include <algorithm>
+
+#include "hweno_internal.h"
+
+namespace hw {
+namespace {
+
+constexpr int RB = 128;
+
+__device__ __forceinline__ int mpt1(const Img& m, int k) { return m.sx < 0 ? 3 - k : k; }
+
+template <bool FLAGGED>
+__device__ __forceinline__ double load_mom1(const Prob& P, const double* __restrict__ U, const uint8_t* __restrict__ mask,
+                                            const double* __restrict__ Mod, int var, int kind, const Img& m) {
+  if (kind == 0) return U[sidx(P, var, 0, m.i, 0)];
+  double v;
+  if (FLAGGED && mask[m.i]) v = Mod[(long long)var * P.plane + m.i];
+  else v = U[sidx(P, var, 1, m.i, 0)];
+  return m.sx < 0 ? -v : v;
+}
+
+template <typename T, int NV, bool FLAGGED>
+__global__ void __launch_bounds__(RB) rec1d_kernel(Prob P, Weights<T> W, Beta1<T> B, const double* __restrict__ U,
+                                                  const uint8_t* __restrict__ mask, const double* __restrict__ Mod,
+                                                  const int* __restrict__ list, const int* __restrict__ count,
+                                                  T* __restrict__ G, T* __restrict__ aux) {
+  const int n = FLAGGED ? *count : P.nx;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int i = FLAGGED ? list[t] : t;
+    const Img nb[3] = {image(P, i - 1, 0), image(P, i, 0), image(P, i + 1, 0)};
+    T vals0[4];
+    T pl = T(0), pr = T(0);
+#pragma unroll 1
+    for (int v = 0; v < NV; ++v) {
+      T d[6];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        d[c] = T(load_mom1<FLAGGED>(P, U, mask, Mod, v, 0, nb[c]));
+        d[3 + c] = T(load_mom1<FLAGGED>(P, U, mask, Mod, v, 1, nb[c]));
+      }
+      T out[4];
+      recon1d<T>(W, B, d, out);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) G[(long long)(v * 4 + p) * P.gplane + i] = out[p];
+      if (!FLAGGED) {
+        if (v == 0) {
+#pragma unroll
+          for (int p = 0; p < 4; ++p) vals0[p] = out[p];
+          if (NV == 1) { pl = scalar_velocity(P, out[0], 0); pr = scalar_velocity(P, out[3], 0); }
+        } else if (v == 1) {
+          pl = out[0] / vals0[0];
+          pr = out[3] / vals0[3];
+        }
+      }
+    }
+    if (!FLAGGED) {
+      T nrm = T(0);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) nrm = tmax(nrm, tabs(vals0[p]));
+      aux[0 * P.gplane + i] = pl;
+      aux[1 * P.gplane + i] = pr;
+      aux[2 * P.gplane + i] = nrm;
+    }
+  }
+}
+
+template <typename T, int NV>
+__global__ void __launch_bounds__(RB) flag1d_kernel(Prob P, Weights<T> W, const double* __restrict__ U,
+                                                   const T* __restrict__ G, const T* __restrict__ aux,
+                                                   uint8_t* __restrict__ mask, double* __restrict__ Mod,
+                                                   int* __restrict__ list, int* __restrict__ count,
+                                                   double* __restrict__ aleph) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < P.nx;
+  bool flag = false;
+  Img L{0, 0, 1, 1}, R{0, 0, 1, 1};
+  if (valid) {
+    L = image(P, i - 1, 0);
+    R = image(P, i + 1, 0);
+    if (P.indicator == IND_ALL) {
+      flag = true;
+    } else if (P.indicator == IND_KXRCF) {
+      // face velocities: average of both sides' velocities at the face
+      const T vl = T(0.5) * (aux[(L.sx < 0 ? 0 : 1) * P.gplane + L.i] + aux[0 * P.gplane + i]);
+      const T vr = T(0.5) * (aux[1 * P.gplane + i] + aux[(R.sx < 0 ? 1 : 0) * P.gplane + R.i]);
+      const T jl = G[0 * P.gplane + i] - G[(long long)mpt1(L, 3) * P.gplane + L.i];
+      const T jr = G[3 * P.gplane + i] - G[(long long)mpt1(R, 0) * P.gplane + R.i];
+      const T s = jl * (vl > T(KX_VDEAD) ? T(1) : T(0)) + jr * (-vr > T(KX_VDEAD) ? T(1) : T(0));
+      const T nrm = aux[2 * P.gplane + i];
+      const T a = nrm == T(0) ? T(0) : tabs(s) / (W.h2 * nrm);
+      if (aleph) aleph[i] = double(a);
+      flag = a > T(1);
+    }
+  }
+  const unsigned act = __ballot_sync(0xffffffffu, flag);
+  if (act) {
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(act) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(act));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (flag) list[base + __popc(act & ((1u << lane) - 1u))] = i;
+  }
+  if (!valid) return;
+  mask[i] = flag ? 1 : 0;
+  if (!flag) return;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const double uL = U[sidx(P, v, 0, L.i, 0)], uR = U[sidx(P, v, 0, R.i, 0)];
+    const double vL = L.sx * U[sidx(P, v, 1, L.i, 0)], vR = R.sx * U[sidx(P, v, 1, R.i, 0)];
+    Mod[(long long)v * P.plane + i] = MOD_WU * (uR - uL) + MOD_WV * (vL + vR);
+  }
+}
+
+struct Rk1 {
+  const double* Uin; const double* Un; double* Uout;
+  const uint8_t* mask; const double* Mod; const uint8_t* maskN; const double* ModN;
+  double dt, cA, cB;
+  double* Lout; double* Umod;
+  unsigned* status;
+};
+
+template <typename T, int NV>
+__device__ __forceinline__ void gl1(const Prob& P, const T* __restrict__ G, const Img& m, int k, T (&u)[NV]) {
+  const int p = mpt1(m, k);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) u[v] = G[(long long)(v * 4 + p) * P.gplane + m.i];
+}
+
+template <typename T, int NV>
+__global__ void __launch_bounds__(RB) update1d_kernel(Prob P, const T* __restrict__ G, Rk1 S) {
+  __shared__ T fx[RB + 1][NV];
+  const int t = threadIdx.x;
+  const int i0 = blockIdx.x * RB;
+  const int i = i0 + t;
+  const bool live = i < P.nx;
+  const Img self{i, 0, 1, 1};
+  // fx[c] is the face left of cell i0 + c; one call site computes every face so
+  // that faces shared by two blocks get bitwise the same flux.
+  for (int c = t; c <= RB; c += RB) {
+    const int il = i0 + c - 1;
+    if (il >= P.nx) continue;
+    T uL[NV], uR[NV];
+    gl1<T, NV>(P, G, image(P, il, 0), 3, uL);
+    gl1<T, NV>(P, G, image(P, il + 1, 0), 0, uR);
+    num_flux<T, NV>(P, uL, uR, 0, fx[c]);
+  }
+  __syncthreads();
+  if (!live) return;
+  T F[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) F[v] = T(0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {     // eq. (F)
+    T u[NV], f[NV];
+    gl1<T, NV>(P, G, self, k, u);
+    phys_flux<T, NV>(P, u, 0, f);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] += gl_w<T>(k) * f[v];
+  }
+  const double idx = 1.0 / P.dx;
+  const T tidx = T(idx);
+  const bool fk = S.mask[i] != 0;
+  const bool fn = S.maskN && S.maskN[i] != 0;
+  double newavg[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const T fp = fx[t + 1][v], fm = fx[t][v];
+    double L[2];
+    L[0] = -((double)fp - (double)fm) * idx;
+    L[1] = (double)(-(fp + fm) * T(0.5) * tidx + F[v] * tidx);
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const long long si = (long long)(v * 2 + m) * P.plane + i;
+      const double uin = (m == 1 && fk) ? S.Mod[(long long)v * P.plane + i] : S.Uin[si];
+      if (S.Lout) {
+        S.Lout[si] = L[m];
+        if (S.Umod) S.Umod[si] = uin;
+        continue;
+      }
+      const double un = (m == 1 && fn) ? S.ModN[(long long)v * P.plane + i] : S.Un[si];
+      const double r = S.cA * un + S.cB * (uin + S.dt * L[m]);
+      S.Uout[si] = r;
+      if (m == 0) newavg[v] = r;
+      if (!isfinite(r)) atomicOr(S.status, ST_NONFINITE);
+    }
+  }
+  if (!S.Lout && NV == 3) {
+    const double rho = newavg[0];
+    const double p = (P.gamma - 1.0) * (newavg[2] - 0.5 * newavg[1] * newavg[1] / rho);
+    if (!(rho > 0.0) || !(p > 0.0)) atomicOr(S.status, ST_NONPOSITIVE);
+  }
+}
+
+template <typename T, int NV>
+void stage_t(const Prob& P, const Weights<T>& W, const Beta1<T>& Bt, const Bufs& B, const StageCall& S, cudaStream_t st) {
+  int* cnt = B.count + S.stage;
+  cudaMemsetAsync(cnt, 0, sizeof(int), st);
+  const int blocks = (P.nx + RB - 1) / RB;
+  rec1d_kernel<T, NV, false><<<blocks, RB, 0, st>>>(P, W, Bt, S.Uin, nullptr, nullptr, nullptr, nullptr, (T*)B.G,
+                                                    (T*)B.aux);
+  flag1d_kernel<T, NV><<<blocks, RB, 0, st>>>(P, W, S.Uin, (const T*)B.G, (const T*)B.aux, S.mask, S.Mod, B.list, cnt,
+                                              S.aleph);
+  if (P.indicator != IND_NONE)
+    rec1d_kernel<T, NV, true><<<blocks, RB, 0, st>>>(P, W, Bt, S.Uin, S.mask, S.Mod, B.list, cnt, (T*)B.G, nullptr);
+  Rk1 r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status};
+  update1d_kernel<T, NV><<<blocks, RB, 0, st>>>(P, (const T*)B.G, r);
+}
+
+}  // namespace
+
+void run_stage_1d(const Prob& P, const HostTabs& T, int fp32, const Bufs& B, const StageCall& S, cudaStream_t st) {
+  if (P.nvar == 3) {
+    if (fp32) stage_t<float, 3>(P, T.wf, T.b1f, B, S, st);
+    else stage_t<double, 3>(P, T.wd, T.b1d, B, S, st);
+  } else {
+    if (fp32) stage_t<float, 1>(P, T.wf, T.b1f, B, S, st);
+    else stage_t<double, 1>(P, T.wd, T.b1d, B, S, st);
+  }
+}
+
+}  // namespace hw

@@ -1,0 +1,395 @@
+// C ABI of the HWENO library: handle, device buffers, stage sequencing.
+// See include/hweno.h for the contract of every entry point.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+
+#define HWT_WITH_INDICATOR_ROWS
+#include "hweno_internal.h"
+#include "hweno.h"
+
+using hw::Prob;
+
+struct hweno_s {
+  hweno_grid g{};
+  hweno_bc bc{};
+  double gamma = 1.4;
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  Prob P{};
+  hw::HostTabs T{};
+  int fp32 = 0;
+  double* U[3] = {nullptr, nullptr, nullptr};
+  int cur = 0, prev = 0;
+  bool have_state = false, stepped = false;
+  hw::Bufs B{};
+  double* ModN = nullptr;        // first-stage modified first moments (kept for stages 2, 3)
+  double* ModK = nullptr;        // modified first moments of the current stage
+  uint8_t* mask3 = nullptr;      // [3][ny][nx] flags of the last step
+  double* red_part = nullptr;    // reduction partials
+  double* red_out = nullptr;     // reduction results (device)
+  double* host_buf = nullptr;    // pinned: reduction results + status
+  std::string err;
+};
+
+namespace {
+
+constexpr int VERSION = 100;
+
+hweno_status fail(hweno_t h, hweno_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+#define CK(h, call)                                                                              \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) return fail(h, HWENO_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t ncell(const hweno_s* h) { return (size_t)h->P.nx * (size_t)h->P.ny; }
+size_t nstate(const hweno_s* h) { return (size_t)h->P.nvar * h->P.nmom * ncell(h); }
+
+// Linear weights of eq. (linear-weight) and the smoothness-indicator rows of
+// eq. (beta) / (2D-beta) for p_l = (S_l q_l - S_{l-1} q_{l-1}) / g_l.
+void build_tables(hweno_s* h) {
+  const double* g = h->g.gamma_bar;
+  long double S[5] = {0, 0, 0, 0, 0};
+  for (int l = 1; l <= 4; ++l) S[l] = S[l - 1] + g[l - 1];
+  auto& wd = h->T.wd;
+  auto& wf = h->T.wf;
+  for (int l = 1; l <= 4; ++l) {
+    wd.gam[l - 1] = (double)(g[l - 1] / S[4]);
+    wd.sg[l - 1] = (double)(S[l] / g[l - 1]);
+    wd.s1g[l - 1] = (double)(S[l - 1] / g[l - 1]);
+    wf.gam[l - 1] = (float)wd.gam[l - 1];
+    wf.sg[l - 1] = (float)wd.sg[l - 1];
+    wf.s1g[l - 1] = (float)wd.s1g[l - 1];
+  }
+  wd.eps = 1e-10;
+  wf.eps = 1e-10f;
+  wd.h2 = h->P.dx * h->P.dx;       // h^{(l+1)/3}, l = 5
+  wf.h2 = (float)wd.h2;
+  auto coef = [&](int l, long double& a, long double& b) {
+    if (h->g.beta_of_q) { a = 1.0L; b = 0.0L; return; }
+    a = S[l] / g[l - 1];
+    b = -S[l - 1] / g[l - 1];
+  };
+  long double a, b;
+  if (h->P.ny == 1 && h->g.dim == 1) {
+    coef(2, a, b);   // q_1 is constant: no derivative contribution
+    for (int r = 0; r < 2; ++r) for (int c = 0; c < 3; ++c) {
+      const long double v = a * hwt::D1_RC2_2[r][c];
+      h->T.b1d.B2[r][c] = (double)v; h->T.b1f.B2[r][c] = (float)v;
+    }
+    coef(3, a, b);
+    for (int r = 0; r < 3; ++r) for (int c = 0; c < 4; ++c) {
+      const int k = hwt::D1_I3[c];
+      const long double v = a * hwt::D1_RC3_3[r][k] + b * hwt::D1_RC3_2[r][k];
+      h->T.b1d.B3[r][c] = (double)v; h->T.b1f.B3[r][c] = (float)v;
+    }
+    coef(4, a, b);
+    for (int r = 0; r < 5; ++r) for (int c = 0; c < 6; ++c) {
+      const long double v = a * hwt::D1_RC4_4[r][c] + b * hwt::D1_RC4_3[r][c];
+      h->T.b1d.B4[r][c] = (double)v; h->T.b1f.B4[r][c] = (float)v;
+    }
+  } else {
+    coef(2, a, b);
+    for (int r = 0; r < 5; ++r) for (int c = 0; c < 9; ++c) {
+      const long double v = a * hwt::D2_RC2_2[r][c];
+      h->T.b2d.B2[r][c] = (double)v; h->T.b2f.B2[r][c] = (float)v;
+    }
+    coef(3, a, b);
+    for (int r = 0; r < 9; ++r) for (int c = 0; c < 11; ++c) {
+      const int k = hwt::D2_I3[c];
+      const long double v = a * hwt::D2_RC3_3[r][k] + b * hwt::D2_RC3_2[r][k];
+      h->T.b2d.B3[r][c] = (double)v; h->T.b2f.B3[r][c] = (float)v;
+    }
+    coef(4, a, b);
+    for (int r = 0; r < 20; ++r) for (int c = 0; c < 23; ++c) {
+      const long double v = a * hwt::D2_RC4_4[r][c] + b * hwt::D2_RC4_3[r][c];
+      h->T.b2d.B4[r][c] = (double)v; h->T.b2f.B4[r][c] = (float)v;
+    }
+  }
+}
+
+hweno_status validate(const hweno_grid* g, const hweno_bc* bc, double gamma, std::string& why) {
+  if (!g || !bc) { why = "grid and bc must not be NULL"; return HWENO_EINVAL; }
+  if (g->dim != 1 && g->dim != 2) { why = "dim must be 1 or 2"; return HWENO_EINVAL; }
+  if (g->nx < 4 || (g->dim == 2 && g->ny < 4)) { why = "need at least 4 cells per direction"; return HWENO_EINVAL; }
+  if ((long long)g->nx * (g->dim == 2 ? g->ny : 1) > (1LL << 31) - 1) { why = "too many cells"; return HWENO_EINVAL; }
+  if (!(g->x1 > g->x0) || (g->dim == 2 && !(g->y1 > g->y0)) || !isfinite(g->x1 - g->x0)) {
+    why = "empty or non-finite domain"; return HWENO_EINVAL;
+  }
+  if (g->eq < 0 || g->eq > 2) { why = "eq must be advection, burgers or euler"; return HWENO_EINVAL; }
+  if (g->precision != 0 && g->precision != 1) { why = "precision must be 0 (fp64) or 1 (fp32 bulk)"; return HWENO_EINVAL; }
+  if (g->indicator < 0 || g->indicator > 2) { why = "indicator must be none, kxrcf or all"; return HWENO_EINVAL; }
+  for (int l = 0; l < 4; ++l)
+    if (!(g->gamma_bar[l] > 0.0) || !isfinite(g->gamma_bar[l])) { why = "gamma_bar must be positive"; return HWENO_EINVAL; }
+  const int k[4] = {bc->xlo, bc->xhi, bc->ylo, bc->yhi};
+  for (int s = 0; s < (g->dim == 2 ? 4 : 2); ++s)
+    if (k[s] != HWENO_BC_PERIODIC && k[s] != HWENO_BC_TRANSMISSIVE) { why = "unknown boundary kind"; return HWENO_EINVAL; }
+  if ((bc->xlo == HWENO_BC_PERIODIC) != (bc->xhi == HWENO_BC_PERIODIC) ||
+      (g->dim == 2 && (bc->ylo == HWENO_BC_PERIODIC) != (bc->yhi == HWENO_BC_PERIODIC))) {
+    why = "periodic sides must come in pairs"; return HWENO_EINVAL;
+  }
+  if (g->dim == 2) {
+    const double dx = (g->x1 - g->x0) / g->nx, dy = (g->y1 - g->y0) / g->ny;
+    if (fabs(dx - dy) > 1e-12 * dx) { why = "2D cells must be square (dx == dy)"; return HWENO_EINVAL; }
+  }
+  if (g->eq == HWENO_EULER && !(gamma > 1.0)) { why = "gamma must exceed 1"; return HWENO_EINVAL; }
+  if (!isfinite(g->adv_a) || !isfinite(g->adv_b)) { why = "advection speeds must be finite"; return HWENO_EINVAL; }
+  return HWENO_OK;
+}
+
+void free_all(hweno_s* h) {
+  for (int k = 0; k < 3; ++k) cudaFree(h->U[k]);
+  cudaFree(h->B.G);
+  cudaFree(h->B.aux);
+  cudaFree(h->B.list);
+  cudaFree(h->B.count);
+  cudaFree(h->B.status);
+  cudaFree(h->ModN);
+  cudaFree(h->ModK);
+  cudaFree(h->mask3);
+  cudaFree(h->red_part);
+  cudaFree(h->red_out);
+  if (h->host_buf) cudaFreeHost(h->host_buf);
+}
+
+// Read the status word; on a non-physical step roll the state back.
+hweno_status check_status(hweno_t h) {
+  CK(h, cudaMemcpyAsync(h->host_buf + 8, h->B.status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  unsigned st;
+  memcpy(&st, h->host_buf + 8, sizeof st);
+  if (st != 0) {
+    CK(h, cudaMemsetAsync(h->B.status, 0, sizeof(unsigned), h->stream));
+    if (h->stepped) h->cur = h->prev;
+    h->stepped = false;
+    char buf[160];
+    snprintf(buf, sizeof buf, "last step produced a non-physical state (status 0x%x: %s%s); rolled back", st,
+             (st & hw::ST_NONFINITE) ? "non-finite " : "", (st & hw::ST_NONPOSITIVE) ? "rho<=0 or p<=0" : "");
+    return fail(h, HWENO_ENONPHYSICAL, buf);
+  }
+  return HWENO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hweno_version(void) { return VERSION; }
+
+const char* hweno_last_error(hweno_t h) { return h ? h->err.c_str() : "null handle"; }
+
+hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gamma, hweno_t* out) {
+  if (!out) return HWENO_EINVAL;
+  *out = nullptr;
+  std::string why;
+  if (validate(grid, bc, gamma, why) != HWENO_OK) {
+    fprintf(stderr, "hweno_create: %s\n", why.c_str());
+    return HWENO_EINVAL;
+  }
+  hweno_s* h = new hweno_s();
+  h->g = *grid;
+  h->bc = *bc;
+  h->gamma = gamma;
+  if (grid->dim == 1) { h->g.ny = 1; h->g.y0 = 0.0; h->g.y1 = 1.0; }
+  if (cudaGetDevice(&h->dev) != cudaSuccess) { delete h; return HWENO_ECUDA; }
+  Prob& P = h->P;
+  P.nx = h->g.nx;
+  P.ny = h->g.dim == 2 ? h->g.ny : 1;
+  P.pitch = (P.nx + 31) / 32 * 32;
+  P.plane = (long long)P.ny * P.pitch;
+  P.gpitch = (P.nx + 31) / 32 * 32;
+  P.gplane = (long long)P.ny * P.gpitch;
+  P.nvar = h->g.eq == HWENO_EULER ? (h->g.dim == 1 ? 3 : 4) : 1;
+  P.nmom = h->g.dim == 1 ? 2 : 3;
+  P.eq = h->g.eq;
+  P.indicator = h->g.indicator;
+  P.bc[0] = bc->xlo; P.bc[1] = bc->xhi;
+  P.bc[2] = h->g.dim == 2 ? bc->ylo : HWENO_BC_PERIODIC;
+  P.bc[3] = h->g.dim == 2 ? bc->yhi : HWENO_BC_PERIODIC;
+  P.dx = (h->g.x1 - h->g.x0) / P.nx;
+  P.dy = h->g.dim == 2 ? (h->g.y1 - h->g.y0) / P.ny : 1.0;
+  P.gamma = gamma;
+  P.adv_a = h->g.adv_a;
+  P.adv_b = h->g.adv_b;
+  h->fp32 = h->g.precision;
+  build_tables(h);
+
+  const size_t npt = h->g.dim == 1 ? 4 : 16;
+  const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
+  const size_t sbytes = (size_t)P.nvar * P.nmom * P.plane * sizeof(double);
+  const size_t mbytes = (size_t)P.nvar * (P.nmom - 1) * P.plane * sizeof(double);
+  const size_t nc = (size_t)P.nx * P.ny;
+  bool ok = true;
+  for (int k = 0; k < 3; ++k) ok = ok && cudaMalloc(&h->U[k], sbytes) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->B.G, (size_t)P.nvar * npt * P.gplane * esz) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->B.aux, 5 * (size_t)P.gplane * esz) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->B.list, nc * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->B.count, 4 * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->B.status, sizeof(unsigned)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->ModN, mbytes) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->ModK, mbytes) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->mask3, 3 * nc) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->red_part, hw::reduce_partials_len(P) * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->red_out, 8 * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&h->host_buf, 16 * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_all(h);
+    delete h;
+    fprintf(stderr, "hweno_create: device allocation failed\n");
+    return HWENO_ENOMEM;
+  }
+  cudaMemset(h->B.status, 0, sizeof(unsigned));
+  cudaMemset(h->mask3, 0, 3 * nc);
+  cudaMemset(h->B.count, 0, 4 * sizeof(int));
+  for (int k = 0; k < 3; ++k) cudaMemset(h->U[k], 0, sbytes);
+  if (cudaDeviceSynchronize() != cudaSuccess) { free_all(h); delete h; return HWENO_ECUDA; }
+  *out = h;
+  return HWENO_OK;
+}
+
+void hweno_destroy(hweno_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+}
+
+hweno_status hweno_set_stream(hweno_t h, void* s) {
+  if (!h) return HWENO_EINVAL;
+  h->stream = (cudaStream_t)s;
+  return HWENO_OK;
+}
+
+hweno_status hweno_set_moments(hweno_t h, const double* m, size_t count, int on_device) {
+  if (!h) return HWENO_EINVAL;
+  if (!m || count != nstate(h)) return fail(h, HWENO_EINVAL, "set_moments: count must be nvar*nmom*ny*nx");
+  const size_t rows = (size_t)h->P.nvar * h->P.nmom * h->P.ny;
+  CK(h, cudaMemcpy2DAsync(h->U[h->cur], h->P.pitch * sizeof(double), m, h->P.nx * sizeof(double),
+                          h->P.nx * sizeof(double), rows, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                          h->stream));
+  CK(h, cudaMemsetAsync(h->B.status, 0, sizeof(unsigned), h->stream));
+  h->have_state = true;
+  h->stepped = false;
+  if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
+  return HWENO_OK;
+}
+
+hweno_status hweno_get_moments(hweno_t h, double* m, size_t count, int on_device) {
+  if (!h) return HWENO_EINVAL;
+  if (!m || count != nstate(h)) return fail(h, HWENO_EINVAL, "get_moments: count must be nvar*nmom*ny*nx");
+  if (!h->have_state) return fail(h, HWENO_ESTATE, "get_moments: no moments set");
+  if (!on_device) {
+    const hweno_status s = check_status(h);
+    if (s != HWENO_OK) return s;
+  }
+  const size_t rows = (size_t)h->P.nvar * h->P.nmom * h->P.ny;
+  CK(h, cudaMemcpy2DAsync(m, h->P.nx * sizeof(double), h->U[h->cur], h->P.pitch * sizeof(double),
+                          h->P.nx * sizeof(double), rows, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                          h->stream));
+  if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
+  return HWENO_OK;
+}
+
+hweno_status hweno_step(hweno_t h, double dt) {
+  if (!h) return HWENO_EINVAL;
+  if (!h->have_state) return fail(h, HWENO_ESTATE, "step: no moments set");
+  if (!(dt >= 0.0) || !isfinite(dt)) return fail(h, HWENO_EINVAL, "step: dt must be finite and >= 0");
+  const int a = h->cur, b = (h->cur + 1) % 3, c = (h->cur + 2) % 3;
+  const size_t nc = ncell(h);
+  auto run = [&](const hw::StageCall& S) {
+    if (h->g.dim == 1) hw::run_stage_1d(h->P, h->T, h->fp32, h->B, S, h->stream);
+    else hw::run_stage_2d(h->P, h->T, h->fp32, h->B, S, h->stream);
+  };
+  hw::StageCall S{};
+  // U^(1) = U^n' + dt L(U^n')
+  S.stage = 0; S.Uin = h->U[a]; S.Un = h->U[a]; S.Uout = h->U[b]; S.dt = dt; S.cA = 0.0; S.cB = 1.0;
+  S.mask = h->mask3; S.Mod = h->ModN; S.maskN = nullptr; S.ModN = nullptr;
+  run(S);
+  // U^(2) = 3/4 U^n' + 1/4 (U^(1)' + dt L(U^(1)'))
+  S.stage = 1; S.Uin = h->U[b]; S.Un = h->U[a]; S.Uout = h->U[c]; S.cA = 0.75; S.cB = 0.25;
+  S.mask = h->mask3 + nc; S.Mod = h->ModK; S.maskN = h->mask3; S.ModN = h->ModN;
+  run(S);
+  // U^{n+1} = 1/3 U^n' + 2/3 (U^(2)' + dt L(U^(2)'))
+  S.stage = 2; S.Uin = h->U[c]; S.Un = h->U[a]; S.Uout = h->U[b]; S.cA = 1.0 / 3.0; S.cB = 2.0 / 3.0;
+  S.mask = h->mask3 + 2 * nc; S.Mod = h->ModK;
+  run(S);
+  CK(h, cudaGetLastError());
+  h->prev = a;
+  h->cur = b;
+  h->stepped = true;
+  return HWENO_OK;
+}
+
+hweno_status hweno_sync(hweno_t h) {
+  if (!h) return HWENO_EINVAL;
+  return check_status(h);
+}
+
+hweno_status hweno_max_dt(hweno_t h, double cfl, double* dt_out) {
+  if (!h || !dt_out) return HWENO_EINVAL;
+  if (!h->have_state) return fail(h, HWENO_ESTATE, "max_dt: no moments set");
+  if (!(cfl > 0.0)) return fail(h, HWENO_EINVAL, "max_dt: cfl must be positive");
+  hweno_status s = check_status(h);
+  if (s != HWENO_OK) return s;
+  hw::run_wavespeed(h->P, h->U[h->cur], h->red_part, h->red_out, h->stream);
+  CK(h, cudaMemcpyAsync(h->host_buf, h->red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  const double ax = h->host_buf[0], ay = h->host_buf[1];
+  if (!isfinite(ax) || !isfinite(ay)) return fail(h, HWENO_ENONPHYSICAL, "max_dt: non-physical cell average");
+  double dt;
+  if (h->g.dim == 1) dt = ax > 0.0 ? cfl * h->P.dx / ax : INFINITY;
+  else {
+    const double r = ax / h->P.dx + ay / h->P.dy;
+    dt = r > 0.0 ? cfl / r : INFINITY;
+  }
+  *dt_out = dt;
+  return HWENO_OK;
+}
+
+hweno_status hweno_troubled_mask(hweno_t h, unsigned char* mask, size_t count) {
+  if (!h) return HWENO_EINVAL;
+  if (!mask || count != 3 * ncell(h)) return fail(h, HWENO_EINVAL, "troubled_mask: count must be 3*ny*nx");
+  CK(h, cudaMemcpyAsync(mask, h->mask3, count, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return HWENO_OK;
+}
+
+hweno_status hweno_totals(hweno_t h, double* sums) {
+  if (!h || !sums) return HWENO_EINVAL;
+  if (!h->have_state) return fail(h, HWENO_ESTATE, "totals: no moments set");
+  hweno_status s = check_status(h);
+  if (s != HWENO_OK) return s;
+  hw::run_totals(h->P, h->U[h->cur], h->red_part, h->red_out, h->stream);
+  CK(h, cudaMemcpyAsync(h->host_buf, h->red_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  const double area = h->P.dx * h->P.dy;
+  for (int v = 0; v < h->P.nvar; ++v) sums[v] = h->host_buf[v] * area;
+  return HWENO_OK;
+}
+
+hweno_status hweno_rhs(hweno_t h, const double* U, double* Umod, double* L, unsigned char* mask, double* aleph) {
+  if (!h) return HWENO_EINVAL;
+  if (!U || !Umod || !L || !mask) return fail(h, HWENO_EINVAL, "rhs: U, Umod, L and mask are required");
+  Prob P = h->P;           // caller arrays are unpadded
+  P.pitch = P.nx;
+  P.plane = (long long)P.ny * P.nx;
+  hw::StageCall S{};
+  S.stage = 3; S.Uin = U; S.Un = U; S.Uout = nullptr; S.dt = 0.0; S.cA = 0.0; S.cB = 1.0;
+  S.mask = mask; S.Mod = h->ModK; S.maskN = nullptr; S.ModN = nullptr;
+  S.Lout = L; S.Umod = Umod; S.aleph = aleph;
+  if (h->g.dim == 1) hw::run_stage_1d(P, h->T, h->fp32, h->B, S, h->stream);
+  else hw::run_stage_2d(P, h->T, h->fp32, h->B, S, h->stream);
+  CK(h, cudaGetLastError());
+  return HWENO_OK;
+}
+
+}  // extern "C"

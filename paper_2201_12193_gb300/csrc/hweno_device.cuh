@@ -1,0 +1,382 @@
+// Device-side building blocks of the HWENO stage kernels (sm_103a).
+//
+// Scheme: moment-based multi-resolution HWENO, Li, Shu & Qiu (arXiv 2201.12193).
+// Section and equation names below are the paper's.
+//
+// Precision: T = double (FP64 path) or T = float (FP32-bulk path).  The state,
+// the Runge-Kutta combination and the conservation sums stay FP64 in both.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define HWT_VALUE_QUAL static __constant__
+#include "hweno_tables.h"
+
+namespace hw {
+
+constexpr int EQ_ADV = 0, EQ_BURGERS = 1, EQ_EULER = 2;
+constexpr int BC_PERIODIC = 0, BC_TRANSMISSIVE = 1;
+constexpr int IND_NONE = 0, IND_KXRCF = 1, IND_ALL = 2;
+
+// device status word bits
+constexpr unsigned ST_NONFINITE = 1u;     // a non-finite value in the new state
+constexpr unsigned ST_NONPOSITIVE = 2u;   // rho <= 0 or p <= 0 in a new cell average (Euler)
+
+// Problem description passed by value to every kernel.
+struct Prob {
+  int nx, ny;             // cells (ny = 1 in 1D)
+  int pitch;              // row stride of the state arrays (doubles)
+  long long plane;        // stride of one (variable, moment) plane = ny * pitch
+  int gpitch;             // row stride of the point-value / aux arrays (elements of T)
+  long long gplane;       // ny * gpitch
+  int nvar, nmom;         // conserved variables; moments per variable (2 in 1D, 3 in 2D)
+  int eq, indicator;
+  int bc[4];              // x-lo, x-hi, y-lo, y-hi
+  double dx, dy;
+  double gamma;           // ratio of specific heats
+  double adv_a, adv_b;    // linear advection speeds
+};
+
+// Linear-weight data of eq. (linear-weight) and eq. (p) for positive gbar[4]:
+// gamma_{l,4} = g_l / S_4 and p_l = (S_l q_l - S_{l-1} q_{l-1}) / g_l.
+template <typename T>
+struct Weights {
+  T gam[4];      // gamma_{l,4}
+  T sg[4];       // S_l / g_l
+  T s1g[4];      // S_{l-1} / g_l  (0 for l = 1)
+  T eps;         // 1e-10 of eqs. (w1_-LR), (non-linear-weight)
+  T h2;          // h^{(l+1)/3} with l = 5, h = dx  (eq. (KXRCF))
+};
+
+// Rows of the smoothness indicators beta_2..beta_4 for the run-time weights:
+// beta_l = sum_r (B_l[r] . d_l)^2, d_l the level's data (eq. (beta), (2D-beta)).
+template <typename T> struct Beta1 { T B2[2][3]; T B3[3][4]; T B4[5][6]; };
+template <typename T> struct Beta2 { T B2[5][9]; T B3[9][11]; T B4[20][23]; };
+
+// ---------------------------------------------------------------- tables by precision
+template <typename T> struct Tab;
+template <> struct Tab<double> {
+  static __device__ __forceinline__ double v1_2(int p, int c) { return hwt::D1_V2[p][c]; }
+  static __device__ __forceinline__ double v1_3(int p, int c) { return hwt::D1_V3[p][c]; }
+  static __device__ __forceinline__ double v1_4(int p, int c) { return hwt::D1_V4[p][c]; }
+  static __device__ __forceinline__ double v2_2(int p, int c) { return hwt::D2_V2[p][c]; }
+  static __device__ __forceinline__ double v2_3(int p, int c) { return hwt::D2_V3[p][c]; }
+  static __device__ __forceinline__ double v2_4(int p, int c) { return hwt::D2_V4[p][c]; }
+};
+template <> struct Tab<float> {
+  static __device__ __forceinline__ float v1_2(int p, int c) { return hwt::D1_V2f[p][c]; }
+  static __device__ __forceinline__ float v1_3(int p, int c) { return hwt::D1_V3f[p][c]; }
+  static __device__ __forceinline__ float v1_4(int p, int c) { return hwt::D1_V4f[p][c]; }
+  static __device__ __forceinline__ float v2_2(int p, int c) { return hwt::D2_V2f[p][c]; }
+  static __device__ __forceinline__ float v2_3(int p, int c) { return hwt::D2_V3f[p][c]; }
+  static __device__ __forceinline__ float v2_4(int p, int c) { return hwt::D2_V4f[p][c]; }
+};
+
+// Gauss-Lobatto nodes and weights of eq. (F)
+template <typename T> __device__ __forceinline__ T gl_w(int k) { return (k == 0 || k == 3) ? T(1.0 / 12.0) : T(5.0 / 12.0); }
+template <typename T> __device__ __forceinline__ T gl_x(int k) {
+  return k == 0 ? T(-0.5) : k == 1 ? T(-0.22360679774997896964) : k == 2 ? T(0.22360679774997896964) : T(0.5);
+}
+
+template <typename T> __device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
+template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+
+// ---------------------------------------------------------------- boundary images
+// A ghost cell is the image of an interior cell: periodic wrap, or (transmissive)
+// the mirror about the boundary face, under which the mirrored direction's first
+// moment changes sign and point values are reversed along that direction.
+struct Img { int i, j, sx, sy; };
+
+__device__ __forceinline__ int wrap(int i, int n) { i %= n; return i < 0 ? i + n : i; }
+
+__device__ __forceinline__ Img image(const Prob& P, int i, int j) {
+  Img r{i, j, 1, 1};
+  if (i < 0) { if (P.bc[0] == BC_PERIODIC) r.i = wrap(i, P.nx); else { r.i = -1 - i; r.sx = -1; } }
+  else if (i >= P.nx) { if (P.bc[1] == BC_PERIODIC) r.i = wrap(i, P.nx); else { r.i = 2 * P.nx - 1 - i; r.sx = -1; } }
+  if (j < 0) { if (P.bc[2] == BC_PERIODIC) r.j = wrap(j, P.ny); else { r.j = -1 - j; r.sy = -1; } }
+  else if (j >= P.ny) { if (P.bc[3] == BC_PERIODIC) r.j = wrap(j, P.ny); else { r.j = 2 * P.ny - 1 - j; r.sy = -1; } }
+  return r;
+}
+
+__device__ __forceinline__ long long sidx(const Prob& P, int var, int mom, int i, int j) {
+  return (long long)(var * P.nmom + mom) * P.plane + (long long)j * P.pitch + i;
+}
+
+// ---------------------------------------------------------------- physics
+// Physical flux of eq. (1D-Euler) / (2D-Euler) or of the scalar laws in
+// direction dir (0 = x, 1 = y); NV = 1 (scalar), 3 (1D Euler), 4 (2D Euler).
+template <typename T, int NV>
+__device__ __forceinline__ void phys_flux(const Prob& P, const T* u, int dir, T* f) {
+  if constexpr (NV == 1) {
+    if (P.eq == EQ_ADV) f[0] = T(dir == 0 ? P.adv_a : P.adv_b) * u[0];
+    else f[0] = T(0.5) * u[0] * u[0];
+  } else if constexpr (NV == 3) {
+    const T g = T(P.gamma);
+    const T inv = T(1) / u[0], mu = u[1] * inv, E = u[2];
+    const T p = (g - T(1)) * (E - T(0.5) * u[1] * mu);
+    f[0] = u[1]; f[1] = u[1] * mu + p; f[2] = mu * (E + p);
+  } else {
+    const T g = T(P.gamma);
+    const T inv = T(1) / u[0], mu = u[1] * inv, nu = u[2] * inv, E = u[3];
+    const T p = (g - T(1)) * (E - T(0.5) * (u[1] * mu + u[2] * nu));
+    if (dir == 0) { f[0] = u[1]; f[1] = u[1] * mu + p; f[2] = u[1] * nu; f[3] = mu * (E + p); }
+    else          { f[0] = u[2]; f[1] = u[2] * mu; f[2] = u[2] * nu + p; f[3] = nu * (E + p); }
+  }
+}
+
+// Velocity seen by the KXRCF indicator for scalar laws (Remarks 2, 3): f'(u), g'(u).
+template <typename T>
+__device__ __forceinline__ T scalar_velocity(const Prob& P, T u, int dir) {
+  if (P.eq == EQ_ADV) return T(dir == 0 ? P.adv_a : P.adv_b);
+  return u;
+}
+
+// HLLC flux, eqs. (f_HLLC), (COEF), (uLR_), as a rotated 1D solver in direction
+// dir (the tangential velocity is carried through the star state).
+// Branch order: 0 <= sL -> fL; 0 <= s* -> f*L; 0 <= sR -> f*R; else fR.
+template <typename T, int NV>
+__device__ __forceinline__ void hllc(const Prob& P, const T* uL, const T* uR, int dir, T* F) {
+  constexpr bool two = NV == 4;
+  const T g = T(P.gamma);
+  const int in = 1 + dir, it = 2 - dir;
+  constexpr int iE = NV - 1;
+  const T rL = uL[0], rR = uR[0];
+  const T iL = T(1) / rL, iR = T(1) / rR;
+  const T mL = uL[in] * iL, mR = uR[in] * iR;
+  const T tL = two ? uL[it] * iL : T(0), tR = two ? uR[it] * iR : T(0);
+  const T EL = uL[iE], ER = uR[iE];
+  const T pL = (g - T(1)) * (EL - T(0.5) * rL * (mL * mL + tL * tL));
+  const T pR = (g - T(1)) * (ER - T(0.5) * rR * (mR * mR + tR * tR));
+  const T cL = sqrt(g * pL * iL), cR = sqrt(g * pR * iR);
+  const T rs = T(0.5) * (rL + rR), cs = T(0.5) * (cL + cR);
+  const T crs = cs * rs;
+  const T ps = T(0.5) * (pL + pR + (mL - mR) * crs);
+  const T ss = T(0.5) * (mL + mR + (pL - pR) / crs);
+  const T k = (g + T(1)) / (T(2) * g);
+  const T coefL = ps <= pL ? T(1) : sqrt(T(1) + k * (ps / pL - T(1)));
+  const T coefR = ps <= pR ? T(1) : sqrt(T(1) + k * (ps / pR - T(1)));
+  const T sL = mL - cL * coefL, sR = mR + cR * coefR;
+  const bool useL = T(0) <= sL || T(0) <= ss;     // left physical or left star flux
+  const T rK = useL ? rL : rR, mK = useL ? mL : mR, tK = useL ? tL : tR;
+  const T EK = useL ? EL : ER, pK = useL ? pL : pR, sK = useL ? sL : sR;
+  // physical normal flux of the chosen side
+  T fK[NV], uK[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) uK[v] = useL ? uL[v] : uR[v];
+  fK[0] = rK * mK;
+  fK[1] = dir == 0 ? rK * mK * mK + pK : rK * mK * tK;
+  if constexpr (two) fK[2] = dir == 0 ? rK * mK * tK : rK * mK * mK + pK;
+  fK[iE] = mK * (EK + pK);
+  if (T(0) <= sL || !(T(0) <= sR || T(0) <= ss)) {   // supersonic: fL or fR
+#pragma unroll
+    for (int v = 0; v < NV; ++v) F[v] = fK[v];
+    return;
+  }
+  const T fac = rK * (sK - mK) / (sK - ss);
+  T us[NV];
+  us[0] = fac;
+  us[in] = fac * ss;
+  if constexpr (two) us[it] = fac * tK;
+  us[iE] = fac * (EK / rK + (ss - mK) * (ss + pK / (rK * (sK - mK))));
+#pragma unroll
+  for (int v = 0; v < NV; ++v) F[v] = fK[v] + sK * (us[v] - uK[v]);
+}
+
+// Scalar laws: local Lax-Friedrichs flux with alpha = max(|f'(uL)|, |f'(uR)|).
+template <typename T>
+__device__ __forceinline__ T llf(const Prob& P, T uL, T uR, int dir) {
+  T fl, fr;
+  phys_flux<T, 1>(P, &uL, dir, &fl);
+  phys_flux<T, 1>(P, &uR, dir, &fr);
+  const T aL = tabs(scalar_velocity(P, uL, dir)), aR = tabs(scalar_velocity(P, uR, dir));
+  return T(0.5) * (fl + fr) - T(0.5) * tmax(aL, aR) * (uR - uL);
+}
+
+template <typename T, int NV>
+__device__ __forceinline__ void num_flux(const Prob& P, const T* uL, const T* uR, int dir, T* F) {
+  if constexpr (NV == 1) F[0] = llf(P, uL[0], uR[0], dir);
+  else hllc<T, NV>(P, uL, uR, dir, F);
+}
+
+// Unroll factor of the long table loops: FP64 issue is the bottleneck, so the
+// FP64 path keeps loops rolled (indexed constant loads are hidden behind the
+// slow FP64 pipe) and saves registers; FP32 unrolls fully.
+template <typename T> struct Unroll { static constexpr int rows = 1, pts = 1; };
+template <> struct Unroll<float> { static constexpr int rows = 32, pts = 16; };
+
+// ---------------------------------------------------------------- nonlinear weights
+// WENO-Z weights of eqs. (tau4), (non-linear-weight) and the combination of
+// eq. (re-p) rewritten on q_1..q_4:  u = sum_k c_k q_k with
+// c_k = omega_k S_k/g_k - omega_{k+1} S_k/g_{k+1},  c_4 = omega_4 S_4/g_4.
+template <typename T>
+__device__ __forceinline__ void combine_weights(const Weights<T>& W, const T beta[4], T c[4]) {
+  const T tau4s = tabs(beta[3] - beta[0]) + tabs(beta[3] - beta[1]) + tabs(beta[3] - beta[2]);
+  const T tau4 = (tau4s * T(1.0 / 3.0)) * (tau4s * T(1.0 / 3.0));
+  T wb[4], ws = T(0);
+#pragma unroll
+  for (int l = 0; l < 4; ++l) { wb[l] = W.gam[l] * (T(1) + tau4 / (beta[l] + W.eps)); ws += wb[l]; }
+  const T inv = T(1) / ws;
+  T om[4];
+#pragma unroll
+  for (int l = 0; l < 4; ++l) om[l] = wb[l] * inv;
+  c[0] = om[0] * W.sg[0] - om[1] * W.s1g[1];
+  c[1] = om[1] * W.sg[1] - om[2] * W.s1g[2];
+  c[2] = om[2] * W.sg[2] - om[3] * W.s1g[3];
+  c[3] = om[3] * W.sg[3];
+}
+
+// ---------------------------------------------------------------- 1D reconstruction
+// d = (u_{i-1}, u_i, u_{i+1}, v_{i-1}, v_i, v_{i+1}) of one variable; out = the
+// four Gauss-Lobatto values of eq. (re-u).  Steps 1.1-1.3 of the 1D algorithm.
+template <typename T>
+__device__ __forceinline__ void recon1d(const Weights<T>& W, const Beta1<T>& B, const T (&d)[6], T (&out)[4]) {
+  const T d3[4] = {d[0], d[1], d[2], d[4]};
+  T beta[4];
+  {
+    T b = T(0);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) { T s = T(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) s = fma(B.B2[r][c], d[c], s);
+      b = fma(s, s, b); }
+    beta[1] = b;
+    b = T(0);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) { T s = T(0);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) s = fma(B.B3[r][c], d3[c], s);
+      b = fma(s, s, b); }
+    beta[2] = b;
+    b = T(0);
+#pragma unroll
+    for (int r = 0; r < 5; ++r) { T s = T(0);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) s = fma(B.B4[r][c], d[c], s);
+      b = fma(s, s, b); }
+    beta[3] = b;
+  }
+  // beta_1: eqs. (beta1-LR), (tau1), (w1_-LR), (w1-LR), (beta1)
+  {
+    const T dl = d[1] - d[0], dr = d[2] - d[1];
+    const T bl = dl * dl, br = dr * dr;
+    const T t1 = tabs(br - bl) * tabs(br - bl);
+    const T wl = T(0.5) * (T(1) + t1 / (bl + W.eps));
+    const T wr = T(0.5) * (T(1) + t1 / (br + W.eps));
+    const T inv = T(1) / (wl + wr);
+    const T gg = (wl * inv) * dl + (wr * inv) * dr;
+    beta[0] = gg * gg;
+  }
+  T c[4];
+  combine_weights(W, beta, c);
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    T s2 = T(0), s3 = T(0), s4 = T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) s2 = fma(Tab<T>::v1_2(p, k), d[k], s2);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s3 = fma(Tab<T>::v1_3(p, k), d3[k], s3);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) s4 = fma(Tab<T>::v1_4(p, k), d[k], s4);
+    out[p] = c[0] * d[1] + c[1] * s2 + c[2] * s3 + c[3] * s4;
+  }
+}
+
+// ---------------------------------------------------------------- 2D reconstruction
+// d = the 23 data of q_4 (u at labels 1..9, v at 1,3,4,5,6,7,9, w at
+// 1,2,3,5,7,8,9; labels of the paper's 3x3 stencil table), out[k*4+l] =
+// u_{i,j}(xi_k, eta_l) of eq. (2D-re-u).  Steps 1.1-1.3 of the 2D algorithm.
+// Square cells: beta_1 of eq. (2D-beta1) is (sum w_1k Dx_k)^2 + (sum w_1k Dy_k)^2.
+template <typename T>
+__device__ __forceinline__ void recon2d(const Weights<T>& W, const Beta2<T>& B, const T (&d)[23], T (&out)[16]) {
+  T d3[11];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) d3[c] = d[c];
+  d3[9] = d[12];
+  d3[10] = d[19];
+  T beta[4];
+  {
+    T b = T(0);
+#pragma unroll
+    for (int r = 0; r < 5; ++r) { T s = T(0);
+#pragma unroll
+      for (int c = 0; c < 9; ++c) s = fma(B.B2[r][c], d[c], s);
+      b = fma(s, s, b); }
+    beta[1] = b;
+    b = T(0);
+#pragma unroll Unroll<T>::rows
+    for (int r = 0; r < 9; ++r) { T s = T(0);
+#pragma unroll
+      for (int c = 0; c < 11; ++c) s = fma(B.B3[r][c], d3[c], s);
+      b = fma(s, s, b); }
+    beta[2] = b;
+    b = T(0);
+#pragma unroll Unroll<T>::rows
+    for (int r = 0; r < 20; ++r) { T s = T(0);
+#pragma unroll
+      for (int c = 0; c < 23; ++c) s = fma(B.B4[r][c], d[c], s);
+      b = fma(s, s, b); }
+    beta[3] = b;
+  }
+  // beta_1: eqs. (2D-q1-1234) .. (2D-beta1); tau_1 over the 6 unordered pairs
+  {
+    const T u2 = d[1], u4 = d[3], u5 = d[4], u6 = d[5], u8 = d[7];
+    const T bx[4] = {u5 - u4, u6 - u5, u6 - u5, u5 - u4};
+    const T by[4] = {u8 - u5, u8 - u5, u5 - u2, u5 - u2};
+    T b1[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) b1[k] = bx[k] * bx[k] + by[k] * by[k];
+    T ts = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int l = k + 1; l < 4; ++l) ts += tabs(b1[k] - b1[l]);
+    const T t1 = (ts * T(1.0 / 6.0)) * (ts * T(1.0 / 6.0));
+    T w[4], wsum = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { w[k] = T(0.25) * (T(1) + t1 / (b1[k] + W.eps)); wsum += w[k]; }
+    const T inv = T(1) / wsum;
+    T gx = T(0), gy = T(0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) { gx = fma(w[k] * inv, bx[k], gx); gy = fma(w[k] * inv, by[k], gy); }
+    beta[0] = gx * gx + gy * gy;
+  }
+  T c[4];
+  combine_weights(W, beta, c);
+#pragma unroll Unroll<T>::pts
+  for (int p = 0; p < 16; ++p) {
+    T s2 = T(0), s3 = T(0), s4 = T(0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) s2 = fma(Tab<T>::v2_2(p, k), d[k], s2);
+#pragma unroll
+    for (int k = 0; k < 11; ++k) s3 = fma(Tab<T>::v2_3(p, k), d3[k], s3);
+#pragma unroll
+    for (int k = 0; k < 23; ++k) s4 = fma(Tab<T>::v2_4(p, k), d[k], s4);
+    out[p] = c[0] * d[4] + c[1] * s2 + c[2] * s3 + c[3] * s4;
+  }
+}
+
+// Positions (ox, oy, kind) of the 23 data of q_4 in gather order.
+__device__ __forceinline__ void d4_slot(int c, int& kind, int& ox, int& oy) {
+  // u at labels 1..9 (bottom row first), v at 1,3,4,5,6,7,9, w at 1,2,3,5,7,8,9
+  const int vl[7] = {1, 3, 4, 5, 6, 7, 9};
+  const int wl[7] = {1, 2, 3, 5, 7, 8, 9};
+  int lbl;
+  if (c < 9) { kind = 0; lbl = c + 1; }
+  else if (c < 16) { kind = 1; lbl = vl[c - 9]; }
+  else { kind = 2; lbl = wl[c - 16]; }
+  ox = (lbl - 1) % 3 - 1;
+  oy = (lbl - 1) / 3 - 1;
+}
+
+// A face counts as inflow in KXRCF when its velocity exceeds this (absolute,
+// in the problem's velocity units): rounding noise around a fluid exactly at
+// rest must not decide the indicator.
+constexpr double KX_VDEAD = 1e-12;
+
+// Modification weights of eq. (vi) (quartic p_0 of eq. (p0)):
+// vbar_i <- -5/76 u_{i-1} + 5/76 u_{i+1} - 11/38 v_{i-1} - 11/38 v_{i+1}.
+constexpr double MOD_WU = 5.0 / 76.0;
+constexpr double MOD_WV = -11.0 / 38.0;
+
+}  // namespace hw

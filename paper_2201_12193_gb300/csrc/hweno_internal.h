@@ -1,0 +1,60 @@
+// Internal interface between the C ABI (hweno_api.cu) and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hweno_device.cuh"
+
+namespace hw {
+
+// Per-handle tables in both precisions (filled once at creation).
+struct HostTabs {
+  Weights<double> wd;
+  Weights<float> wf;
+  Beta1<double> b1d;
+  Beta1<float> b1f;
+  Beta2<double> b2d;
+  Beta2<float> b2f;
+};
+
+// Work buffers owned by a handle.
+struct Bufs {
+  void* G;            // point values [nvar][npt][ny][gpitch] in the compute precision
+  void* aux;          // KXRCF face-velocity partials and norms [5][ny][gpitch]
+  int* list;          // flagged cells of the current stage (linear index j*nx+i)
+  int* count;         // [3] flagged counts per stage
+  unsigned* status;   // ST_* bits
+};
+
+// One evaluation of the spatial operator with the troubled-cell steps and,
+// unless Lout is set, the Runge-Kutta combination
+//   Uout = cA * Un' + cB * (Uin' + dt * L(Uin'))
+// where ' marks the first moments modified in troubled cells (eq. (vi)):
+// Uin' by this stage's flags, Un' by the first stage's (maskN, ModN).
+struct StageCall {
+  int stage;               // 0, 1, 2 (selects counters)
+  const double* Uin;
+  const double* Un;        // may equal Uin (first stage)
+  double* Uout;            // RK output (ignored when Lout is set)
+  double dt, cA, cB;
+  uint8_t* mask;           // out: this stage's flags [ny*nx]
+  double* Mod;             // out: modified first moments of flagged cells [nvar][nmom-1][plane]
+  const uint8_t* maskN;    // first-stage flags (for Un'); nullptr = Un unmodified
+  const double* ModN;      // first-stage modified first moments
+  double* Lout;            // optional: write L(Uin') (state layout) instead of the RK update
+  double* Umod;            // optional (with Lout): write Uin'
+  double* aleph;           // optional: KXRCF values [ny*nx]
+};
+
+void run_stage_1d(const Prob& P, const HostTabs& T, int fp32, const Bufs& B, const StageCall& S, cudaStream_t st);
+void run_stage_2d(const Prob& P, const HostTabs& T, int fp32, const Bufs& B, const StageCall& S, cudaStream_t st);
+
+// Reductions over the cell averages (FP64): maximum wave speeds per direction
+// and totals sum(ubar) per variable.  partials needs reduce_partials_len(P)
+// doubles; out gets {ax, ay} or the nvar totals (unscaled sums).
+int reduce_partials_len(const Prob& P);
+void run_wavespeed(const Prob& P, const double* U, double* partials, double* out, cudaStream_t st);
+void run_totals(const Prob& P, const double* U, double* partials, double* out, cudaStream_t st);
+
+}  // namespace hw

@@ -1,0 +1,127 @@
+// Reductions over the cell averages (FP64): the CFL wave speeds and the
+// conservation totals.  Warp shuffles inside a block, one partial per block,
+// then a single-block pass in a fixed order (deterministic for a given grid).
+#include <math.h>
+
+#include <algorithm>
+
+#include "hweno_internal.h"
+
+namespace hw {
+namespace {
+
+constexpr int RT = 256;       // threads per block
+constexpr int MAXB = 1024;    // blocks of the first pass (partials per quantity)
+
+template <int K>
+__device__ __forceinline__ void block_reduce(double (&v)[K], bool is_max, double (*sm)[RT / 32]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double w = __shfl_down_sync(0xffffffffu, v[k], o);
+      v[k] = is_max ? fmax(v[k], w) : v[k] + w;
+    }
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sm[k][wid] = v[k];
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      double x = lane < RT / 32 ? sm[k][lane] : 0.0;   // 0 is neutral for sums and for max of speeds
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double w = __shfl_down_sync(0xffffffffu, x, o);
+        x = is_max ? fmax(x, w) : x + w;
+      }
+      v[k] = x;
+    }
+  }
+}
+
+// Largest |f'| (scalars) or |velocity| + sound speed (Euler) per direction,
+// from cell averages.  A non-physical average yields +inf (dt = 0).
+__global__ void __launch_bounds__(RT) wavespeed_kernel(Prob P, const double* __restrict__ U, double* __restrict__ part) {
+  __shared__ double sm[2][RT / 32];
+  double v[2] = {0.0, 0.0};
+  const long long n = (long long)P.nx * P.ny;
+  for (long long t = (long long)blockIdx.x * RT + threadIdx.x; t < n; t += (long long)gridDim.x * RT) {
+    const int i = (int)(t % P.nx), j = (int)(t / P.nx);
+    double sx, sy;
+    if (P.eq == EQ_ADV) { sx = fabs(P.adv_a); sy = fabs(P.adv_b); }
+    else if (P.eq == EQ_BURGERS) { sx = sy = fabs(U[sidx(P, 0, 0, i, j)]); }
+    else {
+      const double rho = U[sidx(P, 0, 0, i, j)];
+      const double mu = U[sidx(P, 1, 0, i, j)] / rho;
+      const double nu = P.nvar == 4 ? U[sidx(P, 2, 0, i, j)] / rho : 0.0;
+      const double E = U[sidx(P, P.nvar - 1, 0, i, j)];
+      const double p = (P.gamma - 1.0) * (E - 0.5 * rho * (mu * mu + nu * nu));
+      const double c = sqrt(P.gamma * p / rho);
+      sx = fabs(mu) + c;
+      sy = fabs(nu) + c;
+      if (!(rho > 0.0) || !(p > 0.0) || !isfinite(sx + sy)) sx = sy = INFINITY;
+    }
+    v[0] = fmax(v[0], sx);
+    v[1] = fmax(v[1], sy);
+  }
+  block_reduce<2>(v, true, sm);
+  if (threadIdx.x == 0) { part[blockIdx.x] = v[0]; part[MAXB + blockIdx.x] = v[1]; }
+}
+
+__global__ void __launch_bounds__(RT) totals_kernel(Prob P, const double* __restrict__ U, double* __restrict__ part) {
+  __shared__ double sm[4][RT / 32];
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  const long long n = (long long)P.nx * P.ny;
+  for (long long t = (long long)blockIdx.x * RT + threadIdx.x; t < n; t += (long long)gridDim.x * RT) {
+    const int i = (int)(t % P.nx), j = (int)(t / P.nx);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (k < P.nvar) v[k] += U[sidx(P, k, 0, i, j)];
+  }
+  block_reduce<4>(v, false, sm);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) part[k * MAXB + blockIdx.x] = v[k];
+}
+
+// Single block: reduce K rows of nb partials each into out[K].
+template <int K>
+__global__ void __launch_bounds__(RT) finish_kernel(const double* __restrict__ part, int nb, bool is_max,
+                                                    double* __restrict__ out) {
+  __shared__ double sm[K][RT / 32];
+  double v[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    v[k] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += RT) v[k] = is_max ? fmax(v[k], part[k * MAXB + b]) : v[k] + part[k * MAXB + b];
+  }
+  block_reduce<K>(v, is_max, sm);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) out[k] = v[k];
+}
+
+int first_pass_blocks(const Prob& P) {
+  const long long n = (long long)P.nx * P.ny;
+  return (int)std::min<long long>(MAXB, (n + RT - 1) / RT);
+}
+
+}  // namespace
+
+int reduce_partials_len(const Prob&) { return 4 * MAXB; }
+
+void run_wavespeed(const Prob& P, const double* U, double* partials, double* out, cudaStream_t st) {
+  const int nb = first_pass_blocks(P);
+  wavespeed_kernel<<<nb, RT, 0, st>>>(P, U, partials);
+  finish_kernel<2><<<1, RT, 0, st>>>(partials, nb, true, out);
+}
+
+void run_totals(const Prob& P, const double* U, double* partials, double* out, cudaStream_t st) {
+  const int nb = first_pass_blocks(P);
+  totals_kernel<<<nb, RT, 0, st>>>(P, U, partials);
+  finish_kernel<4><<<1, RT, 0, st>>>(partials, nb, false, out);
+}
+
+}  // namespace hw

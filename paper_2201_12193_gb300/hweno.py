@@ -1,0 +1,207 @@
+"""Thin Python binding of the C ABI in include/hweno.h (argument marshalling only).
+
+Every step of the computation runs in libhweno.so (CUDA, sm_103a).  There is no
+CPU fallback: if the library is missing or no GPU is present, the calls fail.
+Device buffers may be torch CUDA tensors; host buffers numpy arrays or CPU
+tensors.  PyTorch only provides device memory and the stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhweno.so")
+_lib = None
+
+STATUS = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "ENONPHYSICAL", -4: "ETIMEOUT", -5: "ESTATE", -6: "ENOMEM"}
+EQ = {"advection": 0, "burgers": 1, "euler": 2}
+IND = {"none": 0, "kxrcf": 1, "all": 2}
+BC = {"periodic": 0, "transmissive": 1}
+PREC = {"fp64": 0, "fp32": 1}
+
+
+class HwenoError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("eq", ctypes.c_int), ("adv_a", ctypes.c_double), ("adv_b", ctypes.c_double),
+                ("precision", ctypes.c_int), ("indicator", ctypes.c_int), ("gamma_bar", ctypes.c_double * 4),
+                ("beta_of_q", ctypes.c_int)]
+
+
+class Bc(ctypes.Structure):
+    _fields_ = [("xlo", ctypes.c_int), ("xhi", ctypes.c_int), ("ylo", ctypes.c_int), ("yhi", ctypes.c_int)]
+
+
+def lib():
+    """Load libhweno.so (fails loudly when it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is missing: run paper_2201_12193_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        H = ctypes.c_void_p
+        D = ctypes.POINTER(ctypes.c_double)
+        L.hweno_create.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Bc), ctypes.c_double, ctypes.POINTER(H)]
+        L.hweno_destroy.argtypes = [H]
+        L.hweno_destroy.restype = None
+        L.hweno_set_stream.argtypes = [H, ctypes.c_void_p]
+        L.hweno_set_moments.argtypes = [H, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+        L.hweno_get_moments.argtypes = [H, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+        L.hweno_step.argtypes = [H, ctypes.c_double]
+        L.hweno_max_dt.argtypes = [H, ctypes.c_double, D]
+        L.hweno_troubled_mask.argtypes = [H, ctypes.c_void_p, ctypes.c_size_t]
+        L.hweno_totals.argtypes = [H, D]
+        L.hweno_sync.argtypes = [H]
+        L.hweno_rhs.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.hweno_last_error.argtypes = [H]
+        L.hweno_last_error.restype = ctypes.c_char_p
+        L.hweno_version.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(x):
+    """(address, on_device, element count) of a contiguous numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data, 0, x.size
+    if not x.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return x.data_ptr(), int(x.is_cuda), x.numel()
+
+
+def _f64(x):
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64:
+            raise TypeError("moments must be float64")
+    elif x.dtype.is_floating_point and x.element_size() != 8:
+        raise TypeError("moments must be float64")
+    return x
+
+
+class Solver:
+    """One problem on the GPU; method names follow the C ABI (hweno_*)."""
+
+    def __init__(self, dim, nx, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, eq="euler", adv=(1.0, 0.0),
+                 precision="fp64", indicator="kxrcf", gamma_bar=(1.0, 10.0, 100.0, 1000.0), beta_of_q=False,
+                 bc=("transmissive",) * 4, gamma=1.4, stream=None):
+        g = Grid()
+        g.dim, g.nx, g.ny = dim, nx, (ny if dim == 2 else 1)
+        g.x0, g.x1, g.y0, g.y1 = x0, x1, y0, y1
+        g.eq = EQ[eq]
+        g.adv_a, g.adv_b = adv
+        g.precision = PREC[precision]
+        g.indicator = IND[indicator]
+        for k in range(4):
+            g.gamma_bar[k] = gamma_bar[k]
+        g.beta_of_q = int(bool(beta_of_q))
+        b = Bc(*[BC[k] for k in bc])
+        h = ctypes.c_void_p()
+        st = lib().hweno_create(ctypes.byref(g), ctypes.byref(b), float(gamma), ctypes.byref(h))
+        if st != 0:
+            raise HwenoError(st, "hweno_create failed (see stderr)")
+        self._h = h
+        self.grid = g
+        self.dim, self.nx, self.ny = dim, nx, g.ny
+        self.nvar = 1 if eq != "euler" else (3 if dim == 1 else 4)
+        self.nmom = 2 if dim == 1 else 3
+        self.shape = (self.nvar, self.nmom, self.ny, self.nx)
+        self.count = int(np.prod(self.shape))
+        if stream is not None:
+            self.set_stream(stream)
+
+    @classmethod
+    def from_problem(cls, p, **kw):
+        return cls(p.dim, p.nx, p.ny, p.x0, p.x1, p.y0, p.y1, eq=p.eq, adv=p.adv, bc=p.bc, gamma=p.gamma, **kw)
+
+    def _check(self, st):
+        if st != 0:
+            raise HwenoError(st, lib().hweno_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hweno_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, a raw cudaStream_t integer, or None (default stream)."""
+        s = getattr(stream, "cuda_stream", stream) or 0
+        self._check(lib().hweno_set_stream(self._h, ctypes.c_void_p(s)))
+
+    def set_moments(self, m):
+        if isinstance(m, np.ndarray):
+            m = np.ascontiguousarray(m)
+        addr, dev, n = _ptr(_f64(m))
+        self._check(lib().hweno_set_moments(self._h, ctypes.c_void_p(addr), n, dev))
+
+    def get_moments(self, out=None):
+        """Into out (torch CUDA tensor or host array) or a new numpy array."""
+        if out is None:
+            out = np.empty(self.shape, np.float64)
+        addr, dev, n = _ptr(_f64(out))
+        self._check(lib().hweno_get_moments(self._h, ctypes.c_void_p(addr), n, dev))
+        return out
+
+    def step(self, dt):
+        self._check(lib().hweno_step(self._h, float(dt)))
+
+    def max_dt(self, cfl=0.6):
+        dt = ctypes.c_double()
+        self._check(lib().hweno_max_dt(self._h, float(cfl), ctypes.byref(dt)))
+        return dt.value
+
+    def troubled_mask(self):
+        out = np.empty((3, self.ny, self.nx), np.uint8)
+        self._check(lib().hweno_troubled_mask(self._h, ctypes.c_void_p(out.ctypes.data), out.size))
+        return out
+
+    def totals(self):
+        out = (ctypes.c_double * 4)()
+        self._check(lib().hweno_totals(self._h, out))
+        return np.array(out[: self.nvar])
+
+    def sync(self):
+        self._check(lib().hweno_sync(self._h))
+
+    def rhs(self, U, Umod, L, mask, aleph=None):
+        """Device tensors: U (in), Umod, L, mask (uint8 [ny, nx]), aleph (optional float64 [ny, nx])."""
+        for x in (U, Umod, L):
+            if _ptr(x)[2] != self.count or not _ptr(x)[1]:
+                raise ValueError("U, Umod and L must be CUDA tensors of nvar*nmom*ny*nx float64")
+        if _ptr(mask)[2] != self.nx * self.ny or not _ptr(mask)[1]:
+            raise ValueError("mask must be a CUDA uint8 tensor of ny*nx")
+        ptrs = [_ptr(x)[0] for x in (U, Umod, L, mask)]
+        a = _ptr(aleph)[0] if aleph is not None else None
+        self._check(lib().hweno_rhs(self._h, *[ctypes.c_void_p(p) for p in ptrs], ctypes.c_void_p(a)))
+
+    def run(self, t_end, cfl=0.6, dt=None, max_steps=10 ** 9):
+        """Advance to t_end (CFL dt unless dt is given), clipping the last step."""
+        t, n = 0.0, 0
+        while t < t_end - 1e-14 * max(1.0, t_end) and n < max_steps:
+            h = dt if dt is not None else self.max_dt(cfl)
+            h = min(h, t_end - t)
+            self.step(h)
+            t += h
+            n += 1
+        self.sync()
+        return n
+
+
+def version():
+    return lib().hweno_version()
