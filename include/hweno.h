@@ -143,6 +143,15 @@ hweno_status hweno_sync(hweno_t h);
  * Asynchronous on the handle's stream. */
 hweno_status hweno_rhs(hweno_t h, const double* U, double* Umod, double* L, unsigned char* mask, double* aleph);
 
+/* Per-kernel timing (instrumentation; no counterpart in the paper).  With
+ * enable != 0, every kernel launch of later steps is bracketed by CUDA events
+ * on the handle's stream.  hweno_profile_read synchronises and writes, for the
+ * nkinds >= 4 kernel kinds {0 reconstruct, 1 indicator + modification,
+ * 2 reconstruct troubled cells, 3 fluxes + quadrature + Runge-Kutta update},
+ * the summed device milliseconds and launch counts since the last read. */
+hweno_status hweno_profile(hweno_t h, int enable);
+hweno_status hweno_profile_read(hweno_t h, double* ms, int* launches, int nkinds);
+
 /* Message of the last error on this handle (never NULL). */
 const char* hweno_last_error(hweno_t h);
 

@@ -207,14 +207,23 @@ void stage_t(const Prob& P, const Weights<T>& W, const Beta1<T>& Bt, const Bufs&
   int* cnt = B.count + S.stage;
   cudaMemsetAsync(cnt, 0, sizeof(int), st);
   const int blocks = (P.nx + RB - 1) / RB;
+  if (B.prof) B.prof->begin(0, st);
   rec1d_kernel<T, NV, false><<<blocks, RB, 0, st>>>(P, W, Bt, S.Uin, nullptr, nullptr, nullptr, nullptr, (T*)B.G,
                                                     (T*)B.aux);
+  if (B.prof) B.prof->end(st);
+  if (B.prof) B.prof->begin(1, st);
   flag1d_kernel<T, NV><<<blocks, RB, 0, st>>>(P, W, S.Uin, (const T*)B.G, (const T*)B.aux, S.mask, S.Mod, B.list, cnt,
                                               S.aleph);
-  if (P.indicator != IND_NONE)
+  if (B.prof) B.prof->end(st);
+  if (P.indicator != IND_NONE) {
+    if (B.prof) B.prof->begin(2, st);
     rec1d_kernel<T, NV, true><<<blocks, RB, 0, st>>>(P, W, Bt, S.Uin, S.mask, S.Mod, B.list, cnt, (T*)B.G, nullptr);
+    if (B.prof) B.prof->end(st);
+  }
   Rk1 r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status};
+  if (B.prof) B.prof->begin(3, st);
   update1d_kernel<T, NV><<<blocks, RB, 0, st>>>(P, (const T*)B.G, r);
+  if (B.prof) B.prof->end(st);
 }
 
 }  // namespace

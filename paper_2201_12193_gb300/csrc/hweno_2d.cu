@@ -357,20 +357,25 @@ void stage_t(const Prob& P, const Weights<T>& W, const Beta2<T>& Bt, const Bufs&
   int* cnt = B.count + S.stage;
   cudaMemsetAsync(cnt, 0, sizeof(int), st);
   const int rblocks = (int)((ncell + RB - 1) / RB);
+  if (B.prof) B.prof->begin(0, st);
   rec2d_kernel<T, NV, false><<<rblocks, RB, 0, st>>>(P, W, Bt, S.Uin, nullptr, nullptr, nullptr, nullptr,
                                                      (T*)B.G, (T*)B.aux);
+  if (B.prof) B.prof->end(st);
   const dim3 blk(TX, TY), grd((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
+  if (B.prof) B.prof->begin(1, st);
   flag2d_kernel<T, NV><<<grd, blk, 0, st>>>(P, W, S.Uin, (const T*)B.G, (const T*)B.aux, S.mask, S.Mod, B.list,
                                             cnt, S.aleph);
+  if (B.prof) B.prof->end(st);
   if (P.indicator != IND_NONE) {
-    int dev = 0, nsm = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int fblocks = (int)std::min<long long>(rblocks, (long long)nsm * 8);
+    const int fblocks = (int)std::min<long long>(rblocks, (long long)P.nsm * 8);
+    if (B.prof) B.prof->begin(2, st);
     rec2d_kernel<T, NV, true><<<fblocks, RB, 0, st>>>(P, W, Bt, S.Uin, S.mask, S.Mod, B.list, cnt, (T*)B.G, nullptr);
+    if (B.prof) B.prof->end(st);
   }
   Rk r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status};
+  if (B.prof) B.prof->begin(3, st);
   update2d_kernel<T, NV><<<grd, blk, 0, st>>>(P, (const T*)B.G, r);
+  if (B.prof) B.prof->end(st);
 }
 
 }  // namespace

@@ -32,6 +32,7 @@ struct hweno_s {
   double* red_part = nullptr;    // reduction partials
   double* red_out = nullptr;     // reduction results (device)
   double* host_buf = nullptr;    // pinned: reduction results + status
+  hw::Prof prof;                 // per-kernel event timing (hweno_profile)
   std::string err;
 };
 
@@ -219,6 +220,8 @@ hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gam
   P.gamma = gamma;
   P.adv_a = h->g.adv_a;
   P.adv_b = h->g.adv_b;
+  P.nsm = 152;
+  cudaDeviceGetAttribute(&P.nsm, cudaDevAttrMultiProcessorCount, h->dev);
   h->fp32 = h->g.precision;
   build_tables(h);
 
@@ -388,6 +391,24 @@ hweno_status hweno_rhs(hweno_t h, const double* U, double* Umod, double* L, unsi
   S.Lout = L; S.Umod = Umod; S.aleph = aleph;
   if (h->g.dim == 1) hw::run_stage_1d(P, h->T, h->fp32, h->B, S, h->stream);
   else hw::run_stage_2d(P, h->T, h->fp32, h->B, S, h->stream);
+  CK(h, cudaGetLastError());
+  return HWENO_OK;
+}
+
+hweno_status hweno_profile(hweno_t h, int enable) {
+  if (!h) return HWENO_EINVAL;
+  CK(h, cudaStreamSynchronize(h->stream));
+  double ms[hw::Prof::KINDS];
+  int n[hw::Prof::KINDS];
+  h->prof.read(ms, n);    // drop anything recorded so far
+  h->B.prof = enable ? &h->prof : nullptr;
+  return HWENO_OK;
+}
+
+hweno_status hweno_profile_read(hweno_t h, double* ms, int* launches, int nkinds) {
+  if (!h || !ms || !launches || nkinds < hw::Prof::KINDS) return fail(h, HWENO_EINVAL, "profile_read: need 4 slots");
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->prof.read(ms, launches);
   CK(h, cudaGetLastError());
   return HWENO_OK;
 }

@@ -36,6 +36,7 @@ struct Prob {
   double dx, dy;
   double gamma;           // ratio of specific heats
   double adv_a, adv_b;    // linear advection speeds
+  int nsm;                // multiprocessors of the device (grid sizing)
 };
 
 // Linear-weight data of eq. (linear-weight) and eq. (p) for positive gbar[4]:

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "hweno_device.cuh"
 
 namespace hw {
@@ -18,6 +20,39 @@ struct HostTabs {
   Beta2<float> b2f;
 };
 
+// Optional per-kernel timing: CUDA events recorded around each launch on the
+// launching stream, read back (and summed per kernel kind) after a sync.
+struct Prof {
+  static constexpr int KINDS = 4;   // 0 reconstruct, 1 indicator + modify, 2 reconstruct troubled, 3 flux + update
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> kinds;           // kind of each begin/end pair
+  size_t used = 0;                  // events handed out
+  cudaEvent_t next() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  void begin(int kind, cudaStream_t s) { kinds.push_back(kind); cudaEventRecord(next(), s); }
+  void end(cudaStream_t s) { cudaEventRecord(next(), s); }
+  // Sum elapsed ms per kind into ms[KINDS] and launches[KINDS]; then reset.
+  void read(double* ms, int* launches) {
+    for (int k = 0; k < KINDS; ++k) { ms[k] = 0.0; launches[k] = 0; }
+    for (size_t p = 0; p < kinds.size(); ++p) {
+      float t = 0.f;
+      cudaEventSynchronize(pool[2 * p + 1]);
+      cudaEventElapsedTime(&t, pool[2 * p], pool[2 * p + 1]);
+      ms[kinds[p]] += t;
+      launches[kinds[p]] += 1;
+    }
+    kinds.clear();
+    used = 0;
+  }
+  ~Prof() { for (cudaEvent_t e : pool) cudaEventDestroy(e); }
+};
+
 // Work buffers owned by a handle.
 struct Bufs {
   void* G;            // point values [nvar][npt][ny][gpitch] in the compute precision
@@ -25,6 +60,7 @@ struct Bufs {
   int* list;          // flagged cells of the current stage (linear index j*nx+i)
   int* count;         // [3] flagged counts per stage
   unsigned* status;   // ST_* bits
+  Prof* prof;         // per-kernel timing, or nullptr
 };
 
 // One evaluation of the spatial operator with the troubled-cell steps and,

@@ -62,6 +62,8 @@ def lib():
         L.hweno_totals.argtypes = [H, D]
         L.hweno_sync.argtypes = [H]
         L.hweno_rhs.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+        L.hweno_profile.argtypes = [H, ctypes.c_int]
+        L.hweno_profile_read.argtypes = [H, D, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
         L.hweno_last_error.argtypes = [H]
         L.hweno_last_error.restype = ctypes.c_char_p
         L.hweno_version.restype = ctypes.c_int
@@ -189,6 +191,18 @@ class Solver:
         ptrs = [_ptr(x)[0] for x in (U, Umod, L, mask)]
         a = _ptr(aleph)[0] if aleph is not None else None
         self._check(lib().hweno_rhs(self._h, *[ctypes.c_void_p(p) for p in ptrs], ctypes.c_void_p(a)))
+
+    KERNEL_KINDS = ("reconstruct", "indicator", "reconstruct_troubled", "update")
+
+    def profile(self, enable=True):
+        self._check(lib().hweno_profile(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        """{kind: (device ms, launches)} since the last read."""
+        ms = (ctypes.c_double * 4)()
+        n = (ctypes.c_int * 4)()
+        self._check(lib().hweno_profile_read(self._h, ms, n, 4))
+        return {k: (ms[i], n[i]) for i, k in enumerate(self.KERNEL_KINDS)}
 
     def run(self, t_end, cfl=0.6, dt=None, max_steps=10 ** 9):
         """Advance to t_end (CFL dt unless dt is given), clipping the last step."""

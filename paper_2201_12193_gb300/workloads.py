@@ -199,14 +199,23 @@ def four_quadrant_states(seed):
 
 
 def four_quadrant_2d(n=2048, seed=0, ny=None):
-    """2D Riemann data on [0,1]^2 split at (0.5, 0.5), transmissive, to t = 0.25."""
+    """2D Riemann data on [0,1]^2 split at (0.5, 0.5), transmissive, to t = 0.25.
+    When n is even the split lies on cell faces and the moments are exact
+    (quadrant state, zero first moments); otherwise they are integrated."""
     ny = ny or n
     rho, mu, nu, p = four_quadrant_states(seed)
 
     def f(X, Y):
         q = (X > 0.5).astype(np.int64) + 2 * (Y > 0.5).astype(np.int64)
         return prim_to_cons_2d(rho[q], mu[q], nu[q], p[q])
-    m = moments_2d(f, 0.0, 1.0, 0.0, 1.0 * ny / n, n, ny)
+    if n % 2 == 0:
+        xc = (np.arange(n) + 0.5) / n
+        yc = (np.arange(ny) + 0.5) / n
+        q = (xc[None, :] > 0.5).astype(np.int64) + 2 * (yc[:, None] > 0.5).astype(np.int64)
+        m = np.zeros((4, 3, ny, n))
+        m[:, 0] = prim_to_cons_2d(rho[q], mu[q], nu[q], p[q])
+    else:
+        m = moments_2d(f, 0.0, 1.0, 0.0, 1.0 * ny / n, n, ny)
     return Problem("four_quadrant_2d", 2, n, ny, 0.0, 1.0, 0.0, 1.0 * ny / n, "euler",
                    ("transmissive",) * 4, m, t_end=0.25, seed=seed,
                    meta={"rho": rho.tolist(), "mu": mu.tolist(), "nu": nu.tolist(), "p": p.tolist()})
