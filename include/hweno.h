@@ -152,6 +152,30 @@ hweno_status hweno_rhs(hweno_t h, const double* U, double* Umod, double* L, unsi
 hweno_status hweno_profile(hweno_t h, int enable);
 hweno_status hweno_profile_read(hweno_t h, double* ms, int* launches, int nkinds);
 
+/* CFL reduction that allocates nothing (the paper has no counterpart; it
+ * serves callers that cannot call cudaMalloc, e.g. code running under a frozen
+ * memory budget or where the implicit synchronisation of an allocation is not
+ * allowed, and that therefore cannot create a handle).
+ *   grid : problem description as for hweno_create (dim, nx, ny, domain, eq,
+ *          adv_a/adv_b); the boundary kinds do not matter here.
+ *   gamma: ratio of specific heats (Euler).
+ *   m    : device pointer, state in the layout above (no padding).
+ *   cfl  : CFL number (> 0).
+ *   out  : device pointer to 3 doubles, written {max a_x, max a_y, dt} with the
+ *          wave speeds and dt of hweno_max_dt; dt = 0 if a cell average is
+ *          non-physical.
+ *   cuda_stream: the stream to run on (NULL = legacy default stream).
+ * Asynchronous: out is valid once the stream has reached this work.  Scratch is
+ * a static device array of 16384 x 2 doubles (256 KiB) per device that loads
+ * the library, held until exit; grids beyond 4,194,304 cells (16384 blocks of
+ * 256) are rejected with HWENO_EINVAL.  The first call on a device looks the
+ * array up (cudaGetSymbolAddress, with that device current): make that first
+ * call before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU race; order them on one stream.  Returns EINVAL for bad
+ * arguments, ECUDA if a launch fails. */
+hweno_status hweno_max_dt_noalloc(const hweno_grid* grid, double gamma, const double* m, double cfl, double* out,
+                                  void* cuda_stream);
+
 /* Message of the last error on this handle (never NULL). */
 const char* hweno_last_error(hweno_t h);
 

@@ -64,6 +64,8 @@ def lib():
         L.hweno_rhs.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.hweno_profile.argtypes = [H, ctypes.c_int]
         L.hweno_profile_read.argtypes = [H, D, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
+        L.hweno_max_dt_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.c_double, ctypes.c_void_p, ctypes.c_double,
+                                           ctypes.c_void_p, ctypes.c_void_p]
         L.hweno_last_error.argtypes = [H]
         L.hweno_last_error.restype = ctypes.c_char_p
         L.hweno_version.restype = ctypes.c_int
@@ -219,3 +221,17 @@ class Solver:
 
 def version():
     return lib().hweno_version()
+
+
+def max_dt_noalloc(grid, gamma, m, cfl, out, stream=None):
+    """hweno_max_dt_noalloc: m and out are CUDA float64 tensors (state; 3 doubles
+    receiving max a_x, max a_y, dt); nothing is allocated by the library."""
+    a, dev, n = _ptr(_f64(m))
+    o, odev, on = _ptr(_f64(out))
+    if not (dev and odev) or on < 3:
+        raise ValueError("m and out must be CUDA float64 tensors (out with 3 elements)")
+    s = getattr(stream, "cuda_stream", stream) or 0
+    st = lib().hweno_max_dt_noalloc(ctypes.byref(grid), float(gamma), ctypes.c_void_p(a), float(cfl),
+                                    ctypes.c_void_p(o), ctypes.c_void_p(s))
+    if st != 0:
+        raise HwenoError(st, "hweno_max_dt_noalloc failed (see stderr)")
