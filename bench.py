@@ -38,10 +38,18 @@ CFL = 0.6
 WORKLOAD = "2d_euler_four_quadrant_2048x2048"
 METRIC = "2D Euler cell-updates/s (per RK stage)"
 UNIT = "cell-updates/s"
-# algorithmic FP64 work of one reconstruction of one variable in one cell:
-# 16 points x (9 + 11 + 23) value MACs, 5x9 + 9x11 + 20x23 indicator MACs, 34 squares,
-# 16 x 4 combination MACs  ->  1390 MAC = 2780 flop
-REC_FLOP_PER_VAR = 2 * (16 * (9 + 11 + 23) + (5 * 9 + 9 * 11 + 20 * 23) + (5 + 9 + 20) + 16 * 4)
+# Algorithmic work of one reconstruction of one variable in one cell, as the kernel
+# evaluates it (mirror-parity form): split + smoothness indicators + point values
+# (counted by the table generator, D2_FLOP_SBV in hweno_parity.h) plus beta_1 and the
+# nonlinear weights (112 flop, a division counted as one).  Per cell add the 44 flop
+# of the KXRCF face-velocity partials and norm (Euler).
+
+
+def _rec_flop_per_cell(nvar=4):
+    import re
+    with open(os.path.join(ROOT, "paper_2201_12193_gb300", "csrc", "hweno_parity.h")) as f:
+        sbv = int(re.search(r"D2_FLOP_SBV = (\d+);", f.read()).group(1))
+    return nvar * (sbv + 112) + 44
 # algorithmic HBM bytes per cell-stage: read U^(k) (12 doubles), read U^n for stages 2-3, write U^(k+1)
 ALGO_BYTES_PER_CELL_STAGE = 12 * 8 * (1 + 2.0 / 3.0 + 1)
 FP64_PEAK_NOMINAL = 1.25e12   # GB300 FP64 FLOP/s (nominal)
@@ -55,6 +63,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=N, help=argparse.SUPPRESS)
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32-bulk form")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="form of the main measurement (fp64 = the scheme as specified)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -215,7 +225,7 @@ def run_ours(args, world, rank, local):
     smi_index = vis.split(",")[local] if vis and vis.split(",")[local].strip().isdigit() else local
     clocks = ClockSampler(smi_index)
 
-    s64, ms, prof, clk, out64 = run_solver(torch, hweno, p, "fp64", args.steps, args.warmup, world,
+    s64, ms, prof, clk, out64 = run_solver(torch, hweno, p, args.precision, args.steps, args.warmup, world,
                                            profile=True, clocks=clocks)
     ms = max_over_ranks(ms, world)
     value = cells * 3 * args.steps * world / (ms * 1e-3)
@@ -224,10 +234,7 @@ def run_ours(args, world, rank, local):
     # roofline of the dominant kernel (largest share of device time)
     kind, (kms, kn) = max(prof.items(), key=lambda kv: kv[1][0])
     total_kernel_ms = sum(v[0] for v in prof.values())
-    if kind in ("reconstruct", "reconstruct_troubled"):
-        flop = REC_FLOP_PER_VAR * s64.nvar * cells * kn if kind == "reconstruct" else None
-    else:
-        flop = None
+    flop = _rec_flop_per_cell(s64.nvar) * cells * kn if kind == "reconstruct" else None
     roof = None
     if flop:
         achieved = flop / (kms * 1e-3)

@@ -94,9 +94,19 @@ __device__ __forceinline__ void rec2d_cell(const Prob& P, const Weights<T>& W, c
 #pragma unroll
         for (int p = 0; p < 16; ++p) nrm = tmax(nrm, tabs(out[p]));
         if (P.eq == EQ_EULER) {
+          // 1/rho at the 12 boundary points (the face velocities need only those)
+          constexpr int bp[12] = {0, 1, 2, 3, 4, 7, 8, 11, 12, 13, 14, 15};
+          if constexpr (sizeof(T) == 8) {
+            T x[12], r[12];
 #pragma unroll
-          for (int p = 0; p < 16; ++p)
-            if (p / 4 == 0 || p / 4 == 3 || p % 4 == 0 || p % 4 == 3) rinv[p] = T(1) / out[p];
+            for (int q = 0; q < 12; ++q) x[q] = out[bp[q]];
+            batch_inverse<12, T>(x, r);
+#pragma unroll
+            for (int q = 0; q < 12; ++q) rinv[bp[q]] = r[q];
+          } else {
+#pragma unroll
+            for (int q = 0; q < 12; ++q) rinv[bp[q]] = T(1) / out[bp[q]];
+          }
         } else if (P.eq == EQ_BURGERS) {
 #pragma unroll
           for (int l = 0; l < 4; ++l) {
@@ -301,18 +311,38 @@ __global__ void __launch_bounds__(TX * TY) update2d_kernel(Prob P, const T* __re
       Gmx[v] += we * yf[ty][tx][l][v];
     }
   }
+  if constexpr (NV == 4 && sizeof(T) == 8) {
+    // Euler, FP64: the 16 reciprocal densities with one division
+    T rho[16], inv[16];
 #pragma unroll
-  for (int k = 0; k < 4; ++k)
+    for (int p = 0; p < 16; ++p) rho[p] = G[(long long)p * P.gplane + goff(P, i, j)];
+    batch_inverse<16, T>(rho, inv);
 #pragma unroll
-    for (int l = 0; l < 4; ++l) {
-      T u[NV], fx[NV], gy[NV];
-      gl_state<T, NV>(P, G, self, k, l, u);
-      phys_flux<T, NV>(P, u, 0, fx);
-      phys_flux<T, NV>(P, u, 1, gy);
-      const T w = gl_w<T>(k) * gl_w<T>(l);
+    for (int k = 0; k < 4; ++k)
 #pragma unroll
-      for (int v = 0; v < NV; ++v) { Fc[v] += w * fx[v]; Gc[v] += w * gy[v]; }
-    }
+      for (int l = 0; l < 4; ++l) {
+        T u[NV], fx[NV], gy[NV];
+        gl_state<T, NV>(P, G, self, k, l, u);
+        euler_flux_inv<T, NV>(P, u, inv[k * 4 + l], 0, fx);
+        euler_flux_inv<T, NV>(P, u, inv[k * 4 + l], 1, gy);
+        const T w = gl_w<T>(k) * gl_w<T>(l);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { Fc[v] += w * fx[v]; Gc[v] += w * gy[v]; }
+      }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) {
+        T u[NV], fx[NV], gy[NV];
+        gl_state<T, NV>(P, G, self, k, l, u);
+        phys_flux<T, NV>(P, u, 0, fx);
+        phys_flux<T, NV>(P, u, 1, gy);
+        const T w = gl_w<T>(k) * gl_w<T>(l);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { Fc[v] += w * fx[v]; Gc[v] += w * gy[v]; }
+      }
+  }
   // eq. (2D-equ-int-approximation); the average equation in FP64 from the
   // face integrals so that the flux differences telescope in every precision
   const double idx = 1.0 / P.dx, idy = 1.0 / P.dy;

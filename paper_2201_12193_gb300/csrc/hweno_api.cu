@@ -7,7 +7,7 @@
 #include <algorithm>
 #include <string>
 
-#define HWT_WITH_INDICATOR_ROWS
+#define HWP_HOST_TABLES
 #include "hweno_internal.h"
 #include "hweno.h"
 
@@ -80,40 +80,23 @@ void build_tables(hweno_s* h) {
     b = -S[l - 1] / g[l - 1];
   };
   long double a, b;
-  if (h->P.ny == 1 && h->g.dim == 1) {
-    coef(2, a, b);   // q_1 is constant: no derivative contribution
-    for (int r = 0; r < 2; ++r) for (int c = 0; c < 3; ++c) {
-      const long double v = a * hwt::D1_RC2_2[r][c];
-      h->T.b1d.B2[r][c] = (double)v; h->T.b1f.B2[r][c] = (float)v;
+  // flat rows: B_l[k] = a_l RC_l_l[k] + b_l RC_l_(l-1)[k]; q_1 is constant, so level 2 has no b part
+  auto fill = [&](int l, const double* rl, const double* rm, int n, double* outd, float* outf) {
+    coef(l, a, b);
+    for (int k = 0; k < n; ++k) {
+      const long double v = a * rl[k] + (rm ? b * rm[k] : 0.0L);
+      outd[k] = (double)v;
+      outf[k] = (float)v;
     }
-    coef(3, a, b);
-    for (int r = 0; r < 3; ++r) for (int c = 0; c < 4; ++c) {
-      const int k = hwt::D1_I3[c];
-      const long double v = a * hwt::D1_RC3_3[r][k] + b * hwt::D1_RC3_2[r][k];
-      h->T.b1d.B3[r][c] = (double)v; h->T.b1f.B3[r][c] = (float)v;
-    }
-    coef(4, a, b);
-    for (int r = 0; r < 5; ++r) for (int c = 0; c < 6; ++c) {
-      const long double v = a * hwt::D1_RC4_4[r][c] + b * hwt::D1_RC4_3[r][c];
-      h->T.b1d.B4[r][c] = (double)v; h->T.b1f.B4[r][c] = (float)v;
-    }
+  };
+  if (h->g.dim == 1) {
+    fill(2, hwp::D1P_RC2_2, nullptr, hwp::D1_NB2, h->T.b1d.B2, h->T.b1f.B2);
+    fill(3, hwp::D1P_RC3_3, hwp::D1P_RC3_2, hwp::D1_NB3, h->T.b1d.B3, h->T.b1f.B3);
+    fill(4, hwp::D1P_RC4_4, hwp::D1P_RC4_3, hwp::D1_NB4, h->T.b1d.B4, h->T.b1f.B4);
   } else {
-    coef(2, a, b);
-    for (int r = 0; r < 5; ++r) for (int c = 0; c < 9; ++c) {
-      const long double v = a * hwt::D2_RC2_2[r][c];
-      h->T.b2d.B2[r][c] = (double)v; h->T.b2f.B2[r][c] = (float)v;
-    }
-    coef(3, a, b);
-    for (int r = 0; r < 9; ++r) for (int c = 0; c < 11; ++c) {
-      const int k = hwt::D2_I3[c];
-      const long double v = a * hwt::D2_RC3_3[r][k] + b * hwt::D2_RC3_2[r][k];
-      h->T.b2d.B3[r][c] = (double)v; h->T.b2f.B3[r][c] = (float)v;
-    }
-    coef(4, a, b);
-    for (int r = 0; r < 20; ++r) for (int c = 0; c < 23; ++c) {
-      const long double v = a * hwt::D2_RC4_4[r][c] + b * hwt::D2_RC4_3[r][c];
-      h->T.b2d.B4[r][c] = (double)v; h->T.b2f.B4[r][c] = (float)v;
-    }
+    fill(2, hwp::D2P_RC2_2, nullptr, hwp::D2_NB2, h->T.b2d.B2, h->T.b2f.B2);
+    fill(3, hwp::D2P_RC3_3, hwp::D2P_RC3_2, hwp::D2_NB3, h->T.b2d.B3, h->T.b2f.B3);
+    fill(4, hwp::D2P_RC4_4, hwp::D2P_RC4_3, hwp::D2_NB4, h->T.b2d.B4, h->T.b2f.B4);
   }
 }
 

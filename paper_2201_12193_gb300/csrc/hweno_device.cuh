@@ -10,8 +10,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#define HWT_VALUE_QUAL static __constant__
-#include "hweno_tables.h"
+#include "hweno_parity.h"
 
 namespace hw {
 
@@ -50,29 +49,11 @@ struct Weights {
   T h2;          // h^{(l+1)/3} with l = 5, h = dx  (eq. (KXRCF))
 };
 
-// Rows of the smoothness indicators beta_2..beta_4 for the run-time weights:
-// beta_l = sum_r (B_l[r] . d_l)^2, d_l the level's data (eq. (beta), (2D-beta)).
-template <typename T> struct Beta1 { T B2[2][3]; T B3[3][4]; T B4[5][6]; };
-template <typename T> struct Beta2 { T B2[5][9]; T B3[9][11]; T B4[20][23]; };
-
-// ---------------------------------------------------------------- tables by precision
-template <typename T> struct Tab;
-template <> struct Tab<double> {
-  static __device__ __forceinline__ double v1_2(int p, int c) { return hwt::D1_V2[p][c]; }
-  static __device__ __forceinline__ double v1_3(int p, int c) { return hwt::D1_V3[p][c]; }
-  static __device__ __forceinline__ double v1_4(int p, int c) { return hwt::D1_V4[p][c]; }
-  static __device__ __forceinline__ double v2_2(int p, int c) { return hwt::D2_V2[p][c]; }
-  static __device__ __forceinline__ double v2_3(int p, int c) { return hwt::D2_V3[p][c]; }
-  static __device__ __forceinline__ double v2_4(int p, int c) { return hwt::D2_V4[p][c]; }
-};
-template <> struct Tab<float> {
-  static __device__ __forceinline__ float v1_2(int p, int c) { return hwt::D1_V2f[p][c]; }
-  static __device__ __forceinline__ float v1_3(int p, int c) { return hwt::D1_V3f[p][c]; }
-  static __device__ __forceinline__ float v1_4(int p, int c) { return hwt::D1_V4f[p][c]; }
-  static __device__ __forceinline__ float v2_2(int p, int c) { return hwt::D2_V2f[p][c]; }
-  static __device__ __forceinline__ float v2_3(int p, int c) { return hwt::D2_V3f[p][c]; }
-  static __device__ __forceinline__ float v2_4(int p, int c) { return hwt::D2_V4f[p][c]; }
-};
+// Rows of the smoothness indicators beta_2..beta_4 for the run-time weights,
+// in the flat parity-basis order of hweno_parity.h: beta_l = sum_rows (row . s)^2
+// with row = (S_l/g_l) R C_l - (S_{l-1}/g_l) R C_{l-1}  (eq. (beta), (2D-beta), (p)).
+template <typename T> struct Beta1 { T B2[hwp::D1_NB2]; T B3[hwp::D1_NB3]; T B4[hwp::D1_NB4]; };
+template <typename T> struct Beta2 { T B2[hwp::D2_NB2]; T B3[hwp::D2_NB3]; T B4[hwp::D2_NB4]; };
 
 // Gauss-Lobatto nodes and weights of eq. (F)
 template <typename T> __device__ __forceinline__ T gl_w(int k) { return (k == 0 || k == 3) ? T(1.0 / 12.0) : T(5.0 / 12.0); }
@@ -126,6 +107,40 @@ __device__ __forceinline__ void phys_flux(const Prob& P, const T* u, int dir, T*
   }
 }
 
+// Euler flux with the reciprocal of the density supplied by the caller.
+template <typename T, int NV>
+__device__ __forceinline__ void euler_flux_inv(const Prob& P, const T* u, T inv, int dir, T* f) {
+  const T g = T(P.gamma);
+  if constexpr (NV == 3) {
+    const T mu = u[1] * inv, E = u[2];
+    const T p = (g - T(1)) * (E - T(0.5) * u[1] * mu);
+    f[0] = u[1]; f[1] = u[1] * mu + p; f[2] = mu * (E + p);
+  } else {
+    const T mu = u[1] * inv, nu = u[2] * inv, E = u[3];
+    const T p = (g - T(1)) * (E - T(0.5) * (u[1] * mu + u[2] * nu));
+    if (dir == 0) { f[0] = u[1]; f[1] = u[1] * mu + p; f[2] = u[1] * nu; f[3] = mu * (E + p); }
+    else          { f[0] = u[2]; f[1] = u[2] * mu; f[2] = u[2] * nu + p; f[3] = nu * (E + p); }
+  }
+}
+
+// Reciprocals of N values with a single division (prefix products, one inverse,
+// back substitution); used by the FP64 path, where a division costs about as
+// much as a dozen fused multiply-adds.
+template <int N, typename T>
+__device__ __forceinline__ void batch_inverse(const T (&x)[N], T (&inv)[N]) {
+  T pre[N];
+  pre[0] = x[0];
+#pragma unroll
+  for (int i = 1; i < N; ++i) pre[i] = pre[i - 1] * x[i];
+  T r = T(1) / pre[N - 1];
+#pragma unroll
+  for (int i = N - 1; i > 0; --i) {
+    inv[i] = r * pre[i - 1];
+    r = r * x[i];
+  }
+  inv[0] = r;
+}
+
 // Velocity seen by the KXRCF indicator for scalar laws (Remarks 2, 3): f'(u), g'(u).
 template <typename T>
 __device__ __forceinline__ T scalar_velocity(const Prob& P, T u, int dir) {
@@ -143,7 +158,15 @@ __device__ __forceinline__ void hllc(const Prob& P, const T* uL, const T* uR, in
   const int in = 1 + dir, it = 2 - dir;
   constexpr int iE = NV - 1;
   const T rL = uL[0], rR = uR[0];
-  const T iL = T(1) / rL, iR = T(1) / rR;
+  T iL, iR;
+  if constexpr (sizeof(T) == 8) {   // FP64: one division for both reciprocals
+    const T q = T(1) / (rL * rR);
+    iL = rR * q;
+    iR = rL * q;
+  } else {
+    iL = T(1) / rL;
+    iR = T(1) / rR;
+  }
   const T mL = uL[in] * iL, mR = uR[in] * iR;
   const T tL = two ? uL[it] * iL : T(0), tR = two ? uR[it] * iR : T(0);
   const T EL = uL[iE], ER = uR[iE];
@@ -174,12 +197,24 @@ __device__ __forceinline__ void hllc(const Prob& P, const T* uL, const T* uR, in
     for (int v = 0; v < NV; ++v) F[v] = fK[v];
     return;
   }
-  const T fac = rK * (sK - mK) / (sK - ss);
+  const T a = sK - mK, b = sK - ss;
+  T fac, ek, pk;
+  if constexpr (sizeof(T) == 8) {   // FP64: D = 1/(a b) gives 1/a and 1/b with one division
+    const T iK = useL ? iL : iR;
+    const T D = T(1) / (a * b);
+    fac = rK * a * (a * D);
+    ek = EK * iK;
+    pk = pK * iK * (b * D);
+  } else {
+    fac = rK * a / b;
+    ek = EK / rK;
+    pk = pK / (rK * a);
+  }
   T us[NV];
   us[0] = fac;
   us[in] = fac * ss;
   if constexpr (two) us[it] = fac * tK;
-  us[iE] = fac * (EK / rK + (ss - mK) * (ss + pK / (rK * (sK - mK))));
+  us[iE] = fac * (ek + (ss - mK) * (ss + pk));
 #pragma unroll
   for (int v = 0; v < NV; ++v) F[v] = fK[v] + sK * (us[v] - uK[v]);
 }
@@ -200,12 +235,6 @@ __device__ __forceinline__ void num_flux(const Prob& P, const T* uL, const T* uR
   else hllc<T, NV>(P, uL, uR, dir, F);
 }
 
-// Unroll factor of the long table loops: FP64 issue is the bottleneck, so the
-// FP64 path keeps loops rolled (indexed constant loads are hidden behind the
-// slow FP64 pipe) and saves registers; FP32 unrolls fully.
-template <typename T> struct Unroll { static constexpr int rows = 1, pts = 1; };
-template <> struct Unroll<float> { static constexpr int rows = 32, pts = 16; };
-
 // ---------------------------------------------------------------- nonlinear weights
 // WENO-Z weights of eqs. (tau4), (non-linear-weight) and the combination of
 // eq. (re-p) rewritten on q_1..q_4:  u = sum_k c_k q_k with
@@ -214,13 +243,27 @@ template <typename T>
 __device__ __forceinline__ void combine_weights(const Weights<T>& W, const T beta[4], T c[4]) {
   const T tau4s = tabs(beta[3] - beta[0]) + tabs(beta[3] - beta[1]) + tabs(beta[3] - beta[2]);
   const T tau4 = (tau4s * T(1.0 / 3.0)) * (tau4s * T(1.0 / 3.0));
-  T wb[4], ws = T(0);
-#pragma unroll
-  for (int l = 0; l < 4; ++l) { wb[l] = W.gam[l] * (T(1) + tau4 / (beta[l] + W.eps)); ws += wb[l]; }
-  const T inv = T(1) / ws;
   T om[4];
+  if constexpr (sizeof(T) == 8) {
+    // FP64: one division.  With x_l = beta_l + eps, wbar_l = gamma_l (x_l + tau)/x_l;
+    // scaling every wbar_l by prod_m x_m gives N_l = gamma_l (x_l + tau) prod_{m!=l} x_m
+    // and omega_l = N_l / sum_m N_m.
+    const T x0 = beta[0] + W.eps, x1 = beta[1] + W.eps, x2 = beta[2] + W.eps, x3 = beta[3] + W.eps;
+    const T p01 = x0 * x1, p23 = x2 * x3;
+    const T n0 = W.gam[0] * (x0 + tau4) * (x1 * p23);
+    const T n1 = W.gam[1] * (x1 + tau4) * (x0 * p23);
+    const T n2 = W.gam[2] * (x2 + tau4) * (p01 * x3);
+    const T n3 = W.gam[3] * (x3 + tau4) * (p01 * x2);
+    const T inv = T(1) / ((n0 + n1) + (n2 + n3));
+    om[0] = n0 * inv; om[1] = n1 * inv; om[2] = n2 * inv; om[3] = n3 * inv;
+  } else {
+    T wb[4], ws = T(0);
 #pragma unroll
-  for (int l = 0; l < 4; ++l) om[l] = wb[l] * inv;
+    for (int l = 0; l < 4; ++l) { wb[l] = W.gam[l] * (T(1) + tau4 / (beta[l] + W.eps)); ws += wb[l]; }
+    const T inv = T(1) / ws;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) om[l] = wb[l] * inv;
+  }
   c[0] = om[0] * W.sg[0] - om[1] * W.s1g[1];
   c[1] = om[1] * W.sg[1] - om[2] * W.s1g[2];
   c[2] = om[2] * W.sg[2] - om[3] * W.s1g[3];
@@ -232,55 +275,31 @@ __device__ __forceinline__ void combine_weights(const Weights<T>& W, const T bet
 // four Gauss-Lobatto values of eq. (re-u).  Steps 1.1-1.3 of the 1D algorithm.
 template <typename T>
 __device__ __forceinline__ void recon1d(const Weights<T>& W, const Beta1<T>& B, const T (&d)[6], T (&out)[4]) {
-  const T d3[4] = {d[0], d[1], d[2], d[4]};
+  T s[6];
+  hwp::split1d<T>(d, s);
   T beta[4];
-  {
-    T b = T(0);
-#pragma unroll
-    for (int r = 0; r < 2; ++r) { T s = T(0);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) s = fma(B.B2[r][c], d[c], s);
-      b = fma(s, s, b); }
-    beta[1] = b;
-    b = T(0);
-#pragma unroll
-    for (int r = 0; r < 3; ++r) { T s = T(0);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) s = fma(B.B3[r][c], d3[c], s);
-      b = fma(s, s, b); }
-    beta[2] = b;
-    b = T(0);
-#pragma unroll
-    for (int r = 0; r < 5; ++r) { T s = T(0);
-#pragma unroll
-      for (int c = 0; c < 6; ++c) s = fma(B.B4[r][c], d[c], s);
-      b = fma(s, s, b); }
-    beta[3] = b;
-  }
+  hwp::beta1d<T>(B.B2, B.B3, B.B4, s, beta[1], beta[2], beta[3]);
   // beta_1: eqs. (beta1-LR), (tau1), (w1_-LR), (w1-LR), (beta1)
   {
     const T dl = d[1] - d[0], dr = d[2] - d[1];
     const T bl = dl * dl, br = dr * dr;
     const T t1 = tabs(br - bl) * tabs(br - bl);
-    const T wl = T(0.5) * (T(1) + t1 / (bl + W.eps));
-    const T wr = T(0.5) * (T(1) + t1 / (br + W.eps));
-    const T inv = T(1) / (wl + wr);
-    const T gg = (wl * inv) * dl + (wr * inv) * dr;
+    T gg;
+    if constexpr (sizeof(T) == 8) {   // common denominator: one division
+      const T xl = bl + W.eps, xr = br + W.eps;
+      const T nl = (xl + t1) * xr, nr = (xr + t1) * xl;
+      gg = (nl * dl + nr * dr) / (nl + nr);
+    } else {
+      const T wl = T(0.5) * (T(1) + t1 / (bl + W.eps));
+      const T wr = T(0.5) * (T(1) + t1 / (br + W.eps));
+      const T inv = T(1) / (wl + wr);
+      gg = (wl * inv) * dl + (wr * inv) * dr;
+    }
     beta[0] = gg * gg;
   }
   T c[4];
   combine_weights(W, beta, c);
-#pragma unroll
-  for (int p = 0; p < 4; ++p) {
-    T s2 = T(0), s3 = T(0), s4 = T(0);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) s2 = fma(Tab<T>::v1_2(p, k), d[k], s2);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) s3 = fma(Tab<T>::v1_3(p, k), d3[k], s3);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) s4 = fma(Tab<T>::v1_4(p, k), d[k], s4);
-    out[p] = c[0] * d[1] + c[1] * s2 + c[2] * s3 + c[3] * s4;
-  }
+  hwp::values1d<T>(s, d[1], c, out);
 }
 
 // ---------------------------------------------------------------- 2D reconstruction
@@ -290,35 +309,10 @@ __device__ __forceinline__ void recon1d(const Weights<T>& W, const Beta1<T>& B, 
 // Square cells: beta_1 of eq. (2D-beta1) is (sum w_1k Dx_k)^2 + (sum w_1k Dy_k)^2.
 template <typename T>
 __device__ __forceinline__ void recon2d(const Weights<T>& W, const Beta2<T>& B, const T (&d)[23], T (&out)[16]) {
-  T d3[11];
-#pragma unroll
-  for (int c = 0; c < 9; ++c) d3[c] = d[c];
-  d3[9] = d[12];
-  d3[10] = d[19];
+  T s[23];
+  hwp::split2d<T>(d, s);
   T beta[4];
-  {
-    T b = T(0);
-#pragma unroll
-    for (int r = 0; r < 5; ++r) { T s = T(0);
-#pragma unroll
-      for (int c = 0; c < 9; ++c) s = fma(B.B2[r][c], d[c], s);
-      b = fma(s, s, b); }
-    beta[1] = b;
-    b = T(0);
-#pragma unroll Unroll<T>::rows
-    for (int r = 0; r < 9; ++r) { T s = T(0);
-#pragma unroll
-      for (int c = 0; c < 11; ++c) s = fma(B.B3[r][c], d3[c], s);
-      b = fma(s, s, b); }
-    beta[2] = b;
-    b = T(0);
-#pragma unroll Unroll<T>::rows
-    for (int r = 0; r < 20; ++r) { T s = T(0);
-#pragma unroll
-      for (int c = 0; c < 23; ++c) s = fma(B.B4[r][c], d[c], s);
-      b = fma(s, s, b); }
-    beta[3] = b;
-  }
+  hwp::beta2d<T>(B.B2, B.B3, B.B4, s, beta[1], beta[2], beta[3]);
   // beta_1: eqs. (2D-q1-1234) .. (2D-beta1); tau_1 over the 6 unordered pairs
   {
     const T u2 = d[1], u4 = d[3], u5 = d[4], u6 = d[5], u8 = d[7];
@@ -333,28 +327,29 @@ __device__ __forceinline__ void recon2d(const Weights<T>& W, const Beta2<T>& B, 
 #pragma unroll
       for (int l = k + 1; l < 4; ++l) ts += tabs(b1[k] - b1[l]);
     const T t1 = (ts * T(1.0 / 6.0)) * (ts * T(1.0 / 6.0));
-    T w[4], wsum = T(0);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) { w[k] = T(0.25) * (T(1) + t1 / (b1[k] + W.eps)); wsum += w[k]; }
-    const T inv = T(1) / wsum;
     T gx = T(0), gy = T(0);
+    if constexpr (sizeof(T) == 8) {   // common denominator: one division
+      const T y0 = b1[0] + W.eps, y1 = b1[1] + W.eps, y2 = b1[2] + W.eps, y3 = b1[3] + W.eps;
+      const T p01 = y0 * y1, p23 = y2 * y3;
+      const T n[4] = {(y0 + t1) * (y1 * p23), (y1 + t1) * (y0 * p23), (y2 + t1) * (p01 * y3), (y3 + t1) * (p01 * y2)};
+      const T inv = T(1) / ((n[0] + n[1]) + (n[2] + n[3]));
 #pragma unroll
-    for (int k = 0; k < 4; ++k) { gx = fma(w[k] * inv, bx[k], gx); gy = fma(w[k] * inv, by[k], gy); }
+      for (int k = 0; k < 4; ++k) { gx = fma(n[k], bx[k], gx); gy = fma(n[k], by[k], gy); }
+      gx *= inv;
+      gy *= inv;
+    } else {
+      T w[4], wsum = T(0);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) { w[k] = T(0.25) * (T(1) + t1 / (b1[k] + W.eps)); wsum += w[k]; }
+      const T inv = T(1) / wsum;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) { gx = fma(w[k] * inv, bx[k], gx); gy = fma(w[k] * inv, by[k], gy); }
+    }
     beta[0] = gx * gx + gy * gy;
   }
   T c[4];
   combine_weights(W, beta, c);
-#pragma unroll Unroll<T>::pts
-  for (int p = 0; p < 16; ++p) {
-    T s2 = T(0), s3 = T(0), s4 = T(0);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) s2 = fma(Tab<T>::v2_2(p, k), d[k], s2);
-#pragma unroll
-    for (int k = 0; k < 11; ++k) s3 = fma(Tab<T>::v2_3(p, k), d3[k], s3);
-#pragma unroll
-    for (int k = 0; k < 23; ++k) s4 = fma(Tab<T>::v2_4(p, k), d[k], s4);
-    out[p] = c[0] * d[4] + c[1] * s2 + c[2] * s3 + c[3] * s4;
-  }
+  hwp::values2d<T>(s, d[4], c, out);
 }
 
 // Positions (ox, oy, kind) of the 23 data of q_4 in gather order.

@@ -54,9 +54,63 @@ def test_generated_header_is_current():
     gen = _gen()
     import io
     buf = io.StringIO()
-    gen.main(buf)
-    with open(os.path.join(CSRC, "hweno_tables.h")) as f:
+    gen.emit_parity(buf)
+    with open(os.path.join(CSRC, "hweno_parity.h")) as f:
         assert f.read() == buf.getvalue()
+
+
+def _oracle_data(d4, dvec, dim):
+    if dim == 1:
+        return dvec.copy()
+    data = np.zeros(27)
+    for c, (kind, ox, oy) in enumerate(d4):
+        data[kind * 9 + (oy + 1) * 3 + (ox + 1)] = dvec[c]
+    return data
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_parity_form_matches_oracle(orc, dim):
+    """The form the kernels evaluate: parity split, per-class value rows at the base
+    points with the mirror signs, and per-class indicator rows, against the
+    oracle's polynomials and smoothness indicators."""
+    gen = _gen()
+    P = gen.build_parity(dim)
+    d4, basis, sl, bases, VP, RCP = P
+    lay = gen.beta_layout(dim, P)
+    classes = gen.parity_classes(dim)
+    nodes = [-0.5, -np.sqrt(5) / 10, np.sqrt(5) / 10, 0.5]
+    rng = np.random.default_rng(5 + dim)
+    gbar = (1.0, 2.0, 4.0, 8.0)
+    S = np.cumsum((0.0,) + gbar)
+    for _ in range(3):
+        dvec = rng.standard_normal(len(d4))
+        s = np.zeros(len(d4))
+        for c in classes:
+            for j, r in enumerate(basis[c]):
+                s[sl[c][j]] = np.dot(r, dvec)
+        data = _oracle_data(d4, dvec, dim)
+        for lvl in (2, 3, 4):
+            cf = orc.poly(dim, lvl, data, "q")
+            for b in bases:
+                for sx in (1, -1):
+                    for sy in ((1, -1) if dim == 2 else (1,)):
+                        k = b[0] if sx > 0 else 3 - b[0]
+                        l = b[1] if (dim == 1 or sy > 0) else 3 - b[1]
+                        got = 0.0
+                        for c in classes:
+                            chi = (sx if c[0] else 1) * (sy if c[1] else 1)
+                            got += chi * sum(float(g.to_decimal()) * s[sl[c][j]] for j, g in enumerate(VP[(lvl, b, c)]))
+                        x, y = nodes[k], (nodes[l] if dim == 2 else 0.0)
+                        want = sum(cf[a, bb] * x ** a * y ** bb for a in range(6) for bb in range(6))
+                        assert abs(got - want) <= 1e-12 * (1 + abs(want))
+        _, beta, _ = orc.recon_cell(dim, data, gbar)
+        for lvl in (2, 3, 4):
+            a, bcoef = S[lvl] / gbar[lvl - 1], -S[lvl - 1] / gbar[lvl - 1]
+            tot = 0.0
+            for ent in lay[lvl]:
+                r = sum((a * float(x) + bcoef * float(y)) * s[j] for (j, x, y) in ent)
+                tot += r * r
+            np.testing.assert_allclose(tot, beta[lvl - 1], rtol=1e-11)
 
 
 @pytest.mark.parametrize("dim", [1, 2])
