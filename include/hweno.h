@@ -143,6 +143,41 @@ hweno_status hweno_sync(hweno_t h);
  * Asynchronous on the handle's stream. */
 hweno_status hweno_rhs(hweno_t h, const double* U, double* Umod, double* L, unsigned char* mask, double* aleph);
 
+/* ---------------------------------------------------------------- batches
+ * Many independent 2D Euler problems of different sizes in one handle; every
+ * problem is the scheme above on its own grid and boundary kinds.  One batched
+ * step is one SSP-RK3 step of every problem, run as one persistent cooperative
+ * launch per Runge-Kutta stage (all problems' cells and tiles form one work
+ * list), captured in a CUDA graph and replayed.  Phases inside a launch are
+ * separated by a grid barrier whose waits are bounded; a wait that gives up
+ * sets HWENO_ETIMEOUT (reported by the next synchronising call, which rolls the
+ * step back).  All grids must be dim 2, eq Euler, and share precision,
+ * indicator, gamma_bar and beta_of_q; cells square per problem.
+ *
+ * hweno_create_batch: n problems (grids[k], bcs[k]).
+ * hweno_batch_set_moments / get_moments: problem k's moments in the state
+ *   layout (count = 12 ny nx); get with a host destination synchronises.
+ * hweno_step_batch: dt_device = device array of n doubles (one dt per problem)
+ *   or NULL: each problem takes its CFL dt (reading of Sec. 3, as
+ *   hweno_max_dt) from its own cell averages, computed on the device.
+ * hweno_batch_dt: the dt each problem used in the last step (host, n doubles).
+ * hweno_batch_troubled_mask: problem k's flags of the last step [3][ny][nx].
+ * hweno_batch_set_tile: update-phase tile shape 0: 32x4, 1: 16x8, 2: 64x2
+ *   (results do not depend on it; an autotuner picks the fastest). */
+hweno_status hweno_create_batch(const hweno_grid* grids, const hweno_bc* bcs, int n, double gamma, hweno_t* out);
+hweno_status hweno_batch_set_moments(hweno_t h, int k, const double* m, size_t count, int on_device);
+hweno_status hweno_batch_get_moments(hweno_t h, int k, double* m, size_t count, int on_device);
+hweno_status hweno_step_batch(hweno_t h, const double* dt_device, double cfl);
+hweno_status hweno_batch_dt(hweno_t h, double* dt, int n);
+hweno_status hweno_batch_troubled_mask(hweno_t h, int k, unsigned char* mask, size_t count);
+hweno_status hweno_batch_set_tile(hweno_t h, int variant);
+/* 1 if the last batched step was replayed from a captured CUDA graph, 0 if its
+ * launches were issued directly (capture unavailable), -1 for a non-batch handle. */
+int hweno_batch_uses_graph(hweno_t h);
+/* Per-problem status bits of the last failure a synchronising call reported
+ * (1 = non-finite value, 2 = rho <= 0 or p <= 0; 0 = fine), n entries. */
+hweno_status hweno_batch_status(hweno_t h, unsigned* bits, int n);
+
 /* Per-kernel timing (instrumentation; no counterpart in the paper).  With
  * enable != 0, every kernel launch of later steps is bracketed by CUDA events
  * on the handle's stream.  hweno_profile_read synchronises and writes, for the

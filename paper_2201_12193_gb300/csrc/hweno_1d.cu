@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(RB) flag1d_kernel(Prob P, Weights<T> W, const 
       const T jr = G[3 * P.gplane + i] - G[(long long)mpt1(R, 0) * P.gplane + R.i];
       const T s = jl * (vl > T(KX_VDEAD) ? T(1) : T(0)) + jr * (-vr > T(KX_VDEAD) ? T(1) : T(0));
       const T nrm = aux[2 * P.gplane + i];
-      const T a = nrm == T(0) ? T(0) : tabs(s) / (W.h2 * nrm);
+      const T a = nrm == T(0) ? T(0) : tabs(s) / (T(P.dx * P.dx) * nrm);   // h^{(l+1)/3}, l = 5
       if (aleph) aleph[i] = double(a);
       flag = a > T(1);
     }

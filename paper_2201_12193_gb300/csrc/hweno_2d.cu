@@ -193,42 +193,25 @@ __device__ __forceinline__ T kxrcf2d(const Prob& P, const Weights<T>& W, const T
   }
   const T nrm = aux[4 * P.gplane + o];
   if (len == T(0) || nrm == T(0)) return T(0);
-  return tabs(s) / len / (W.h2 * nrm);
+  return tabs(s) / len / (T(P.dx * P.dx) * nrm);   // h^{(l+1)/3}, l = 5, h = dx
 }
 
-template <typename T, int NV>
-__global__ void __launch_bounds__(TX * TY) flag2d_kernel(Prob P, Weights<T> W, const double* __restrict__ U,
-                                                        const T* __restrict__ G, const T* __restrict__ aux,
-                                                        uint8_t* __restrict__ mask, double* __restrict__ Mod,
-                                                        int* __restrict__ list, int* __restrict__ count,
-                                                        double* __restrict__ aleph) {
-  const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
-  const bool valid = i < P.nx && j < P.ny;
-  bool flag = false;
-  if (valid) {
-    if (P.indicator == IND_ALL) {
-      flag = true;
-    } else if (P.indicator == IND_KXRCF) {
-      const T a = kxrcf2d<T>(P, W, G, aux, i, j);
-      if (aleph) aleph[(long long)j * P.nx + i] = double(a);
-      flag = a > T(1);
-    }
-  }
-  // warp-aggregated append to the troubled-cell list (a warp is one tile row)
-  const unsigned act = __ballot_sync(0xffffffffu, flag);
-  if (act) {
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(act) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(count, __popc(act));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (flag) list[base + __popc(act & ((1u << lane) - 1u))] = j * P.nx + i;
-  }
-  if (!valid) return;
-  mask[(long long)j * P.nx + i] = flag ? 1 : 0;
-  if (!flag) return;
-  // Step 2.2 (dimension by dimension): modified first moments from the
-  // pre-modification moments of the x and y neighbours.
+// Step 2.1 for one cell: the troubled-cell decision of the configured indicator.
+template <typename T>
+__device__ __forceinline__ bool flag2d_cell(const Prob& P, const Weights<T>& W, const T* __restrict__ G,
+                                            const T* __restrict__ aux, int i, int j, double* __restrict__ aleph) {
+  if (P.indicator == IND_ALL) return true;
+  if (P.indicator != IND_KXRCF) return false;
+  const T a = kxrcf2d<T>(P, W, G, aux, i, j);
+  if (aleph) aleph[(long long)j * P.nx + i] = double(a);
+  return a > T(1);
+}
+
+// Step 2.2 for one troubled cell (dimension by dimension): modified first
+// moments from the pre-modification moments of the x and y neighbours.
+template <int NV>
+__device__ __forceinline__ void modify2d_cell(const Prob& P, const double* __restrict__ U, double* __restrict__ Mod,
+                                              int i, int j) {
   const Img L = image(P, i - 1, j), R = image(P, i + 1, j), Bo = image(P, i, j - 1), Tp = image(P, i, j + 1);
   const long long o = (long long)j * P.pitch + i;
 #pragma unroll
@@ -240,6 +223,34 @@ __global__ void __launch_bounds__(TX * TY) flag2d_kernel(Prob P, Weights<T> W, c
     Mod[(long long)(v * 2 + 0) * P.plane + o] = MOD_WU * (uR - uL) + MOD_WV * (vL + vR);
     Mod[(long long)(v * 2 + 1) * P.plane + o] = MOD_WU * (uT - uB) + MOD_WV * (wB + wT);
   }
+}
+
+// Warp-aggregated append of flagged entries to a list (all 32 lanes take part).
+template <typename E>
+__device__ __forceinline__ void warp_append(bool flag, E entry, E* __restrict__ list, int* __restrict__ count) {
+  const unsigned act = __ballot_sync(0xffffffffu, flag);
+  if (!act) return;
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(act) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(count, __popc(act));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (flag) list[base + __popc(act & ((1u << lane) - 1u))] = entry;
+}
+
+template <typename T, int NV>
+__global__ void __launch_bounds__(TX * TY) flag2d_kernel(Prob P, Weights<T> W, const double* __restrict__ U,
+                                                        const T* __restrict__ G, const T* __restrict__ aux,
+                                                        uint8_t* __restrict__ mask, double* __restrict__ Mod,
+                                                        int* __restrict__ list, int* __restrict__ count,
+                                                        double* __restrict__ aleph) {
+  const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
+  const bool valid = i < P.nx && j < P.ny;
+  const bool flag = valid && flag2d_cell<T>(P, W, G, aux, i, j, aleph);
+  warp_append<int>(flag, j * P.nx + i, list, count);   // a warp is one tile row
+  if (!valid) return;
+  mask[(long long)j * P.nx + i] = flag ? 1 : 0;
+  if (flag) modify2d_cell<NV>(P, U, Mod, i, j);
 }
 
 template <typename T, int NV>
@@ -258,12 +269,12 @@ struct Rk {
   unsigned* status;
 };
 
-template <typename T, int NV>
-__global__ void __launch_bounds__(TX * TY) update2d_kernel(Prob P, const T* __restrict__ G, Rk S) {
-  __shared__ T xf[TY][TX + 1][4][NV];
-  __shared__ T yf[TY + 1][TX][4][NV];
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+// Step 3 for the TXV x TYV tile at (i0, j0): face fluxes into shared memory, then
+// quadrature, L(U) and the Runge-Kutta combination per cell.  tid = ty*TXV + tx.
+template <typename T, int NV, int TXV, int TYV>
+__device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict__ G, const Rk& S, int i0, int j0,
+                                              int tid, T (&xf)[TYV][TXV + 1][4][NV], T (&yf)[TYV + 1][TXV][4][NV]) {
+  const int tx = tid % TXV, ty = tid / TXV;
   const int i = i0 + tx, j = j0 + ty;
   const bool live = i < P.nx && j < P.ny;
   const Img self{i, j, 1, 1};
@@ -271,18 +282,19 @@ __global__ void __launch_bounds__(TX * TY) update2d_kernel(Prob P, const T* __re
   // call site, so that a face shared by two tiles gets bitwise the same flux
   // from both (the flux differences then telescope exactly in FP64).
   // xf[r][c] is the face left of cell (i0 + c, j0 + r); yf[r][c] the face below it.
-  constexpr int NXP = (TX + 1) * TY * 4, NYP = TX * (TY + 1) * 4;
-  for (int f = ty * TX + tx; f < NXP + NYP; f += TX * TY) {
+  constexpr int NXP = (TXV + 1) * TYV * 4, NYP = TXV * (TYV + 1) * 4;
+  __syncthreads();   // the shared arrays may still be read for a previous tile
+  for (int f = tid; f < NXP + NYP; f += TXV * TYV) {
     T uL[NV], uR[NV];
     if (f < NXP) {
-      const int l = f & 3, face = f >> 2, c = face % (TX + 1), r = face / (TX + 1);
+      const int l = f & 3, face = f >> 2, c = face % (TXV + 1), r = face / (TXV + 1);
       const int il = i0 + c - 1, jj = j0 + r;
       if (jj >= P.ny || il >= P.nx) continue;
       gl_state<T, NV>(P, G, image(P, il, jj), 3, l, uL);
       gl_state<T, NV>(P, G, image(P, il + 1, jj), 0, l, uR);
       num_flux<T, NV>(P, uL, uR, 0, xf[r][c][l]);
     } else {
-      const int g = f - NXP, k = g & 3, face = g >> 2, c = face % TX, r = face / TX;
+      const int g = f - NXP, k = g & 3, face = g >> 2, c = face % TXV, r = face / TXV;
       const int ii = i0 + c, jb = j0 + r - 1;
       if (ii >= P.nx || jb >= P.ny) continue;
       gl_state<T, NV>(P, G, image(P, ii, jb), k, 3, uL);
@@ -382,6 +394,13 @@ __global__ void __launch_bounds__(TX * TY) update2d_kernel(Prob P, const T* __re
 }
 
 template <typename T, int NV>
+__global__ void __launch_bounds__(TX * TY) update2d_kernel(Prob P, const T* __restrict__ G, Rk S) {
+  __shared__ T xf[TY][TX + 1][4][NV];
+  __shared__ T yf[TY + 1][TX][4][NV];
+  update2d_tile<T, NV, TX, TY>(P, G, S, blockIdx.x * TX, blockIdx.y * TY, threadIdx.y * TX + threadIdx.x, xf, yf);
+}
+
+template <typename T, int NV>
 void stage_t(const Prob& P, const Weights<T>& W, const Beta2<T>& Bt, const Bufs& B, const StageCall& S, cudaStream_t st) {
   const long long ncell = (long long)P.nx * P.ny;
   int* cnt = B.count + S.stage;
@@ -408,6 +427,189 @@ void stage_t(const Prob& P, const Weights<T>& W, const Beta2<T>& Bt, const Bufs&
   if (B.prof) B.prof->end(st);
 }
 
+// ---------------------------------------------------------------- batched problems
+//
+// One persistent cooperative launch per Runge-Kutta stage advances every problem
+// of a batch.  Work items of all problems form one list per phase (128-cell rows
+// for the per-cell phases, update tiles for the flux phase); the resident blocks
+// stride over it.  Phases are separated by a grid barrier whose wait is bounded:
+// past the limit the block records ST_TIMEOUT and continues (the host reports
+// HWENO_ETIMEOUT), so no wait can hang the GPU.
+
+constexpr unsigned long long BARRIER_SPIN_LIMIT = 1ull << 26;   // x >= 64 ns sleeps: seconds
+
+__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned long long spins = 0;
+      while (*vgen == gen) {
+        if (++spins > BARRIER_SPIN_LIMIT) {
+          atomicOr(status, ST_TIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+// problem owning work item it (first[] ascending)
+template <int FIELD>
+__device__ __forceinline__ int owner(const BProb* __restrict__ probs, int n, int it) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    const int f = FIELD == 0 ? probs[mid].rec_first : probs[mid].upd_first;
+    if (f <= it) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, int TXV, int TYV>
+__global__ void __launch_bounds__(TXV * TYV) batch_stage_kernel(BatchStage A, Weights<T> W, Beta2<T> B) {
+  static_assert(TXV * TYV == RB, "tiles and rows use the same block");
+  __shared__ T xf[TYV][TXV + 1][4][4];
+  __shared__ T yf[TYV + 1][TXV][4][4];
+  const int tid = threadIdx.x;
+  const unsigned nb = gridDim.x;
+  T* G = (T*)A.G;
+  T* aux = (T*)A.aux;
+  // CFL wave speeds of U^n (first stage, when the caller gives no dt)
+  if (A.stage == 0 && !A.dt_in) {
+    for (int it = blockIdx.x; it < A.n_rec; it += nb) {
+      const int p = owner<0>(A.probs, A.nprob, it);
+      const Prob P = A.probs[p].P;
+      const double* U = A.Uin + A.probs[p].uoff;
+      const int cell = (it - A.probs[p].rec_first) * RB + tid;
+      double sx = 0.0, sy = 0.0;
+      if (cell < P.nx * P.ny) {
+        const int i = cell % P.nx, j = cell / P.nx;
+        const double rho = U[sidx(P, 0, 0, i, j)];
+        const double mu = U[sidx(P, 1, 0, i, j)] / rho, nu = U[sidx(P, 2, 0, i, j)] / rho;
+        const double pr = (P.gamma - 1.0) * (U[sidx(P, 3, 0, i, j)] - 0.5 * rho * (mu * mu + nu * nu));
+        const double c = sqrt(P.gamma * pr / rho);
+        sx = fabs(mu) + c;
+        sy = fabs(nu) + c;
+        if (!(rho > 0.0) || !(pr > 0.0) || !isfinite(sx + sy)) sx = sy = INFINITY;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sx = fmax(sx, __shfl_down_sync(0xffffffffu, sx, o));
+        sy = fmax(sy, __shfl_down_sync(0xffffffffu, sy, o));
+      }
+      if ((tid & 31) == 0) {   // non-negative doubles order like their bit patterns
+        atomicMax(A.speeds + 2 * p, (unsigned long long)__double_as_longlong(sx));
+        atomicMax(A.speeds + 2 * p + 1, (unsigned long long)__double_as_longlong(sy));
+      }
+    }
+    grid_barrier(A.bar, nb, A.status);
+  }
+  // Step 1: every cell
+  for (int it = blockIdx.x; it < A.n_rec; it += nb) {
+    const int p = owner<0>(A.probs, A.nprob, it);
+    const BProb& Q = A.probs[p];
+    const int cell = (it - Q.rec_first) * RB + tid;
+    if (cell < Q.P.nx * Q.P.ny)
+      rec2d_cell<T, 4, false>(Q.P, W, B, A.Uin + Q.uoff, nullptr, nullptr, cell % Q.P.nx, cell / Q.P.nx, G + Q.goff,
+                              aux + Q.aoff);
+  }
+  grid_barrier(A.bar, nb, A.status);
+  // Steps 2.1-2.2
+  for (int it = blockIdx.x; it < A.n_rec; it += nb) {
+    const int p = owner<0>(A.probs, A.nprob, it);
+    const BProb& Q = A.probs[p];
+    const int cell = (it - Q.rec_first) * RB + tid;
+    const bool valid = cell < Q.P.nx * Q.P.ny;
+    const int i = cell % Q.P.nx, j = cell / Q.P.nx;
+    const bool flag = valid && flag2d_cell<T>(Q.P, W, G + Q.goff, aux + Q.aoff, i, j, nullptr);
+    warp_append<unsigned long long>(flag, ((unsigned long long)p << 32) | (unsigned)cell, A.list, A.count);
+    if (valid) {
+      A.mask[Q.coff + cell] = flag ? 1 : 0;
+      if (flag) modify2d_cell<4>(Q.P, A.Uin + Q.uoff, A.Mod + Q.moff, i, j);
+    }
+  }
+  grid_barrier(A.bar, nb, A.status);
+  // Step 2.3: troubled cells
+  {
+    const int n = *(volatile int*)A.count;
+    for (int t = blockIdx.x * RB + tid; t < n; t += nb * RB) {
+      const unsigned long long e = A.list[t];
+      const int p = (int)(e >> 32), cell = (int)(e & 0xffffffffu);
+      const BProb& Q = A.probs[p];
+      rec2d_cell<T, 4, true>(Q.P, W, B, A.Uin + Q.uoff, A.mask + Q.coff, A.Mod + Q.moff, cell % Q.P.nx,
+                             cell / Q.P.nx, G + Q.goff, nullptr);
+    }
+  }
+  grid_barrier(A.bar, nb, A.status);
+  // Step 3: fluxes, quadrature, L, Runge-Kutta
+  for (int it = blockIdx.x; it < A.n_upd; it += nb) {
+    const int p = owner<1>(A.probs, A.nprob, it);
+    const BProb& Q = A.probs[p];
+    double dt;
+    if (A.dt_in) {
+      dt = A.dt_in[p];
+    } else {
+      const double ax = __longlong_as_double((long long)A.speeds[2 * p]);
+      const double ay = __longlong_as_double((long long)A.speeds[2 * p + 1]);
+      const double r = ax / Q.P.dx + ay / Q.P.dy;
+      dt = (r > 0.0 && isfinite(r)) ? A.cfl / r : 0.0;
+    }
+    const int t = it - Q.upd_first;
+    if (A.stage == 0 && t == 0 && tid == 0) A.dt_out[p] = dt;
+    Rk S{A.Uin + Q.uoff, A.Un + Q.uoff, A.Uout + Q.uoff, A.mask + Q.coff, A.Mod + Q.moff,
+         A.maskN ? A.maskN + Q.coff : nullptr, A.ModN ? A.ModN + Q.moff : nullptr, dt, A.cA, A.cB,
+         nullptr, nullptr, A.pstatus + p};
+    update2d_tile<T, 4, TXV, TYV>(Q.P, G + Q.goff, S, (t % Q.tiles_x) * TXV, (t / Q.tiles_x) * TYV, tid, xf, yf);
+  }
+}
+
+template <typename T, int TXV, int TYV>
+cudaError_t launch_batch(const Weights<T>& W, const Beta2<T>& Bt, const BatchStage& S, int nsm, cudaStream_t st) {
+  auto kern = batch_stage_kernel<T, TXV, TYV>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, RB, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nsm * per_sm);
+  cfg.blockDim = dim3(RB);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, S, W, Bt);
+}
+
+}  // namespace
+
+cudaError_t run_batch_stage(const HostTabs& T, int fp32, int tile_variant, const BatchStage& S, int nsm,
+                            cudaStream_t st) {
+  // tile shapes of the update phase (all 128 threads): 0: 32x4, 1: 16x8, 2: 64x2
+  if (fp32) {
+    if (tile_variant == 1) return launch_batch<float, 16, 8>(T.wf, T.b2f, S, nsm, st);
+    if (tile_variant == 2) return launch_batch<float, 64, 2>(T.wf, T.b2f, S, nsm, st);
+    return launch_batch<float, 32, 4>(T.wf, T.b2f, S, nsm, st);
+  }
+  if (tile_variant == 1) return launch_batch<double, 16, 8>(T.wd, T.b2d, S, nsm, st);
+  if (tile_variant == 2) return launch_batch<double, 64, 2>(T.wd, T.b2d, S, nsm, st);
+  return launch_batch<double, 32, 4>(T.wd, T.b2d, S, nsm, st);
+}
+
+namespace {
 }  // namespace
 
 void run_stage_2d(const Prob& P, const HostTabs& T, int fp32, const Bufs& B, const StageCall& S, cudaStream_t st) {

@@ -34,6 +34,25 @@ struct hweno_s {
   double* host_buf = nullptr;    // pinned: reduction results + status
   hw::Prof prof;                 // per-kernel event timing (hweno_profile)
   std::string err;
+  // batch mode (hweno_create_batch): many independent 2D Euler problems
+  bool batch = false;
+  int nprob = 0;
+  std::vector<hw::BProb> probs;  // host copy of the descriptors
+  hw::BProb* dprobs = nullptr;
+  long long tot_cells = 0;
+  int n_rec = 0, n_upd = 0;
+  int tile_variant = 0;
+  unsigned long long* blist = nullptr;
+  unsigned long long* speeds = nullptr;
+  double* dt_out = nullptr;
+  unsigned* bar = nullptr;
+  unsigned* pstatus = nullptr;   // per-problem status bits (device)
+  std::vector<unsigned> last_pstatus;   // per-problem bits of the last reported failure
+  cudaGraphExec_t graphs[3] = {nullptr, nullptr, nullptr};   // one per state rotation
+  const double* graph_dt = nullptr;
+  double graph_cfl = -1.0;
+  int graph_variant = -1;
+  bool use_graph = true;
 };
 
 namespace {
@@ -72,8 +91,6 @@ void build_tables(hweno_s* h) {
   }
   wd.eps = 1e-10;
   wf.eps = 1e-10f;
-  wd.h2 = h->P.dx * h->P.dx;       // h^{(l+1)/3}, l = 5
-  wf.h2 = (float)wd.h2;
   auto coef = [&](int l, long double& a, long double& b) {
     if (h->g.beta_of_q) { a = 1.0L; b = 0.0L; return; }
     a = S[l] / g[l - 1];
@@ -129,7 +146,19 @@ hweno_status validate(const hweno_grid* g, const hweno_bc* bc, double gamma, std
   return HWENO_OK;
 }
 
+void drop_graphs(hweno_s* h) {
+  for (int k = 0; k < 3; ++k)
+    if (h->graphs[k]) { cudaGraphExecDestroy(h->graphs[k]); h->graphs[k] = nullptr; }
+}
+
 void free_all(hweno_s* h) {
+  drop_graphs(h);
+  cudaFree(h->dprobs);
+  cudaFree(h->blist);
+  cudaFree(h->speeds);
+  cudaFree(h->dt_out);
+  cudaFree(h->bar);
+  cudaFree(h->pstatus);
   for (int k = 0; k < 3; ++k) cudaFree(h->U[k]);
   cudaFree(h->B.G);
   cudaFree(h->B.aux);
@@ -150,14 +179,26 @@ hweno_status check_status(hweno_t h) {
   CK(h, cudaStreamSynchronize(h->stream));
   unsigned st;
   memcpy(&st, h->host_buf + 8, sizeof st);
+  if (h->batch) {   // per-problem bits
+    std::vector<unsigned> ps(h->nprob);
+    CK(h, cudaMemcpy(ps.data(), h->pstatus, h->nprob * sizeof(unsigned), cudaMemcpyDeviceToHost));
+    unsigned any = 0;
+    for (unsigned v : ps) any |= v;
+    if (any) {
+      h->last_pstatus = ps;
+      CK(h, cudaMemsetAsync(h->pstatus, 0, h->nprob * sizeof(unsigned), h->stream));
+    }
+    st |= any;
+  }
   if (st != 0) {
     CK(h, cudaMemsetAsync(h->B.status, 0, sizeof(unsigned), h->stream));
     if (h->stepped) h->cur = h->prev;
     h->stepped = false;
-    char buf[160];
-    snprintf(buf, sizeof buf, "last step produced a non-physical state (status 0x%x: %s%s); rolled back", st,
-             (st & hw::ST_NONFINITE) ? "non-finite " : "", (st & hw::ST_NONPOSITIVE) ? "rho<=0 or p<=0" : "");
-    return fail(h, HWENO_ENONPHYSICAL, buf);
+    char buf[200];
+    snprintf(buf, sizeof buf, "last step produced a non-physical state or timed out (status 0x%x: %s%s%s); rolled back",
+             st, (st & hw::ST_NONFINITE) ? "non-finite " : "", (st & hw::ST_NONPOSITIVE) ? "rho<=0 or p<=0 " : "",
+             (st & hw::ST_TIMEOUT) ? "grid barrier wait limit" : "");
+    return fail(h, (st & hw::ST_TIMEOUT) ? HWENO_ETIMEOUT : HWENO_ENONPHYSICAL, buf);
   }
   return HWENO_OK;
 }
@@ -396,4 +437,279 @@ hweno_status hweno_profile_read(hweno_t h, double* ms, int* launches, int nkinds
   return HWENO_OK;
 }
 
+// ---------------------------------------------------------------- batches
+
+namespace {
+
+// Descriptors of every problem for the current update-tile variant.
+void layout_batch(hweno_t h) {
+  static const int TXS[3] = {32, 16, 64}, TYS[3] = {4, 8, 2};
+  const int tx = TXS[h->tile_variant], ty = TYS[h->tile_variant];
+  int rec = 0, upd = 0;
+  for (auto& q : h->probs) {
+    q.rec_first = rec;
+    q.upd_first = upd;
+    q.tiles_x = (q.P.nx + tx - 1) / tx;
+    rec += (q.P.nx * q.P.ny + 127) / 128;
+    upd += q.tiles_x * ((q.P.ny + ty - 1) / ty);
+  }
+  h->n_rec = rec;
+  h->n_upd = upd;
+}
+
+size_t batch_count(const hweno_s* h, int k) {
+  const Prob& P = h->probs[k].P;
+  return (size_t)P.nvar * P.nmom * P.nx * P.ny;
+}
+
+hweno_status batch_graph(hweno_t h, int a, const double* dt_in, double cfl, cudaGraphExec_t* out);
+
+}  // namespace
+
+hweno_status hweno_create_batch(const hweno_grid* grids, const hweno_bc* bcs, int n, double gamma, hweno_t* out) {
+  if (!out || !grids || !bcs || n < 1) return HWENO_EINVAL;
+  *out = nullptr;
+  for (int k = 0; k < n; ++k) {
+    std::string why;
+    if (validate(&grids[k], &bcs[k], gamma, why) != HWENO_OK) {
+      fprintf(stderr, "hweno_create_batch: problem %d: %s\n", k, why.c_str());
+      return HWENO_EINVAL;
+    }
+    const hweno_grid& g = grids[k];
+    if (g.dim != 2 || g.eq != HWENO_EULER || g.precision != grids[0].precision ||
+        g.indicator != grids[0].indicator || g.beta_of_q != grids[0].beta_of_q ||
+        memcmp(g.gamma_bar, grids[0].gamma_bar, sizeof g.gamma_bar) != 0) {
+      fprintf(stderr, "hweno_create_batch: problem %d: batches hold 2D Euler problems sharing precision, "
+              "indicator and linear weights\n", k);
+      return HWENO_EINVAL;
+    }
+  }
+  hweno_s* h = new hweno_s();
+  h->batch = true;
+  h->nprob = n;
+  h->g = grids[0];
+  h->bc = bcs[0];
+  h->gamma = gamma;
+  h->fp32 = grids[0].precision;
+  if (cudaGetDevice(&h->dev) != cudaSuccess) { delete h; return HWENO_ECUDA; }
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->dev);
+  long long tu = 0, tg = 0, ta = 0, tm = 0, tc = 0;
+  for (int k = 0; k < n; ++k) {
+    hw::BProb q{};
+    Prob& P = q.P;
+    const hweno_grid& g = grids[k];
+    P.nx = g.nx; P.ny = g.ny;
+    P.pitch = (P.nx + 31) / 32 * 32; P.plane = (long long)P.ny * P.pitch;
+    P.gpitch = P.pitch; P.gplane = P.plane;
+    P.nvar = 4; P.nmom = 3; P.eq = HWENO_EULER; P.indicator = g.indicator;
+    P.bc[0] = bcs[k].xlo; P.bc[1] = bcs[k].xhi; P.bc[2] = bcs[k].ylo; P.bc[3] = bcs[k].yhi;
+    P.dx = (g.x1 - g.x0) / P.nx; P.dy = (g.y1 - g.y0) / P.ny;
+    P.gamma = gamma; P.adv_a = 0.0; P.adv_b = 0.0; P.nsm = nsm;
+    q.uoff = tu; q.goff = tg; q.aoff = ta; q.moff = tm; q.coff = tc;
+    tu += 12 * P.plane; tg += 64 * P.gplane; ta += 5 * P.gplane; tm += 8 * P.plane; tc += (long long)P.nx * P.ny;
+    h->probs.push_back(q);
+  }
+  h->tot_cells = tc;
+  h->P = h->probs[0].P;
+  build_tables(h);
+  layout_batch(h);
+  const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
+  bool ok = true;
+  for (int k = 0; k < 3; ++k) ok = ok && cudaMalloc(&h->U[k], tu * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->B.G, tg * esz) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->B.aux, ta * esz) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->ModN, tm * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->ModK, tm * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->mask3, 3 * tc) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->blist, tc * sizeof(unsigned long long)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->B.count, 4 * sizeof(int)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->B.status, sizeof(unsigned)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->speeds, 2 * n * sizeof(unsigned long long)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->dt_out, n * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->bar, 2 * sizeof(unsigned)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->pstatus, n * sizeof(unsigned)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->dprobs, n * sizeof(hw::BProb)) == cudaSuccess;
+  ok = ok && cudaMallocHost(&h->host_buf, 16 * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    free_all(h);
+    delete h;
+    fprintf(stderr, "hweno_create_batch: device allocation failed\n");
+    return HWENO_ENOMEM;
+  }
+  cudaMemcpy(h->dprobs, h->probs.data(), n * sizeof(hw::BProb), cudaMemcpyHostToDevice);
+  cudaMemset(h->B.status, 0, sizeof(unsigned));
+  cudaMemset(h->mask3, 0, 3 * tc);
+  cudaMemset(h->bar, 0, 2 * sizeof(unsigned));
+  cudaMemset(h->pstatus, 0, n * sizeof(unsigned));
+  cudaMemset(h->dt_out, 0, n * sizeof(double));
+  for (int k = 0; k < 3; ++k) cudaMemset(h->U[k], 0, tu * sizeof(double));
+  if (cudaDeviceSynchronize() != cudaSuccess) { free_all(h); delete h; return HWENO_ECUDA; }
+  *out = h;
+  return HWENO_OK;
+}
+
+hweno_status hweno_batch_set_tile(hweno_t h, int variant) {
+  if (!h || !h->batch || variant < 0 || variant > 2) return HWENO_EINVAL;
+  if (variant == h->tile_variant) return HWENO_OK;
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->tile_variant = variant;
+  layout_batch(h);
+  CK(h, cudaMemcpy(h->dprobs, h->probs.data(), h->nprob * sizeof(hw::BProb), cudaMemcpyHostToDevice));
+  drop_graphs(h);
+  return HWENO_OK;
+}
+
+hweno_status hweno_batch_set_moments(hweno_t h, int k, const double* m, size_t count, int on_device) {
+  if (!h || !h->batch || k < 0 || k >= h->nprob) return HWENO_EINVAL;
+  if (!m || count != batch_count(h, k)) return fail(h, HWENO_EINVAL, "batch_set_moments: count must be 12*ny*nx");
+  const Prob& P = h->probs[k].P;
+  CK(h, cudaMemcpy2DAsync(h->U[h->cur] + h->probs[k].uoff, P.pitch * sizeof(double), m, P.nx * sizeof(double),
+                          P.nx * sizeof(double), (size_t)12 * P.ny,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaMemsetAsync(h->B.status, 0, sizeof(unsigned), h->stream));
+  h->have_state = true;
+  h->stepped = false;
+  if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
+  return HWENO_OK;
+}
+
+hweno_status hweno_batch_get_moments(hweno_t h, int k, double* m, size_t count, int on_device) {
+  if (!h || !h->batch || k < 0 || k >= h->nprob) return HWENO_EINVAL;
+  if (!m || count != batch_count(h, k)) return fail(h, HWENO_EINVAL, "batch_get_moments: count must be 12*ny*nx");
+  if (!on_device) {
+    const hweno_status s = check_status(h);
+    if (s != HWENO_OK) return s;
+  }
+  const Prob& P = h->probs[k].P;
+  CK(h, cudaMemcpy2DAsync(m, P.nx * sizeof(double), h->U[h->cur] + h->probs[k].uoff, P.pitch * sizeof(double),
+                          P.nx * sizeof(double), (size_t)12 * P.ny,
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
+  return HWENO_OK;
+}
+
+hweno_status hweno_batch_troubled_mask(hweno_t h, int k, unsigned char* mask, size_t count) {
+  if (!h || !h->batch || k < 0 || k >= h->nprob) return HWENO_EINVAL;
+  const Prob& P = h->probs[k].P;
+  const size_t nc = (size_t)P.nx * P.ny;
+  if (!mask || count != 3 * nc) return fail(h, HWENO_EINVAL, "batch_troubled_mask: count must be 3*ny*nx");
+  for (int st = 0; st < 3; ++st)
+    CK(h, cudaMemcpyAsync(mask + st * nc, h->mask3 + st * h->tot_cells + h->probs[k].coff, nc,
+                          cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return HWENO_OK;
+}
+
+hweno_status hweno_batch_status(hweno_t h, unsigned* bits, int n) {
+  if (!h || !h->batch || !bits || n != h->nprob) return HWENO_EINVAL;
+  for (int k = 0; k < n; ++k) bits[k] = h->last_pstatus.empty() ? 0u : h->last_pstatus[k];
+  return HWENO_OK;
+}
+
+int hweno_batch_uses_graph(hweno_t h) {
+  if (!h || !h->batch) return -1;
+  return (h->use_graph && h->graphs[h->prev] != nullptr) ? 1 : 0;
+}
+
+hweno_status hweno_batch_dt(hweno_t h, double* dt, int n) {
+  if (!h || !h->batch || !dt || n != h->nprob) return HWENO_EINVAL;
+  CK(h, cudaMemcpyAsync(dt, h->dt_out, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return HWENO_OK;
+}
+
+hweno_status hweno_step_batch(hweno_t h, const double* dt_device, double cfl) {
+  if (!h || !h->batch) return HWENO_EINVAL;
+  if (!h->have_state) return fail(h, HWENO_ESTATE, "step_batch: no moments set");
+  if (!dt_device && !(cfl > 0.0)) return fail(h, HWENO_EINVAL, "step_batch: need dt_device or cfl > 0");
+  const int a = h->cur;
+  if (h->graph_dt != dt_device || h->graph_cfl != cfl || h->graph_variant != h->tile_variant) {
+    drop_graphs(h);
+    h->graph_dt = dt_device;
+    h->graph_cfl = cfl;
+    h->graph_variant = h->tile_variant;
+  }
+  if (h->use_graph && !h->graphs[a]) {
+    const hweno_status s = batch_graph(h, a, dt_device, cfl, &h->graphs[a]);
+    if (s != HWENO_OK) {     // capture unsupported here: launch directly from now on
+      h->use_graph = false;
+      cudaGetLastError();
+    }
+  }
+  if (h->use_graph && h->graphs[a]) {
+    CK(h, cudaGraphLaunch(h->graphs[a], h->stream));
+  } else {
+    hw::BatchStage S{};
+    const int b = (a + 1) % 3, c = (a + 2) % 3;
+    const long long T = h->tot_cells;
+    CK(h, cudaMemsetAsync(h->speeds, 0, 2 * h->nprob * sizeof(unsigned long long), h->stream));
+    CK(h, cudaMemsetAsync(h->B.count, 0, 4 * sizeof(int), h->stream));
+    for (int st = 0; st < 3; ++st) {
+      S.probs = h->dprobs; S.nprob = h->nprob; S.n_rec = h->n_rec; S.n_upd = h->n_upd;
+      S.G = h->B.G; S.aux = h->B.aux; S.list = h->blist; S.count = h->B.count + st;
+      S.speeds = h->speeds; S.dt_in = dt_device; S.dt_out = h->dt_out; S.cfl = cfl;
+      S.status = h->B.status; S.pstatus = h->pstatus; S.bar = h->bar; S.stage = st;
+      S.Un = h->U[a];
+      if (st == 0) { S.Uin = h->U[a]; S.Uout = h->U[b]; S.cA = 0.0; S.cB = 1.0; S.Mod = h->ModN; S.ModN = nullptr;
+                     S.mask = h->mask3; S.maskN = nullptr; }
+      if (st == 1) { S.Uin = h->U[b]; S.Uout = h->U[c]; S.cA = 0.75; S.cB = 0.25; S.Mod = h->ModK; S.ModN = h->ModN;
+                     S.mask = h->mask3 + T; S.maskN = h->mask3; }
+      if (st == 2) { S.Uin = h->U[c]; S.Uout = h->U[b]; S.cA = 1.0 / 3.0; S.cB = 2.0 / 3.0; S.Mod = h->ModK;
+                     S.ModN = h->ModN; S.mask = h->mask3 + 2 * T; S.maskN = h->mask3; }
+      CK(h, cudaMemsetAsync(h->bar, 0, sizeof(unsigned), h->stream));
+      CK(h, hw::run_batch_stage(h->T, h->fp32, h->tile_variant, S, h->P.nsm, h->stream));
+    }
+  }
+  h->prev = a;
+  h->cur = (a + 1) % 3;
+  h->stepped = true;
+  return HWENO_OK;
+}
+
 }  // extern "C"
+
+namespace {
+
+// Capture one batched step (memsets + three cooperative stage launches) for the
+// state rotation starting at buffer a.
+hweno_status batch_graph(hweno_t h, int a, const double* dt_in, double cfl, cudaGraphExec_t* out) {
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return HWENO_ECUDA;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  const int b = (a + 1) % 3, c = (a + 2) % 3;
+  const long long T = h->tot_cells;
+  if (e == cudaSuccess) {
+    cudaMemsetAsync(h->speeds, 0, 2 * h->nprob * sizeof(unsigned long long), cs);
+    cudaMemsetAsync(h->B.count, 0, 4 * sizeof(int), cs);
+    for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
+      hw::BatchStage S{};
+      S.probs = h->dprobs; S.nprob = h->nprob; S.n_rec = h->n_rec; S.n_upd = h->n_upd;
+      S.G = h->B.G; S.aux = h->B.aux; S.list = h->blist; S.count = h->B.count + st;
+      S.speeds = h->speeds; S.dt_in = dt_in; S.dt_out = h->dt_out; S.cfl = cfl;
+      S.status = h->B.status; S.pstatus = h->pstatus; S.bar = h->bar; S.stage = st; S.Un = h->U[a];
+      if (st == 0) { S.Uin = h->U[a]; S.Uout = h->U[b]; S.cA = 0.0; S.cB = 1.0; S.Mod = h->ModN; S.ModN = nullptr;
+                     S.mask = h->mask3; S.maskN = nullptr; }
+      if (st == 1) { S.Uin = h->U[b]; S.Uout = h->U[c]; S.cA = 0.75; S.cB = 0.25; S.Mod = h->ModK; S.ModN = h->ModN;
+                     S.mask = h->mask3 + T; S.maskN = h->mask3; }
+      if (st == 2) { S.Uin = h->U[c]; S.Uout = h->U[b]; S.cA = 1.0 / 3.0; S.cB = 2.0 / 3.0; S.Mod = h->ModK;
+                     S.ModN = h->ModN; S.mask = h->mask3 + 2 * T; S.maskN = h->mask3; }
+      cudaMemsetAsync(h->bar, 0, sizeof(unsigned), cs);
+      e = hw::run_batch_stage(h->T, h->fp32, h->tile_variant, S, h->P.nsm, cs);
+    }
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    return fail(h, HWENO_ECUDA, std::string("batch graph: ") + cudaGetErrorString(e));
+  }
+  return HWENO_OK;
+}
+
+}  // namespace

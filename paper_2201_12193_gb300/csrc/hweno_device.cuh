@@ -46,7 +46,6 @@ struct Weights {
   T sg[4];       // S_l / g_l
   T s1g[4];      // S_{l-1} / g_l  (0 for l = 1)
   T eps;         // 1e-10 of eqs. (w1_-LR), (non-linear-weight)
-  T h2;          // h^{(l+1)/3} with l = 5, h = dx  (eq. (KXRCF))
 };
 
 // Rows of the smoothness indicators beta_2..beta_4 for the run-time weights,

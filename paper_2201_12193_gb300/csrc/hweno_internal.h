@@ -84,6 +84,49 @@ struct StageCall {
 };
 
 void run_stage_1d(const Prob& P, const HostTabs& T, int fp32, const Bufs& B, const StageCall& S, cudaStream_t st);
+
+// ---------------------------------------------------------------- batched 2D problems
+// One problem of a batch: its description and the offsets of its arrays inside
+// the batch-wide buffers (elements of the respective buffer type).
+struct BProb {
+  Prob P;
+  long long uoff;     // state buffers (doubles)
+  long long goff;     // point values (elements of the compute precision)
+  long long aoff;     // KXRCF partials
+  long long moff;     // modified first moments (doubles)
+  long long coff;     // cells before this problem (masks, troubled list)
+  int rec_first;      // first reconstruction item (128 cells each)
+  int upd_first;      // first update tile
+  int tiles_x;        // update tiles per row
+};
+
+// Buffers and coefficients of one batched stage launch.
+struct BatchStage {
+  const BProb* probs;     // device array
+  int nprob, n_rec, n_upd;
+  const double* Uin; const double* Un; double* Uout;
+  void* G; void* aux;
+  double* Mod;            // this stage's modified first moments (first stage: the kept copy)
+  const double* ModN;     // first-stage modified first moments (stages 2, 3), else nullptr
+  uint8_t* mask;          // this stage's flags (batch cell order)
+  const uint8_t* maskN;   // first-stage flags (stages 2, 3), else nullptr
+  unsigned long long* list;   // troubled (problem << 32 | cell)
+  int* count;
+  unsigned long long* speeds; // per problem: max a_x, max a_y as FP64 bit patterns
+  const double* dt_in;    // per-problem dt from the caller, or nullptr (CFL)
+  double* dt_out;         // per-problem dt used (written in the first stage)
+  double cfl, cA, cB;
+  int stage;
+  unsigned* status;       // ST_TIMEOUT of the grid barrier
+  unsigned* pstatus;      // per problem: ST_NONFINITE / ST_NONPOSITIVE of its new state
+  unsigned* bar;          // grid barrier {arrived, generation}
+};
+
+// Launch one batched stage as a single persistent cooperative kernel (grid =
+// resident blocks); returns the CUDA error of the launch.
+cudaError_t run_batch_stage(const HostTabs& T, int fp32, int tile_variant, const BatchStage& S, int nsm,
+                            cudaStream_t st);
+constexpr unsigned ST_TIMEOUT = 4u;   // a bounded grid-barrier wait gave up
 void run_stage_2d(const Prob& P, const HostTabs& T, int fp32, const Bufs& B, const StageCall& S, cudaStream_t st);
 
 // Reductions over the cell averages (FP64): maximum wave speeds per direction

@@ -66,6 +66,16 @@ def lib():
         L.hweno_profile_read.argtypes = [H, D, ctypes.POINTER(ctypes.c_int), ctypes.c_int]
         L.hweno_max_dt_noalloc.argtypes = [ctypes.POINTER(Grid), ctypes.c_double, ctypes.c_void_p, ctypes.c_double,
                                            ctypes.c_void_p, ctypes.c_void_p]
+        L.hweno_create_batch.argtypes = [ctypes.POINTER(Grid), ctypes.POINTER(Bc), ctypes.c_int, ctypes.c_double,
+                                         ctypes.POINTER(H)]
+        L.hweno_batch_set_moments.argtypes = [H, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+        L.hweno_batch_get_moments.argtypes = [H, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+        L.hweno_step_batch.argtypes = [H, ctypes.c_void_p, ctypes.c_double]
+        L.hweno_batch_dt.argtypes = [H, D, ctypes.c_int]
+        L.hweno_batch_troubled_mask.argtypes = [H, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]
+        L.hweno_batch_set_tile.argtypes = [H, ctypes.c_int]
+        L.hweno_batch_uses_graph.argtypes = [H]
+        L.hweno_batch_status.argtypes = [H, ctypes.POINTER(ctypes.c_uint), ctypes.c_int]
         L.hweno_last_error.argtypes = [H]
         L.hweno_last_error.restype = ctypes.c_char_p
         L.hweno_version.restype = ctypes.c_int
@@ -235,3 +245,104 @@ def max_dt_noalloc(grid, gamma, m, cfl, out, stream=None):
                                     ctypes.c_void_p(o), ctypes.c_void_p(s))
     if st != 0:
         raise HwenoError(st, "hweno_max_dt_noalloc failed (see stderr)")
+
+
+def _grid_struct(dim, nx, ny, x0, x1, y0, y1, eq, adv=(0.0, 0.0), precision="fp64", indicator="kxrcf",
+                 gamma_bar=(1.0, 10.0, 100.0, 1000.0), beta_of_q=False):
+    g = Grid()
+    g.dim, g.nx, g.ny = dim, nx, ny
+    g.x0, g.x1, g.y0, g.y1 = x0, x1, y0, y1
+    g.eq = EQ[eq]
+    g.adv_a, g.adv_b = adv
+    g.precision = PREC[precision]
+    g.indicator = IND[indicator]
+    for k in range(4):
+        g.gamma_bar[k] = gamma_bar[k]
+    g.beta_of_q = int(bool(beta_of_q))
+    return g
+
+
+class BatchSolver:
+    """Independent 2D Euler problems advanced together (hweno_create_batch)."""
+
+    def __init__(self, problems, precision="fp64", indicator="kxrcf", gamma_bar=(1.0, 10.0, 100.0, 1000.0),
+                 beta_of_q=False, gamma=1.4, stream=None):
+        n = len(problems)
+        grids = (Grid * n)()
+        bcs = (Bc * n)()
+        for k, p in enumerate(problems):
+            grids[k] = _grid_struct(2, p.nx, p.ny, p.x0, p.x1, p.y0, p.y1, "euler", precision=precision,
+                                    indicator=indicator, gamma_bar=gamma_bar, beta_of_q=beta_of_q)
+            bcs[k] = Bc(*[BC[b] for b in p.bc])
+        h = ctypes.c_void_p()
+        st = lib().hweno_create_batch(grids, bcs, n, float(gamma), ctypes.byref(h))
+        if st != 0:
+            raise HwenoError(st, "hweno_create_batch failed (see stderr)")
+        self._h = h
+        self.n = n
+        self.shapes = [(4, 3, p.ny, p.nx) for p in problems]
+        if stream is not None:
+            s = getattr(stream, "cuda_stream", stream) or 0
+            self._check(lib().hweno_set_stream(self._h, ctypes.c_void_p(s)))
+
+    def _check(self, st):
+        if st != 0:
+            raise HwenoError(st, lib().hweno_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().hweno_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_moments(self, k, m):
+        if isinstance(m, np.ndarray):
+            m = np.ascontiguousarray(m)
+        addr, dev, n = _ptr(_f64(m))
+        self._check(lib().hweno_batch_set_moments(self._h, k, ctypes.c_void_p(addr), n, dev))
+
+    def get_moments(self, k, out=None):
+        if out is None:
+            out = np.empty(self.shapes[k], np.float64)
+        addr, dev, n = _ptr(_f64(out))
+        self._check(lib().hweno_batch_get_moments(self._h, k, ctypes.c_void_p(addr), n, dev))
+        return out
+
+    def step(self, dt=None, cfl=0.6):
+        """dt: None (per-problem CFL dt) or a CUDA float64 tensor of n dts."""
+        p = 0
+        if dt is not None:
+            p, dev, cnt = _ptr(_f64(dt))
+            if not dev or cnt != self.n:
+                raise ValueError("dt must be a CUDA float64 tensor with one entry per problem")
+        self._check(lib().hweno_step_batch(self._h, ctypes.c_void_p(p), float(cfl)))
+
+    def dts(self):
+        out = np.empty(self.n, np.float64)
+        self._check(lib().hweno_batch_dt(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.n))
+        return out
+
+    def troubled_mask(self, k):
+        out = np.empty((3,) + self.shapes[k][2:], np.uint8)
+        self._check(lib().hweno_batch_troubled_mask(self._h, k, ctypes.c_void_p(out.ctypes.data), out.size))
+        return out
+
+    def set_tile(self, variant):
+        self._check(lib().hweno_batch_set_tile(self._h, int(variant)))
+
+    def uses_graph(self):
+        return lib().hweno_batch_uses_graph(self._h) == 1
+
+    def failed_problems(self):
+        """Indices of the problems that made the last reported step non-physical."""
+        bits = (ctypes.c_uint * self.n)()
+        self._check(lib().hweno_batch_status(self._h, bits, self.n))
+        return [k for k in range(self.n) if bits[k]]
+
+    def sync(self):
+        self._check(lib().hweno_sync(self._h))

@@ -221,7 +221,7 @@ def four_quadrant_2d(n=2048, seed=0, ny=None):
                    meta={"rho": rho.tolist(), "mu": mu.tolist(), "nu": nu.tolist(), "p": p.tolist()})
 
 
-def vortex_2d(n=128, seed=0, L=10.0):
+def vortex_2d(n=128, seed=0, L=10.0, npts=8):
     """Isentropic vortex of seeded strength U[1,5] and centre uniform in [0,L]^2,
     mean flow (1,1), periodic; the distance to the centre is the periodic
     (minimum-image) one."""
@@ -240,7 +240,7 @@ def vortex_2d(n=128, seed=0, L=10.0):
         T = 1.0 - (g - 1.0) * eps * eps / (8.0 * g * math.pi ** 2) * e * e
         rho = T ** (1.0 / (g - 1.0))
         return prim_to_cons_2d(rho, mu, nu, rho ** g)
-    m = moments_2d(f, 0.0, L, 0.0, L, n, n)
+    m = moments_2d(f, 0.0, L, 0.0, L, n, n, npts=npts)
     return Problem("vortex_2d", 2, n, n, 0.0, L, 0.0, L, "euler", ("periodic",) * 4, m, seed=seed,
                    meta={"eps": eps, "xc": xc, "yc": yc})
 
@@ -271,3 +271,17 @@ def batch_sizes(seed=0, count=256, choices=(64, 128, 256, 512)):
     """Grid sizes of a batch of independent problems, uniform in choices."""
     rng = np.random.default_rng(seed)
     return [int(x) for x in rng.choice(np.asarray(choices), size=count)]
+
+
+def batch_problems(count=256, seed=0, choices=(64, 128, 256, 512), npts=4):
+    """Independent problems of a batch: sizes uniform in choices; even entries
+    four-quadrant Riemann data on [0,1]^2 (transmissive), odd entries an isentropic
+    vortex on periodic [0,10]^2 (Gauss-Legendre order npts per direction)."""
+    sizes = batch_sizes(seed, count, choices)
+    out = []
+    for k, n in enumerate(sizes):
+        if k % 2 == 0:
+            out.append(four_quadrant_2d(n, seed=seed * 100003 + k))
+        else:
+            out.append(vortex_2d(n, seed=seed * 100003 + k, npts=npts))
+    return out
