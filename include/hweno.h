@@ -60,7 +60,7 @@ typedef enum {
 
 typedef enum { HWENO_ADVECTION = 0, HWENO_BURGERS = 1, HWENO_EULER = 2 } hweno_eq;
 typedef enum { HWENO_BC_PERIODIC = 0, HWENO_BC_TRANSMISSIVE = 1 } hweno_bc_kind;
-typedef enum { HWENO_IND_NONE = 0, HWENO_IND_KXRCF = 1, HWENO_IND_ALL = 2 } hweno_indicator;
+typedef enum { HWENO_IND_NONE = 0, HWENO_IND_KXRCF = 1, HWENO_IND_ALL = 2, HWENO_IND_MLP = 3 } hweno_indicator;
 
 /* Uniform mesh and scheme options.
  *   dim 1 or 2; nx, ny >= 4 (ny ignored in 1D); 2D cells must be square
@@ -71,7 +71,8 @@ typedef enum { HWENO_IND_NONE = 0, HWENO_IND_KXRCF = 1, HWENO_IND_ALL = 2 } hwen
  *   and quadrature with FP64 state, FP64 Runge-Kutta accumulation and FP64
  *   differences of the face fluxes in the cell-average equation.
  *   indicator: HWENO_IND_KXRCF is the scheme (HWENO6-M5-I); NONE gives HWENO6
- *   (no modification); ALL gives HWENO6-M5-NI (every cell modified) (Sec. 3).
+ *   (no modification); ALL gives HWENO6-M5-NI (every cell modified) (Sec. 3);
+ *   MLP: the learned indicator with KXRCF fallback (see below; 2D Euler).
  *   gamma_bar: positive linear-weight seeds of eq. (linear-weight)
  *   (gamma_{l1,l2} = gamma_bar[l1-1] / sum_{l<=l2} gamma_bar[l-1]); the paper
  *   uses {1, 10, 100, 1000}.
@@ -142,6 +143,65 @@ hweno_status hweno_sync(hweno_t h);
  *   aleph out (may be NULL): KXRCF values [ny][nx] doubles.
  * Asynchronous on the handle's stream. */
 hweno_status hweno_rhs(hweno_t h, const double* U, double* Umod, double* L, unsigned char* mask, double* aleph);
+
+/* ---------------------------------------------------------------- learned indicator
+ * (no counterpart in the paper: a small network trained on the paper's KXRCF
+ * decisions, with KXRCF kept as the fallback and the judge)
+ * Network: 108 -> 64 -> 64 -> 1, GELU hidden units, sigmoid output; inputs are
+ * the 3x3 neighbourhood of a cell: per variable and cell k (paper label order)
+ * (ubar_k - ubar_c, vbar_k, wbar_k) / D, D = max |ubar_k - ubar_c| +
+ * dx^2 max |ubar_k| + 1e-12, except that the centre's average slot holds
+ * ubar_c / (max |ubar_k| + 1e-12); clipped to [-8, 8] (108 = 4 variables x
+ * 3 moments x 9 cells, order var, moment, cell).
+ * Parameters: FP32 flat W1[64][108], b1[64], W2[64][64], b2[64], W3[64], b3[1]
+ * (hweno_mlp_nparam() floats).  The contractions run on BF16 tensor cores with
+ * FP32 accumulation.
+ *
+ * Indicator 3 in hweno_grid (2D Euler; single-problem handles): at the start of
+ * each stage every cell's probability s comes from the network on the stage
+ * input.  Where the confidence max(s, 1-s) >= conf, the network decides the flag
+ * (s > 1/2) and a flagged cell's first moments are modified (eq. (vi)) before
+ * Step 1, which reconstructs it from the modified moments (so only cells flagged
+ * by the fallback are reconstructed twice).  The other cells are decided by
+ * KXRCF from the Step-1 point values, as indicator 1 does.  With conf > 1 every
+ * cell falls back and the results equal indicator 1's bit for bit.
+ * hweno_set_mlp installs the parameters (host or device pointer, copied) and
+ * conf (> 0); HWENO_ESTATE if the handle's indicator is not 3; a step before
+ * hweno_set_mlp fails with HWENO_ESTATE.  hweno_mlp_fallbacks returns and resets
+ * the number of cell decisions left to KXRCF since the last call.
+ * hweno_mlp_probe: a device array of ny*nx floats that every later stage fills
+ * with the network's probabilities (row-major j*nx+i), or NULL to stop.
+ * hweno_features: the 108 features (float, row per cell) of the given cells
+ * (device int array, j*nx+i) of a caller state U (device, state layout).
+ * Training (device pointers; asynchronous on stream): hweno_mlp_loss_grad adds
+ * the gradient of the weighted mean binary cross-entropy over n samples to grad
+ * and the loss to *loss (caller zeroes both); w may be NULL (weights 1).
+ * hweno_mlp_adam: one Adam step (beta 0.9, 0.999, eps 1e-8), step counts from 1.
+ * hweno_mlp_forward: probabilities of n feature rows. */
+int hweno_mlp_nparam(void);
+hweno_status hweno_set_mlp(hweno_t h, const float* params, int on_device, float conf);
+hweno_status hweno_mlp_fallbacks(hweno_t h, long long* cells);
+hweno_status hweno_mlp_probe(hweno_t h, float* prob);
+hweno_status hweno_features(hweno_t h, const double* U, const int* cells, int n, float* X);
+hweno_status hweno_mlp_forward(const float* params, const float* X, int n, float* prob, void* stream);
+hweno_status hweno_mlp_loss_grad(const float* params, const float* X, const float* y, const float* w, int n,
+                                 float* grad, float* loss, void* stream);
+hweno_status hweno_mlp_adam(float* params, const float* grad, float* m1, float* m2, int step, float lr,
+                            void* stream);
+
+/* Positivity check of hweno_step / hweno_step_batch (no counterpart in the
+ * paper, which has no positivity treatment): on (default), a stage whose new
+ * cell averages have rho <= 0 or p <= 0 (Euler) fails the step with
+ * HWENO_ENONPHYSICAL and the state is rolled back; off, only non-finite values
+ * fail it (transient negative pressures are carried on, as the scheme itself
+ * does).  Applies to single and batch handles. */
+hweno_status hweno_set_positivity_check(hweno_t h, int on);
+
+/* Troubled re-reconstruction work (Step 2.3): the number of cells reconstructed
+ * a second time, from modified moments, since the last call (then reset to 0).
+ * Single-problem handles; synchronises the handle's stream.  No counterpart in
+ * the paper: a work counter. */
+hweno_status hweno_rerecon_count(hweno_t h, long long* cells);
 
 /* ---------------------------------------------------------------- batches
  * Many independent 2D Euler problems of different sizes in one handle; every

@@ -25,7 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 EQ = {"advection": 0, "burgers": 1, "euler": 2}
-IND = {"none": 0, "kxrcf": 1, "all": 2}
+IND = {"none": 0, "kxrcf": 1, "all": 2, "given": 3}
 BC = {"periodic": 0, "transmissive": 1}
 
 
@@ -102,13 +102,17 @@ def state_shape(cfg: Cfg):
     return (nvars(cfg), 2 if cfg.dim == 1 else 3, cfg.ny if cfg.dim == 2 else 1, cfg.nx)
 
 
-def rhs(cfg: Cfg, U: np.ndarray):
-    """L(U) with the troubled-cell steps. Returns (Umod, L, mask, aleph, status)."""
+def rhs(cfg: Cfg, U: np.ndarray, decisions=None):
+    """L(U) with the troubled-cell steps. Returns (Umod, L, mask, aleph, status).
+    With indicator "given", decisions[cell] is 0 (smooth), 1 (troubled) or 2
+    (KXRCF decides after the given troubled cells are modified)."""
     U = np.ascontiguousarray(U, dtype=np.float64).reshape(state_shape(cfg))
     Um = np.empty_like(U)
     L = np.empty_like(U)
     ncell = cfg.nx * (cfg.ny if cfg.dim == 2 else 1)
     mask = np.zeros(ncell, np.uint8)
+    if decisions is not None:
+        mask[:] = np.asarray(decisions, np.uint8).reshape(-1)
     aleph = np.zeros(ncell, np.float64)
     rc = lib().orc_rhs(ctypes.byref(cfg), _dp(U), _dp(Um), _dp(L), _u8(mask), _dp(aleph))
     return Um, L, mask, aleph, rc

@@ -49,7 +49,8 @@ typedef struct {
   int eq;           /* 0 linear advection, 1 Burgers, 2 Euler */
   double adv_a, adv_b; /* advection speeds (f = a u, g = b u) */
   double gamma;     /* ratio of specific heats (Euler) */
-  int indicator;    /* 0 none (HWENO6), 1 KXRCF (M5-I), 2 all cells (M5-NI) */
+  int indicator;    /* 0 none (HWENO6), 1 KXRCF (M5-I), 2 all cells (M5-NI),
+                       3 given decisions with KXRCF for the deferred cells */
   double gbar[4];   /* positive linear-weight seeds, eq. (linear-weight) */
   int bc[4];        /* x-lo, x-hi, y-lo, y-hi: 0 periodic, 1 transmissive */
 } orc_cfg;
@@ -690,41 +691,16 @@ static int finite_state(const orc_cfg *c, const double *m) {
   return 1;
 }
 
-/*
- * One evaluation of the spatial operator with the troubled-cell steps.
- *   U     : stage input (not modified)
- *   Umod  : out, U with the first moments of troubled cells replaced (Step 2.2)
- *   Lout  : out, L(Umod) in the state layout
- *   mask  : out, troubled flags per cell (may be NULL)
- *   aleph : out, KXRCF values per cell (may be NULL)
- */
-int orc_rhs(const orc_cfg *c, const double *U, double *Umod, double *Lout,
-            unsigned char *mask, double *aleph) {
-  if (build_tables(c->dim)) return ORC_EINVAL;
-  int nv = nvars(c), nm = nmoms(c), ny = c->dim == 1 ? 1 : c->ny;
-  size_t nc = ncell(c), nstate = (size_t)nv * nm * nc;
-  double *G = malloc(nc * nv * 16 * sizeof(double));
-  unsigned char *flag = calloc(nc, 1);
-  /* Step 1: pass-1 point values in every cell */
-  reconstruct_all(c, U, G, NULL);
-  /* Step 2.1: troubled cells */
-  for (int j = 0; j < ny; ++j)
-    for (int i = 0; i < c->nx; ++i) {
-      size_t cell = (size_t)j * c->nx + i;
-      double a = 0.0;
-      if (c->indicator == 1) a = kxrcf_aleph(c, G, i, j);
-      if (aleph) aleph[cell] = a;
-      flag[cell] = c->indicator == 2 ? 1 : (c->indicator == 1 && a > 1.0);
-    }
-  /* Step 2.2: modify first moments of troubled cells (eq. (vi), applied
-   * dimension by dimension in 2D).  Reading: every new value is computed
-   * from the pre-modification moments (Jacobi). */
-  memcpy(Umod, U, nstate * sizeof(double));
+/* Step 2.2: modified first moments of the selected cells (eq. (vi), applied
+ * dimension by dimension in 2D) written into Umod.  Reading: every new value
+ * is computed from the pre-modification moments U (Jacobi). */
+static void modify_cells(const orc_cfg *c, const double *U, double *Umod, const unsigned char *sel) {
+  int nv = nvars(c), ny = c->dim == 1 ? 1 : c->ny;
   const double *w = c->dim == 1 ? T1.mod : T2.mod;
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < c->nx; ++i) {
       size_t cell = (size_t)j * c->nx + i;
-      if (!flag[cell]) continue;
+      if (!sel[cell]) continue;
       for (int v = 0; v < nv; ++v) {
         *MOM(c, Umod, v, 1, i, j) = w[0] * mom_at(c, U, v, 0, i - 1, j) + w[1] * mom_at(c, U, v, 0, i, j)
                                   + w[2] * mom_at(c, U, v, 0, i + 1, j)
@@ -735,8 +711,68 @@ int orc_rhs(const orc_cfg *c, const double *U, double *Umod, double *Lout,
                                     + w[3] * mom_at(c, U, v, 2, i, j - 1) + w[4] * mom_at(c, U, v, 2, i, j + 1);
       }
     }
-  /* Step 2.3: re-reconstruct the troubled cells from the modified moments */
-  reconstruct_all(c, Umod, G, flag);
+}
+
+/*
+ * One evaluation of the spatial operator with the troubled-cell steps.
+ *   U     : stage input (not modified)
+ *   Umod  : out, U with the first moments of troubled cells replaced (Step 2.2)
+ *   Lout  : out, L(Umod) in the state layout
+ *   mask  : out, troubled flags per cell (may be NULL); with indicator 3 also
+ *           in: the given decisions 0 / 1 / 2 (2 = KXRCF decides)
+ *   aleph : out, KXRCF values per cell (may be NULL)
+ */
+int orc_rhs(const orc_cfg *c, const double *U, double *Umod, double *Lout,
+            unsigned char *mask, double *aleph) {
+  if (build_tables(c->dim)) return ORC_EINVAL;
+  int nv = nvars(c), nm = nmoms(c), ny = c->dim == 1 ? 1 : c->ny;
+  size_t nc = ncell(c), nstate = (size_t)nv * nm * nc;
+  double *G = malloc(nc * nv * 16 * sizeof(double));
+  unsigned char *flag = calloc(nc, 1);
+  memcpy(Umod, U, nstate * sizeof(double));
+  if (c->indicator == 3) {
+    /* Decisions given on entry in mask: 0 smooth, 1 troubled, 2 left to KXRCF
+     * (the learned indicator, which decides from the moments alone).  Cells
+     * given as troubled are modified first and Step 1 reconstructs them from
+     * the modified moments; KXRCF then decides the deferred cells from those
+     * point values, and only the cells it flags are reconstructed again. */
+    if (!mask) { free(G); free(flag); return ORC_EINVAL; }
+    unsigned char *late = calloc(nc, 1);
+    for (size_t q = 0; q < nc; ++q) flag[q] = mask[q] == 1;
+    reconstruct_all(c, U, G, NULL);
+    modify_cells(c, U, Umod, flag);
+    reconstruct_all(c, Umod, G, flag);
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < c->nx; ++i) {
+        size_t cell = (size_t)j * c->nx + i;
+        double a = 0.0;
+        if (mask[cell] == 2) {
+          a = kxrcf_aleph(c, G, i, j);
+          late[cell] = a > 1.0;
+        }
+        if (aleph) aleph[cell] = a;
+      }
+    modify_cells(c, U, Umod, late);
+    reconstruct_all(c, Umod, G, late);
+    for (size_t q = 0; q < nc; ++q) flag[q] |= late[q];
+    free(late);
+  } else {
+    /* Step 1: pass-1 point values in every cell */
+    reconstruct_all(c, U, G, NULL);
+    /* Step 2.1: troubled cells */
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < c->nx; ++i) {
+        size_t cell = (size_t)j * c->nx + i;
+        double a = 0.0;
+        if (c->indicator == 1) a = kxrcf_aleph(c, G, i, j);
+        if (aleph) aleph[cell] = a;
+        flag[cell] = c->indicator == 2 ? 1 : (c->indicator == 1 && a > 1.0);
+      }
+    /* Step 2.2: modify the first moments of troubled cells */
+    modify_cells(c, U, Umod, flag);
+    /* Step 2.3: re-reconstruct the troubled cells from the modified moments */
+    reconstruct_all(c, Umod, G, flag);
+  }
   /* Step 3: fluxes, quadrature, semi-discrete right-hand sides */
   memset(Lout, 0, nstate * sizeof(double));
   for (int j = 0; j < ny; ++j)
@@ -814,6 +850,7 @@ int orc_rhs(const orc_cfg *c, const double *U, double *Umod, double *Lout,
  * masks (may be NULL): 3 x ncell troubled flags of the three stages.
  */
 int orc_step(const orc_cfg *c, double *m, double dt, unsigned char *masks) {
+  if (c->indicator == 3) return ORC_EINVAL;   /* decisions exist per stage only */
   size_t nc = ncell(c), n = (size_t)nvars(c) * nmoms(c) * nc;
   double *Un = malloc(n * sizeof(double)), *U1 = malloc(n * sizeof(double));
   double *U2 = malloc(n * sizeof(double)), *Um = malloc(n * sizeof(double)), *L = malloc(n * sizeof(double));
@@ -851,7 +888,10 @@ double orc_max_dt(const orc_cfg *c, const double *m, double cfl) {
       else {
         double rho = u[0], mu = u[1] / rho, nu = c->dim == 2 ? u[2] / rho : 0.0, E = u[nv - 1];
         double p = (c->gamma - 1.0) * (E - 0.5 * rho * (mu * mu + nu * nu));
-        double cs = sqrt(c->gamma * p / rho);
+        /* Reading: the sound speed takes max(p, 0), so that the transient
+         * negative-pressure averages the scheme can produce (it has no
+         * positivity treatment) do not make dt undefined. */
+        double cs = sqrt(c->gamma * fmax(p, 0.0) / rho);
         sx = fabs(mu) + cs; sy = fabs(nu) + cs;
       }
       if (sx > ax) ax = sx;

@@ -33,8 +33,10 @@ template <typename T, int NV, bool FLAGGED>
 __global__ void __launch_bounds__(RB) rec1d_kernel(Prob P, Weights<T> W, Beta1<T> B, const double* __restrict__ U,
                                                   const uint8_t* __restrict__ mask, const double* __restrict__ Mod,
                                                   const int* __restrict__ list, const int* __restrict__ count,
-                                                  T* __restrict__ G, T* __restrict__ aux) {
+                                                  T* __restrict__ G, T* __restrict__ aux,
+                                                  unsigned long long* __restrict__ rerec) {
   const int n = FLAGGED ? *count : P.nx;
+  if (FLAGGED && rerec && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(rerec, (unsigned long long)n);
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
     const int i = FLAGGED ? list[t] : t;
     const Img nb[3] = {image(P, i - 1, 0), image(P, i, 0), image(P, i + 1, 0)};
@@ -209,7 +211,7 @@ void stage_t(const Prob& P, const Weights<T>& W, const Beta1<T>& Bt, const Bufs&
   const int blocks = (P.nx + RB - 1) / RB;
   if (B.prof) B.prof->begin(0, st);
   rec1d_kernel<T, NV, false><<<blocks, RB, 0, st>>>(P, W, Bt, S.Uin, nullptr, nullptr, nullptr, nullptr, (T*)B.G,
-                                                    (T*)B.aux);
+                                                    (T*)B.aux, nullptr);
   if (B.prof) B.prof->end(st);
   if (B.prof) B.prof->begin(1, st);
   flag1d_kernel<T, NV><<<blocks, RB, 0, st>>>(P, W, S.Uin, (const T*)B.G, (const T*)B.aux, S.mask, S.Mod, B.list, cnt,
@@ -217,7 +219,8 @@ void stage_t(const Prob& P, const Weights<T>& W, const Beta1<T>& Bt, const Bufs&
   if (B.prof) B.prof->end(st);
   if (P.indicator != IND_NONE) {
     if (B.prof) B.prof->begin(2, st);
-    rec1d_kernel<T, NV, true><<<blocks, RB, 0, st>>>(P, W, Bt, S.Uin, S.mask, S.Mod, B.list, cnt, (T*)B.G, nullptr);
+    rec1d_kernel<T, NV, true><<<blocks, RB, 0, st>>>(P, W, Bt, S.Uin, S.mask, S.Mod, B.list, cnt, (T*)B.G, nullptr,
+                                                   B.rerec);
     if (B.prof) B.prof->end(st);
   }
   Rk1 r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status};

@@ -25,14 +25,6 @@ namespace {
 constexpr int TX = 32, TY = 4;   // update tile (one warp per row)
 constexpr int RB = 128;          // threads per block of the per-cell kernels
 
-__device__ __forceinline__ int mpt(const Img& m, int k, int l) {
-  if (m.sx < 0) k = 3 - k;
-  if (m.sy < 0) l = 3 - l;
-  return k * 4 + l;
-}
-
-__device__ __forceinline__ long long goff(const Prob& P, int i, int j) { return (long long)j * P.gpitch + i; }
-
 // Images of the 3x3 block around (i,j); the boundary map is separable, so
 // three x-images and three y-images describe all nine cells.
 struct Nbr {
@@ -51,27 +43,37 @@ __device__ __forceinline__ Nbr neighbours(const Prob& P, int i, int j) {
   return n;
 }
 
+// Reconstruction passes: every cell from the stage input (PLAIN); the listed
+// troubled cells from the modified moments (FLAGGED, Step 2.3); or every cell,
+// those already flagged (mask 1) from the modified moments (MIXED: the learned
+// indicator decides before Step 1).
+enum RecMode { REC_PLAIN = 0, REC_FLAGGED = 1, REC_MIXED = 2 };
+
 // Moment of kind 0 (average), 1 (x first moment) or 2 (y first moment) of
-// the stencil cell (ox, oy); first moments of troubled cells come from the
-// modified copy in the FLAGGED pass (eq. (vi) applied before Step 2.3).
-template <bool FLAGGED>
+// the stencil cell (ox, oy); when usemod, first moments of flagged stencil
+// cells come from the modified copy (eq. (vi) applied before Step 2.3).
+template <int MODE>
 __device__ __forceinline__ double load_mom(const Prob& P, const double* __restrict__ U, const uint8_t* __restrict__ mask,
                                            const double* __restrict__ Mod, const Nbr& n, int var, int kind, int ox,
-                                           int oy) {
+                                           int oy, bool usemod) {
   const int ci = n.xi[ox + 1], cj = n.yj[oy + 1];
   const long long so = (long long)cj * P.pitch + ci;
   if (kind == 0) return U[(long long)(var * 3) * P.plane + so];
   double v;
-  if (FLAGGED && mask[(long long)cj * P.nx + ci]) v = Mod[(long long)(var * 2 + kind - 1) * P.plane + so];
-  else v = U[(long long)(var * 3 + kind) * P.plane + so];
+  if (MODE != REC_PLAIN && usemod && mask[(long long)cj * P.nx + ci] == 1)
+    v = Mod[(long long)(var * 2 + kind - 1) * P.plane + so];
+  else
+    v = U[(long long)(var * 3 + kind) * P.plane + so];
   return (kind == 1 ? n.xs[ox + 1] : n.ys[oy + 1]) < 0 ? -v : v;
 }
 
-template <typename T, int NV, bool FLAGGED>
+template <typename T, int NV, int MODE>
 __device__ __forceinline__ void rec2d_cell(const Prob& P, const Weights<T>& W, const Beta2<T>& B,
                                            const double* __restrict__ U, const uint8_t* __restrict__ mask,
                                            const double* __restrict__ Mod, int i, int j, T* __restrict__ G,
                                            T* __restrict__ aux) {
+  constexpr bool FLAGGED = MODE == REC_FLAGGED;
+  const bool usemod = MODE == REC_FLAGGED || (MODE == REC_MIXED && mask[(long long)j * P.nx + i] == 1);
   const Nbr nb = neighbours(P, i, j);
   const long long o = goff(P, i, j);
   T rinv[16];
@@ -83,7 +85,7 @@ __device__ __forceinline__ void rec2d_cell(const Prob& P, const Weights<T>& W, c
     for (int c = 0; c < 23; ++c) {
       int kind, ox, oy;
       d4_slot(c, kind, ox, oy);
-      d[c] = T(load_mom<FLAGGED>(P, U, mask, Mod, nb, v, kind, ox, oy));
+      d[c] = T(load_mom<MODE>(P, U, mask, Mod, nb, v, kind, ox, oy, usemod));
     }
     T out[16];
     recon2d<T>(W, B, d, out);
@@ -143,57 +145,22 @@ __device__ __forceinline__ void rec2d_cell(const Prob& P, const Weights<T>& W, c
   }
 }
 
-template <typename T, int NV, bool FLAGGED>
+// rerec (REC_FLAGGED only, may be null) accumulates the number of cells
+// reconstructed a second time.
+template <typename T, int NV, int MODE>
 __global__ void __launch_bounds__(RB) rec2d_kernel(Prob P, Weights<T> W, Beta2<T> B, const double* __restrict__ U,
                                                   const uint8_t* __restrict__ mask, const double* __restrict__ Mod,
                                                   const int* __restrict__ list, const int* __restrict__ count,
-                                                  T* __restrict__ G, T* __restrict__ aux) {
+                                                  T* __restrict__ G, T* __restrict__ aux,
+                                                  unsigned long long* __restrict__ rerec) {
+  constexpr bool FLAGGED = MODE == REC_FLAGGED;
   const long long ncell = (long long)P.nx * P.ny;
   const long long n = FLAGGED ? (long long)*count : ncell;
+  if (FLAGGED && rerec && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(rerec, (unsigned long long)n);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int cell = FLAGGED ? list[t] : (int)t;
-    rec2d_cell<T, NV, FLAGGED>(P, W, B, U, mask, Mod, cell % P.nx, cell / P.nx, G, aux);
+    rec2d_cell<T, NV, MODE>(P, W, B, U, mask, Mod, cell % P.nx, cell / P.nx, G, aux);
   }
-}
-
-// KXRCF value of eq. (KXRCF_) with eq. (line-integral-average_): inflow faces by
-// the sign of the GL-weighted face velocity (average of both sides), jumps of
-// the indicator variable (variable 0) weighted by dy w_l or dx w_k.
-template <typename T>
-__device__ __forceinline__ T kxrcf2d(const Prob& P, const Weights<T>& W, const T* __restrict__ G,
-                                     const T* __restrict__ aux, int i, int j) {
-  const long long o = goff(P, i, j);
-  const Img L = image(P, i - 1, j), R = image(P, i + 1, j), Bo = image(P, i, j - 1), Tp = image(P, i, j + 1);
-  const long long oL = goff(P, L.i, L.j), oR = goff(P, R.i, R.j), oB = goff(P, Bo.i, Bo.j), oT = goff(P, Tp.i, Tp.j);
-  const T vxl = T(0.5) * (aux[(L.sx < 0 ? 0 : 1) * P.gplane + oL] + aux[0 * P.gplane + o]);
-  const T vxr = T(0.5) * (aux[1 * P.gplane + o] + aux[(R.sx < 0 ? 1 : 0) * P.gplane + oR]);
-  const T vyb = T(0.5) * (aux[(Bo.sy < 0 ? 2 : 3) * P.gplane + oB] + aux[2 * P.gplane + o]);
-  const T vyt = T(0.5) * (aux[3 * P.gplane + o] + aux[(Tp.sy < 0 ? 3 : 2) * P.gplane + oT]);
-  const T dx = T(P.dx), dy = T(P.dy);
-  T s = T(0), len = T(0);
-  if (vxl > T(KX_VDEAD)) {
-#pragma unroll
-    for (int l = 0; l < 4; ++l) s += dy * gl_w<T>(l) * (G[(long long)(l)*P.gplane + o] - G[(long long)mpt(L, 3, l) * P.gplane + oL]);
-    len += dy;
-  }
-  if (-vxr > T(KX_VDEAD)) {
-#pragma unroll
-    for (int l = 0; l < 4; ++l) s += dy * gl_w<T>(l) * (G[(long long)(12 + l) * P.gplane + o] - G[(long long)mpt(R, 0, l) * P.gplane + oR]);
-    len += dy;
-  }
-  if (vyb > T(KX_VDEAD)) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) s += dx * gl_w<T>(k) * (G[(long long)(k * 4) * P.gplane + o] - G[(long long)mpt(Bo, k, 3) * P.gplane + oB]);
-    len += dx;
-  }
-  if (-vyt > T(KX_VDEAD)) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) s += dx * gl_w<T>(k) * (G[(long long)(k * 4 + 3) * P.gplane + o] - G[(long long)mpt(Tp, k, 0) * P.gplane + oT]);
-    len += dx;
-  }
-  const T nrm = aux[4 * P.gplane + o];
-  if (len == T(0) || nrm == T(0)) return T(0);
-  return tabs(s) / len / (T(P.dx * P.dx) * nrm);   // h^{(l+1)/3}, l = 5, h = dx
 }
 
 // Step 2.1 for one cell: the troubled-cell decision of the configured indicator.
@@ -251,6 +218,35 @@ __global__ void __launch_bounds__(TX * TY) flag2d_kernel(Prob P, Weights<T> W, c
   if (!valid) return;
   mask[(long long)j * P.nx + i] = flag ? 1 : 0;
   if (flag) modify2d_cell<NV>(P, U, Mod, i, j);
+}
+
+// KXRCF for the cells the learned indicator left undecided (mask 2): the
+// decision, eq. (vi) for the troubled ones and their list for Step 2.3.
+template <typename T, int NV>
+__global__ void __launch_bounds__(RB) fallback2d_kernel(Prob P, Weights<T> W, const double* __restrict__ U,
+                                                       const T* __restrict__ G, const T* __restrict__ aux,
+                                                       const int* __restrict__ und, const int* __restrict__ und_count,
+                                                       uint8_t* __restrict__ mask, double* __restrict__ Mod,
+                                                       int* __restrict__ list, int* __restrict__ count,
+                                                       double* __restrict__ aleph) {
+  const long long n = *und_count;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  // warp-uniform trip count: every lane of a warp takes part in the append
+  for (long long b = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); b < n; b += stride) {
+    const long long t = b + (threadIdx.x & 31);
+    bool flag = false;
+    int cell = 0;
+    if (t < n) {
+      cell = und[t];
+      const int i = cell % P.nx, j = cell / P.nx;
+      const T a = kxrcf2d<T>(P, W, G, aux, i, j);
+      if (aleph) aleph[cell] = double(a);
+      flag = a > T(1);
+      mask[cell] = flag ? 1 : 0;
+      if (flag) modify2d_cell<NV>(P, U, Mod, i, j);
+    }
+    warp_append<int>(flag, cell, list, count);
+  }
 }
 
 template <typename T, int NV>
@@ -401,24 +397,46 @@ __global__ void __launch_bounds__(TX * TY) update2d_kernel(Prob P, const T* __re
 }
 
 template <typename T, int NV>
-void stage_t(const Prob& P, const Weights<T>& W, const Beta2<T>& Bt, const Bufs& B, const StageCall& S, cudaStream_t st) {
+void stage_t(const Prob& P, const HostTabs& HT, const Weights<T>& W, const Beta2<T>& Bt, const Bufs& B,
+             const StageCall& S, cudaStream_t st) {
   const long long ncell = (long long)P.nx * P.ny;
   int* cnt = B.count + S.stage;
   cudaMemsetAsync(cnt, 0, sizeof(int), st);
   const int rblocks = (int)((ncell + RB - 1) / RB);
-  if (B.prof) B.prof->begin(0, st);
-  rec2d_kernel<T, NV, false><<<rblocks, RB, 0, st>>>(P, W, Bt, S.Uin, nullptr, nullptr, nullptr, nullptr,
-                                                     (T*)B.G, (T*)B.aux);
-  if (B.prof) B.prof->end(st);
+  const int fblocks = (int)std::min<long long>(rblocks, (long long)P.nsm * 8);
   const dim3 blk(TX, TY), grd((P.nx + TX - 1) / TX, (P.ny + TY - 1) / TY);
-  if (B.prof) B.prof->begin(1, st);
-  flag2d_kernel<T, NV><<<grd, blk, 0, st>>>(P, W, S.Uin, (const T*)B.G, (const T*)B.aux, S.mask, S.Mod, B.list,
-                                            cnt, S.aleph);
-  if (B.prof) B.prof->end(st);
+  if (NV == 4 && P.indicator == IND_MLP) {
+    // Learned indicator first (moments only): confident cells are decided and
+    // modified before Step 1, which then reconstructs them from the modified
+    // moments; KXRCF decides the rest from the Step-1 point values, and only
+    // the cells it flags are reconstructed again.
+    int* ucnt = B.und_count + S.stage;
+    cudaMemsetAsync(ucnt, 0, sizeof(int), st);
+    if (B.prof) B.prof->begin(1, st);
+    run_mlpre2d(P, B.mlp, B.mlp_conf, S.Uin, S.mask, S.Mod, B.und, ucnt, B.mlp_stats, B.mlp_prob, st);
+    if (B.prof) B.prof->end(st);
+    if (B.prof) B.prof->begin(0, st);
+    rec2d_kernel<T, NV, REC_MIXED><<<rblocks, RB, 0, st>>>(P, W, Bt, S.Uin, S.mask, S.Mod, nullptr, nullptr,
+                                                           (T*)B.G, (T*)B.aux, nullptr);
+    if (B.prof) B.prof->end(st);
+    if (B.prof) B.prof->begin(1, st);
+    fallback2d_kernel<T, NV><<<fblocks, RB, 0, st>>>(P, W, S.Uin, (const T*)B.G, (const T*)B.aux, B.und, ucnt,
+                                                     S.mask, S.Mod, B.list, cnt, S.aleph);
+    if (B.prof) B.prof->end(st);
+  } else {
+    if (B.prof) B.prof->begin(0, st);
+    rec2d_kernel<T, NV, REC_PLAIN><<<rblocks, RB, 0, st>>>(P, W, Bt, S.Uin, nullptr, nullptr, nullptr, nullptr,
+                                                           (T*)B.G, (T*)B.aux, nullptr);
+    if (B.prof) B.prof->end(st);
+    if (B.prof) B.prof->begin(1, st);
+    flag2d_kernel<T, NV><<<grd, blk, 0, st>>>(P, W, S.Uin, (const T*)B.G, (const T*)B.aux, S.mask, S.Mod, B.list,
+                                              cnt, S.aleph);
+    if (B.prof) B.prof->end(st);
+  }
   if (P.indicator != IND_NONE) {
-    const int fblocks = (int)std::min<long long>(rblocks, (long long)P.nsm * 8);
     if (B.prof) B.prof->begin(2, st);
-    rec2d_kernel<T, NV, true><<<fblocks, RB, 0, st>>>(P, W, Bt, S.Uin, S.mask, S.Mod, B.list, cnt, (T*)B.G, nullptr);
+    rec2d_kernel<T, NV, REC_FLAGGED><<<fblocks, RB, 0, st>>>(P, W, Bt, S.Uin, S.mask, S.Mod, B.list, cnt, (T*)B.G,
+                                                             nullptr, B.rerec);
     if (B.prof) B.prof->end(st);
   }
   Rk r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status};
@@ -498,10 +516,7 @@ __global__ void __launch_bounds__(TXV * TYV) batch_stage_kernel(BatchStage A, We
         const double rho = U[sidx(P, 0, 0, i, j)];
         const double mu = U[sidx(P, 1, 0, i, j)] / rho, nu = U[sidx(P, 2, 0, i, j)] / rho;
         const double pr = (P.gamma - 1.0) * (U[sidx(P, 3, 0, i, j)] - 0.5 * rho * (mu * mu + nu * nu));
-        const double c = sqrt(P.gamma * pr / rho);
-        sx = fabs(mu) + c;
-        sy = fabs(nu) + c;
-        if (!(rho > 0.0) || !(pr > 0.0) || !isfinite(sx + sy)) sx = sy = INFINITY;
+        cell_speeds(P, rho, mu, nu, pr, sx, sy);
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -521,7 +536,7 @@ __global__ void __launch_bounds__(TXV * TYV) batch_stage_kernel(BatchStage A, We
     const BProb& Q = A.probs[p];
     const int cell = (it - Q.rec_first) * RB + tid;
     if (cell < Q.P.nx * Q.P.ny)
-      rec2d_cell<T, 4, false>(Q.P, W, B, A.Uin + Q.uoff, nullptr, nullptr, cell % Q.P.nx, cell / Q.P.nx, G + Q.goff,
+      rec2d_cell<T, 4, REC_PLAIN>(Q.P, W, B, A.Uin + Q.uoff, nullptr, nullptr, cell % Q.P.nx, cell / Q.P.nx, G + Q.goff,
                               aux + Q.aoff);
   }
   grid_barrier(A.bar, nb, A.status);
@@ -547,7 +562,7 @@ __global__ void __launch_bounds__(TXV * TYV) batch_stage_kernel(BatchStage A, We
       const unsigned long long e = A.list[t];
       const int p = (int)(e >> 32), cell = (int)(e & 0xffffffffu);
       const BProb& Q = A.probs[p];
-      rec2d_cell<T, 4, true>(Q.P, W, B, A.Uin + Q.uoff, A.mask + Q.coff, A.Mod + Q.moff, cell % Q.P.nx,
+      rec2d_cell<T, 4, REC_FLAGGED>(Q.P, W, B, A.Uin + Q.uoff, A.mask + Q.coff, A.Mod + Q.moff, cell % Q.P.nx,
                              cell / Q.P.nx, G + Q.goff, nullptr);
     }
   }
@@ -614,11 +629,11 @@ namespace {
 
 void run_stage_2d(const Prob& P, const HostTabs& T, int fp32, const Bufs& B, const StageCall& S, cudaStream_t st) {
   if (P.nvar == 4) {
-    if (fp32) stage_t<float, 4>(P, T.wf, T.b2f, B, S, st);
-    else stage_t<double, 4>(P, T.wd, T.b2d, B, S, st);
+    if (fp32) stage_t<float, 4>(P, T, T.wf, T.b2f, B, S, st);
+    else stage_t<double, 4>(P, T, T.wd, T.b2d, B, S, st);
   } else {
-    if (fp32) stage_t<float, 1>(P, T.wf, T.b2f, B, S, st);
-    else stage_t<double, 1>(P, T.wd, T.b2d, B, S, st);
+    if (fp32) stage_t<float, 1>(P, T, T.wf, T.b2f, B, S, st);
+    else stage_t<double, 1>(P, T, T.wd, T.b2d, B, S, st);
   }
 }
 

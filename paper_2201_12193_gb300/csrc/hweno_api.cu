@@ -33,6 +33,10 @@ struct hweno_s {
   double* red_out = nullptr;     // reduction results (device)
   double* host_buf = nullptr;    // pinned: reduction results + status
   hw::Prof prof;                 // per-kernel event timing (hweno_profile)
+  float* mlp = nullptr;          // learned indicator parameters (device)
+  int* mlp_stats = nullptr;      // fallback counter (device)
+  bool have_mlp = false;
+  bool positivity = true;        // rho <= 0 or p <= 0 in a new cell average fails the step
   std::string err;
   // batch mode (hweno_create_batch): many independent 2D Euler problems
   bool batch = false;
@@ -127,7 +131,10 @@ hweno_status validate(const hweno_grid* g, const hweno_bc* bc, double gamma, std
   }
   if (g->eq < 0 || g->eq > 2) { why = "eq must be advection, burgers or euler"; return HWENO_EINVAL; }
   if (g->precision != 0 && g->precision != 1) { why = "precision must be 0 (fp64) or 1 (fp32 bulk)"; return HWENO_EINVAL; }
-  if (g->indicator < 0 || g->indicator > 2) { why = "indicator must be none, kxrcf or all"; return HWENO_EINVAL; }
+  if (g->indicator < 0 || g->indicator > 3) { why = "indicator must be none, kxrcf, all or mlp"; return HWENO_EINVAL; }
+  if (g->indicator == 3 && (g->dim != 2 || g->eq != HWENO_EULER)) {
+    why = "the learned indicator is defined for 2D Euler"; return HWENO_EINVAL;
+  }
   for (int l = 0; l < 4; ++l)
     if (!(g->gamma_bar[l] > 0.0) || !isfinite(g->gamma_bar[l])) { why = "gamma_bar must be positive"; return HWENO_EINVAL; }
   const int k[4] = {bc->xlo, bc->xhi, bc->ylo, bc->yhi};
@@ -153,6 +160,11 @@ void drop_graphs(hweno_s* h) {
 
 void free_all(hweno_s* h) {
   drop_graphs(h);
+  cudaFree(h->mlp);
+  cudaFree(h->mlp_stats);
+  cudaFree(h->B.und);
+  cudaFree(h->B.und_count);
+  cudaFree(h->B.rerec);
   cudaFree(h->dprobs);
   cudaFree(h->blist);
   cudaFree(h->speeds);
@@ -190,6 +202,7 @@ hweno_status check_status(hweno_t h) {
     }
     st |= any;
   }
+  if (!h->positivity) st &= ~hw::ST_NONPOSITIVE;
   if (st != 0) {
     CK(h, cudaMemsetAsync(h->B.status, 0, sizeof(unsigned), h->stream));
     if (h->stepped) h->cur = h->prev;
@@ -245,6 +258,7 @@ hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gam
   P.adv_a = h->g.adv_a;
   P.adv_b = h->g.adv_b;
   P.nsm = 152;
+  P.positivity = 1;
   cudaDeviceGetAttribute(&P.nsm, cudaDevAttrMultiProcessorCount, h->dev);
   h->fp32 = h->g.precision;
   build_tables(h);
@@ -267,6 +281,17 @@ hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gam
   ok = ok && cudaMalloc(&h->red_part, hw::reduce_partials_len(P) * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->red_out, 8 * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMallocHost(&h->host_buf, 16 * sizeof(double)) == cudaSuccess;
+  ok = ok && cudaMalloc(&h->B.rerec, sizeof(unsigned long long)) == cudaSuccess;
+  if (grid->indicator == HWENO_IND_MLP) {
+    ok = ok && cudaMalloc(&h->mlp, hw::mlp_nparam() * sizeof(float)) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->mlp_stats, sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->B.und, nc * sizeof(int)) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->B.und_count, 4 * sizeof(int)) == cudaSuccess;
+    if (ok) {
+      cudaMemset(h->mlp_stats, 0, sizeof(int));
+      cudaMemset(h->B.und_count, 0, 4 * sizeof(int));
+    }
+  }
   if (!ok) {
     cudaGetLastError();
     free_all(h);
@@ -277,6 +302,7 @@ hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gam
   cudaMemset(h->B.status, 0, sizeof(unsigned));
   cudaMemset(h->mask3, 0, 3 * nc);
   cudaMemset(h->B.count, 0, 4 * sizeof(int));
+  cudaMemset(h->B.rerec, 0, sizeof(unsigned long long));
   for (int k = 0; k < 3; ++k) cudaMemset(h->U[k], 0, sbytes);
   if (cudaDeviceSynchronize() != cudaSuccess) { free_all(h); delete h; return HWENO_ECUDA; }
   *out = h;
@@ -329,6 +355,7 @@ hweno_status hweno_get_moments(hweno_t h, double* m, size_t count, int on_device
 hweno_status hweno_step(hweno_t h, double dt) {
   if (!h) return HWENO_EINVAL;
   if (!h->have_state) return fail(h, HWENO_ESTATE, "step: no moments set");
+  if (h->g.indicator == 3 && !h->have_mlp) return fail(h, HWENO_ESTATE, "step: learned indicator not set (hweno_set_mlp)");
   if (!(dt >= 0.0) || !isfinite(dt)) return fail(h, HWENO_EINVAL, "step: dt must be finite and >= 0");
   const int a = h->cur, b = (h->cur + 1) % 3, c = (h->cur + 2) % 3;
   const size_t nc = ncell(h);
@@ -406,6 +433,7 @@ hweno_status hweno_totals(hweno_t h, double* sums) {
 hweno_status hweno_rhs(hweno_t h, const double* U, double* Umod, double* L, unsigned char* mask, double* aleph) {
   if (!h) return HWENO_EINVAL;
   if (!U || !Umod || !L || !mask) return fail(h, HWENO_EINVAL, "rhs: U, Umod, L and mask are required");
+  if (h->g.indicator == 3 && !h->have_mlp) return fail(h, HWENO_ESTATE, "rhs: learned indicator not set (hweno_set_mlp)");
   Prob P = h->P;           // caller arrays are unpadded
   P.pitch = P.nx;
   P.plane = (long long)P.ny * P.nx;
@@ -417,6 +445,106 @@ hweno_status hweno_rhs(hweno_t h, const double* U, double* Umod, double* L, unsi
   else hw::run_stage_2d(P, h->T, h->fp32, h->B, S, h->stream);
   CK(h, cudaGetLastError());
   return HWENO_OK;
+}
+
+// ---------------------------------------------------------------- learned indicator
+
+static int device_sms() {
+  int dev = 0, n = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n;
+}
+
+int hweno_mlp_nparam(void) { return hw::mlp_nparam(); }
+
+hweno_status hweno_set_mlp(hweno_t h, const float* params, int on_device, float conf) {
+  if (!h || !params || !(conf > 0.0f)) return HWENO_EINVAL;
+  if (h->g.indicator != 3) return fail(h, HWENO_ESTATE, "set_mlp: the handle was not created with indicator 3 (mlp)");
+  const size_t nb = hw::mlp_nparam() * sizeof(float);
+  CK(h, cudaMemcpyAsync(h->mlp, params, nb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->B.mlp = h->mlp;
+  h->B.mlp_conf = conf;
+  h->B.mlp_stats = h->mlp_stats;
+  h->have_mlp = true;
+  return HWENO_OK;
+}
+
+hweno_status hweno_mlp_probe(hweno_t h, float* prob) {
+  if (!h) return HWENO_EINVAL;
+  if (h->g.indicator != 3) return fail(h, HWENO_ESTATE, "mlp_probe: the handle was not created with indicator 3 (mlp)");
+  h->B.mlp_prob = prob;
+  drop_graphs(h);
+  return HWENO_OK;
+}
+
+hweno_status hweno_mlp_fallbacks(hweno_t h, long long* cells) {
+  if (!h || !cells) return HWENO_EINVAL;
+  if (!h->mlp_stats) { *cells = 0; return HWENO_OK; }
+  int v = 0;
+  CK(h, cudaMemcpyAsync(&v, h->mlp_stats, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  CK(h, cudaMemsetAsync(h->mlp_stats, 0, sizeof(int), h->stream));
+  *cells = v;
+  return HWENO_OK;
+}
+
+hweno_status hweno_set_positivity_check(hweno_t h, int on) {
+  if (!h) return HWENO_EINVAL;
+  h->positivity = on != 0;
+  h->P.positivity = on != 0;
+  if (h->batch) {
+    for (auto& q : h->probs) q.P.positivity = on != 0;
+    CK(h, cudaMemcpyAsync(h->dprobs, h->probs.data(), h->probs.size() * sizeof(hw::BProb), cudaMemcpyHostToDevice,
+                          h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+  }
+  return HWENO_OK;
+}
+
+hweno_status hweno_rerecon_count(hweno_t h, long long* cells) {
+  if (!h || !cells) return HWENO_EINVAL;
+  if (h->batch) return fail(h, HWENO_ESTATE, "rerecon_count: single-problem handles only");
+  unsigned long long v = 0;
+  CK(h, cudaMemcpyAsync(&v, h->B.rerec, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  CK(h, cudaMemsetAsync(h->B.rerec, 0, sizeof v, h->stream));
+  *cells = (long long)v;
+  return HWENO_OK;
+}
+
+hweno_status hweno_features(hweno_t h, const double* U, const int* cells, int n, float* X) {
+  if (!h || !U || !cells || !X || n < 0) return HWENO_EINVAL;
+  if (h->g.dim != 2 || h->g.eq != HWENO_EULER) return fail(h, HWENO_EINVAL, "features: 2D Euler only");
+  Prob P = h->P;
+  P.pitch = P.nx;
+  P.plane = (long long)P.ny * P.nx;
+  CK(h, hw::run_features(P, U, cells, n, X, h->stream));
+  return HWENO_OK;
+}
+
+hweno_status hweno_mlp_forward(const float* params, const float* X, int n, float* prob, void* stream) {
+  if (!params || !prob || n < 0) return HWENO_EINVAL;
+  if (n == 0) return HWENO_OK;
+  if (!X) return HWENO_EINVAL;
+  return hw::run_mlp_forward(params, X, n, prob, device_sms(), (cudaStream_t)stream) == cudaSuccess ? HWENO_OK
+                                                                                                   : HWENO_ECUDA;
+}
+
+hweno_status hweno_mlp_loss_grad(const float* params, const float* X, const float* y, const float* w, int n,
+                                 float* grad, float* loss, void* stream) {
+  if (!params || !grad || !loss || n < 0) return HWENO_EINVAL;
+  if (n == 0) return HWENO_OK;
+  if (!X || !y) return HWENO_EINVAL;
+  return hw::run_mlp_train(params, X, y, w, n, grad, loss, device_sms(), (cudaStream_t)stream) == cudaSuccess
+             ? HWENO_OK : HWENO_ECUDA;
+}
+
+hweno_status hweno_mlp_adam(float* params, const float* grad, float* m1, float* m2, int step, float lr,
+                            void* stream) {
+  if (!params || !grad || !m1 || !m2 || step < 1 || !(lr > 0.0f)) return HWENO_EINVAL;
+  return hw::run_adam(params, grad, m1, m2, step, lr, (cudaStream_t)stream) == cudaSuccess ? HWENO_OK : HWENO_ECUDA;
 }
 
 hweno_status hweno_profile(hweno_t h, int enable) {
@@ -483,6 +611,10 @@ hweno_status hweno_create_batch(const hweno_grid* grids, const hweno_bc* bcs, in
               "indicator and linear weights\n", k);
       return HWENO_EINVAL;
     }
+    if (g.indicator == HWENO_IND_MLP) {
+      fprintf(stderr, "hweno_create_batch: the learned indicator runs on single-problem handles\n");
+      return HWENO_EINVAL;
+    }
   }
   hweno_s* h = new hweno_s();
   h->batch = true;
@@ -505,7 +637,7 @@ hweno_status hweno_create_batch(const hweno_grid* grids, const hweno_bc* bcs, in
     P.nvar = 4; P.nmom = 3; P.eq = HWENO_EULER; P.indicator = g.indicator;
     P.bc[0] = bcs[k].xlo; P.bc[1] = bcs[k].xhi; P.bc[2] = bcs[k].ylo; P.bc[3] = bcs[k].yhi;
     P.dx = (g.x1 - g.x0) / P.nx; P.dy = (g.y1 - g.y0) / P.ny;
-    P.gamma = gamma; P.adv_a = 0.0; P.adv_b = 0.0; P.nsm = nsm;
+    P.gamma = gamma; P.adv_a = 0.0; P.adv_b = 0.0; P.nsm = nsm; P.positivity = 1;
     q.uoff = tu; q.goff = tg; q.aoff = ta; q.moff = tm; q.coff = tc;
     tu += 12 * P.plane; tg += 64 * P.gplane; ta += 5 * P.gplane; tm += 8 * P.plane; tc += (long long)P.nx * P.ny;
     h->probs.push_back(q);

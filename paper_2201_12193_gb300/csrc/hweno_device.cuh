@@ -16,7 +16,7 @@ namespace hw {
 
 constexpr int EQ_ADV = 0, EQ_BURGERS = 1, EQ_EULER = 2;
 constexpr int BC_PERIODIC = 0, BC_TRANSMISSIVE = 1;
-constexpr int IND_NONE = 0, IND_KXRCF = 1, IND_ALL = 2;
+constexpr int IND_NONE = 0, IND_KXRCF = 1, IND_ALL = 2, IND_MLP = 3;
 
 // device status word bits
 constexpr unsigned ST_NONFINITE = 1u;     // a non-finite value in the new state
@@ -36,7 +36,19 @@ struct Prob {
   double gamma;           // ratio of specific heats
   double adv_a, adv_b;    // linear advection speeds
   int nsm;                // multiprocessors of the device (grid sizing)
+  int positivity;         // 1: rho <= 0 or p <= 0 averages are non-physical; 0: p is
+                          //    clamped at 0 in the sound speed (only rho <= 0 / non-finite fail)
 };
+
+// Sound speed of a cell average for the CFL rule; +inf marks a non-physical
+// average (dt = 0, the host reports it).
+__device__ __forceinline__ void cell_speeds(const Prob& P, double rho, double mu, double nu, double p, double& sx,
+                                            double& sy) {
+  const double c = sqrt(P.gamma * (P.positivity ? p : fmax(p, 0.0)) / rho);
+  sx = fabs(mu) + c;
+  sy = fabs(nu) + c;
+  if (!(rho > 0.0) || (P.positivity && !(p > 0.0)) || !isfinite(sx + sy)) sx = sy = INFINITY;
+}
 
 // Linear-weight data of eq. (linear-weight) and eq. (p) for positive gbar[4]:
 // gamma_{l,4} = g_l / S_4 and p_l = (S_l q_l - S_{l-1} q_{l-1}) / g_l.
@@ -373,5 +385,55 @@ constexpr double KX_VDEAD = 1e-12;
 // vbar_i <- -5/76 u_{i-1} + 5/76 u_{i+1} - 11/38 v_{i-1} - 11/38 v_{i+1}.
 constexpr double MOD_WU = 5.0 / 76.0;
 constexpr double MOD_WV = -11.0 / 38.0;
+
+// ---------------------------------------------------------------- 2D point values and KXRCF
+// Point-value arrays G[var][16][j][gpitch]; point (k, l) of a possibly mirrored image cell.
+__device__ __forceinline__ int mpt(const Img& m, int k, int l) {
+  if (m.sx < 0) k = 3 - k;
+  if (m.sy < 0) l = 3 - l;
+  return k * 4 + l;
+}
+
+__device__ __forceinline__ long long goff(const Prob& P, int i, int j) { return (long long)j * P.gpitch + i; }
+
+// KXRCF value of eq. (KXRCF_) with eq. (line-integral-average_): inflow faces by
+// the sign of the GL-weighted face velocity (average of both sides), jumps of
+// the indicator variable (variable 0) weighted by dy w_l or dx w_k.
+template <typename T>
+__device__ __forceinline__ T kxrcf2d(const Prob& P, const Weights<T>& W, const T* __restrict__ G,
+                                     const T* __restrict__ aux, int i, int j) {
+  const long long o = goff(P, i, j);
+  const Img L = image(P, i - 1, j), R = image(P, i + 1, j), Bo = image(P, i, j - 1), Tp = image(P, i, j + 1);
+  const long long oL = goff(P, L.i, L.j), oR = goff(P, R.i, R.j), oB = goff(P, Bo.i, Bo.j), oT = goff(P, Tp.i, Tp.j);
+  const T vxl = T(0.5) * (aux[(L.sx < 0 ? 0 : 1) * P.gplane + oL] + aux[0 * P.gplane + o]);
+  const T vxr = T(0.5) * (aux[1 * P.gplane + o] + aux[(R.sx < 0 ? 1 : 0) * P.gplane + oR]);
+  const T vyb = T(0.5) * (aux[(Bo.sy < 0 ? 2 : 3) * P.gplane + oB] + aux[2 * P.gplane + o]);
+  const T vyt = T(0.5) * (aux[3 * P.gplane + o] + aux[(Tp.sy < 0 ? 3 : 2) * P.gplane + oT]);
+  const T dx = T(P.dx), dy = T(P.dy);
+  T s = T(0), len = T(0);
+  if (vxl > T(KX_VDEAD)) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) s += dy * gl_w<T>(l) * (G[(long long)(l)*P.gplane + o] - G[(long long)mpt(L, 3, l) * P.gplane + oL]);
+    len += dy;
+  }
+  if (-vxr > T(KX_VDEAD)) {
+#pragma unroll
+    for (int l = 0; l < 4; ++l) s += dy * gl_w<T>(l) * (G[(long long)(12 + l) * P.gplane + o] - G[(long long)mpt(R, 0, l) * P.gplane + oR]);
+    len += dy;
+  }
+  if (vyb > T(KX_VDEAD)) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s += dx * gl_w<T>(k) * (G[(long long)(k * 4) * P.gplane + o] - G[(long long)mpt(Bo, k, 3) * P.gplane + oB]);
+    len += dx;
+  }
+  if (-vyt > T(KX_VDEAD)) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) s += dx * gl_w<T>(k) * (G[(long long)(k * 4 + 3) * P.gplane + o] - G[(long long)mpt(Tp, k, 0) * P.gplane + oT]);
+    len += dx;
+  }
+  const T nrm = aux[4 * P.gplane + o];
+  if (len == T(0) || nrm == T(0)) return T(0);
+  return tabs(s) / len / (T(P.dx * P.dx) * nrm);   // h^{(l+1)/3}, l = 5, h = dx
+}
 
 }  // namespace hw

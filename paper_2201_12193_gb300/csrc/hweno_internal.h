@@ -61,6 +61,13 @@ struct Bufs {
   int* count;         // [3] flagged counts per stage
   unsigned* status;   // ST_* bits
   Prof* prof;         // per-kernel timing, or nullptr
+  const float* mlp;   // learned indicator parameters (FP32, device), IND_MLP
+  float mlp_conf;     // confidence threshold of the learned indicator
+  int* mlp_stats;     // [1] cells decided by the KXRCF fallback (accumulates)
+  float* mlp_prob;    // optional: the network's probability per cell of the last stage
+  int* und;           // cells the learned indicator left to KXRCF (current stage)
+  int* und_count;     // [3] their counts per stage
+  unsigned long long* rerec;   // [1] cells reconstructed a second time (accumulates), or null
 };
 
 // One evaluation of the spatial operator with the troubled-cell steps and,
@@ -127,6 +134,16 @@ struct BatchStage {
 cudaError_t run_batch_stage(const HostTabs& T, int fp32, int tile_variant, const BatchStage& S, int nsm,
                             cudaStream_t st);
 constexpr unsigned ST_TIMEOUT = 4u;   // a bounded grid-barrier wait gave up
+
+// Learned troubled-cell indicator (hweno_mlp.cu).
+int mlp_nparam();
+cudaError_t run_features(const Prob& P, const double* U, const int* cells, int n, float* X, cudaStream_t st);
+cudaError_t run_mlp_forward(const float* th, const float* X, int n, float* prob, int nsm, cudaStream_t st);
+cudaError_t run_mlp_train(const float* th, const float* X, const float* y, const float* w, int n, float* grad,
+                          float* loss, int nsm, cudaStream_t st);
+cudaError_t run_adam(float* th, const float* grad, float* m1, float* m2, int step, float lr, cudaStream_t st);
+cudaError_t run_mlpre2d(const Prob& P, const float* th, float conf, const double* U, uint8_t* mask, double* Mod,
+                        int* und, int* und_count, int* stats, float* prob, cudaStream_t st);
 void run_stage_2d(const Prob& P, const HostTabs& T, int fp32, const Bufs& B, const StageCall& S, cudaStream_t st);
 
 // Reductions over the cell averages (FP64): maximum wave speeds per direction

@@ -42,7 +42,8 @@ __device__ __forceinline__ void block_reduce(double (&v)[K], bool is_max, double
 }
 
 // Largest |f'| (scalars) or |velocity| + sound speed (Euler) per direction,
-// from cell averages.  A non-physical average yields +inf (dt = 0).
+// from cell averages.  A non-physical average yields +inf (dt = 0).  With the
+// positivity check off the sound speed uses max(p, 0).
 __global__ void __launch_bounds__(RT) wavespeed_kernel(Prob P, const double* __restrict__ U, double* __restrict__ part) {
   __shared__ double sm[2][RT / 32];
   double v[2] = {0.0, 0.0};
@@ -58,10 +59,7 @@ __global__ void __launch_bounds__(RT) wavespeed_kernel(Prob P, const double* __r
       const double nu = P.nvar == 4 ? U[sidx(P, 2, 0, i, j)] / rho : 0.0;
       const double E = U[sidx(P, P.nvar - 1, 0, i, j)];
       const double p = (P.gamma - 1.0) * (E - 0.5 * rho * (mu * mu + nu * nu));
-      const double c = sqrt(P.gamma * p / rho);
-      sx = fabs(mu) + c;
-      sy = fabs(nu) + c;
-      if (!(rho > 0.0) || !(p > 0.0) || !isfinite(sx + sy)) sx = sy = INFINITY;
+      cell_speeds(P, rho, mu, nu, p, sx, sy);
     }
     v[0] = fmax(v[0], sx);
     v[1] = fmax(v[1], sy);

@@ -18,7 +18,7 @@ _lib = None
 
 STATUS = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "ENONPHYSICAL", -4: "ETIMEOUT", -5: "ESTATE", -6: "ENOMEM"}
 EQ = {"advection": 0, "burgers": 1, "euler": 2}
-IND = {"none": 0, "kxrcf": 1, "all": 2}
+IND = {"none": 0, "kxrcf": 1, "all": 2, "mlp": 3}
 BC = {"periodic": 0, "transmissive": 1}
 PREC = {"fp64": 0, "fp32": 1}
 
@@ -76,6 +76,16 @@ def lib():
         L.hweno_batch_set_tile.argtypes = [H, ctypes.c_int]
         L.hweno_batch_uses_graph.argtypes = [H]
         L.hweno_batch_status.argtypes = [H, ctypes.POINTER(ctypes.c_uint), ctypes.c_int]
+        L.hweno_mlp_nparam.restype = ctypes.c_int
+        L.hweno_set_mlp.argtypes = [H, ctypes.c_void_p, ctypes.c_int, ctypes.c_float]
+        L.hweno_mlp_fallbacks.argtypes = [H, ctypes.POINTER(ctypes.c_longlong)]
+        L.hweno_features.argtypes = [H, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+        L.hweno_mlp_forward.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        L.hweno_mlp_loss_grad.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int] + [ctypes.c_void_p] * 3
+        L.hweno_mlp_adam.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int, ctypes.c_float, ctypes.c_void_p]
+        L.hweno_mlp_probe.argtypes = [H, ctypes.c_void_p]
+        L.hweno_rerecon_count.argtypes = [H, ctypes.POINTER(ctypes.c_longlong)]
+        L.hweno_set_positivity_check.argtypes = [H, ctypes.c_int]
         L.hweno_last_error.argtypes = [H]
         L.hweno_last_error.restype = ctypes.c_char_p
         L.hweno_version.restype = ctypes.c_int
@@ -193,7 +203,7 @@ class Solver:
     def sync(self):
         self._check(lib().hweno_sync(self._h))
 
-    def rhs(self, U, Umod, L, mask, aleph=None):
+    def rhs(self, U, Umod, L, mask, aleph=None):  # noqa: D401
         """Device tensors: U (in), Umod, L, mask (uint8 [ny, nx]), aleph (optional float64 [ny, nx])."""
         for x in (U, Umod, L):
             if _ptr(x)[2] != self.count or not _ptr(x)[1]:
@@ -203,6 +213,43 @@ class Solver:
         ptrs = [_ptr(x)[0] for x in (U, Umod, L, mask)]
         a = _ptr(aleph)[0] if aleph is not None else None
         self._check(lib().hweno_rhs(self._h, *[ctypes.c_void_p(p) for p in ptrs], ctypes.c_void_p(a)))
+
+    def set_mlp(self, params, conf=0.9):
+        """Install the learned indicator (handle created with indicator="mlp")."""
+        if isinstance(params, np.ndarray):
+            params = np.ascontiguousarray(params, dtype=np.float32)
+        addr, dev, n = _ptr(params)
+        if n != mlp_nparam():
+            raise ValueError(f"expected {mlp_nparam()} parameters")
+        self._check(lib().hweno_set_mlp(self._h, ctypes.c_void_p(addr), dev, float(conf)))
+
+    def mlp_fallbacks(self):
+        v = ctypes.c_longlong()
+        self._check(lib().hweno_mlp_fallbacks(self._h, ctypes.byref(v)))
+        return v.value
+
+    def mlp_probe(self, prob):
+        """prob: CUDA float32 tensor of ny*nx that each later stage fills with the
+        network's probabilities, or None to stop."""
+        if prob is not None and (_ptr(prob)[2] != self.nx * self.ny or not _ptr(prob)[1]):
+            raise ValueError("prob must be a CUDA float32 tensor of ny*nx")
+        self._probe = prob
+        self._check(lib().hweno_mlp_probe(self._h, ctypes.c_void_p(_ptr(prob)[0] if prob is not None else None)))
+
+    def set_positivity_check(self, on=True):
+        """Off: only non-finite values fail a step (rho <= 0 / p <= 0 averages carry on)."""
+        self._check(lib().hweno_set_positivity_check(self._h, int(bool(on))))
+
+    def rerecon_count(self):
+        """Cells reconstructed a second time (troubled cells, Step 2.3) since the last call."""
+        v = ctypes.c_longlong()
+        self._check(lib().hweno_rerecon_count(self._h, ctypes.byref(v)))
+        return v.value
+
+    def features(self, U, cells, X):
+        """108 features (float32 rows) of cells (int32 CUDA tensor) of state U (CUDA)."""
+        self._check(lib().hweno_features(self._h, ctypes.c_void_p(_ptr(U)[0]), ctypes.c_void_p(_ptr(cells)[0]),
+                                         int(cells.numel()), ctypes.c_void_p(_ptr(X)[0])))
 
     KERNEL_KINDS = ("reconstruct", "indicator", "reconstruct_troubled", "update")
 
@@ -247,6 +294,40 @@ def max_dt_noalloc(grid, gamma, m, cfl, out, stream=None):
         raise HwenoError(st, "hweno_max_dt_noalloc failed (see stderr)")
 
 
+def mlp_nparam():
+    return lib().hweno_mlp_nparam()
+
+
+def _dev(x):
+    a, dev, n = _ptr(x)
+    if not dev:
+        raise ValueError("expected a CUDA tensor")
+    return ctypes.c_void_p(a if n else None)
+
+
+def _stream(stream):
+    return ctypes.c_void_p(getattr(stream, "cuda_stream", stream) or 0)
+
+
+def mlp_forward(params, X, prob, stream=None):
+    st = lib().hweno_mlp_forward(_dev(params), _dev(X), int(X.shape[0]), _dev(prob), _stream(stream))
+    if st != 0:
+        raise HwenoError(st, "hweno_mlp_forward failed")
+
+
+def mlp_loss_grad(params, X, y, w, grad, loss, stream=None):
+    st = lib().hweno_mlp_loss_grad(_dev(params), _dev(X), _dev(y), _dev(w) if w is not None else None,
+                                   int(X.shape[0]), _dev(grad), _dev(loss), _stream(stream))
+    if st != 0:
+        raise HwenoError(st, "hweno_mlp_loss_grad failed")
+
+
+def mlp_adam(params, grad, m1, m2, step, lr, stream=None):
+    st = lib().hweno_mlp_adam(_dev(params), _dev(grad), _dev(m1), _dev(m2), int(step), float(lr), _stream(stream))
+    if st != 0:
+        raise HwenoError(st, "hweno_mlp_adam failed")
+
+
 def _grid_struct(dim, nx, ny, x0, x1, y0, y1, eq, adv=(0.0, 0.0), precision="fp64", indicator="kxrcf",
                  gamma_bar=(1.0, 10.0, 100.0, 1000.0), beta_of_q=False):
     g = Grid()
@@ -288,6 +369,9 @@ class BatchSolver:
     def _check(self, st):
         if st != 0:
             raise HwenoError(st, lib().hweno_last_error(self._h).decode())
+
+    def set_positivity_check(self, on=True):
+        self._check(lib().hweno_set_positivity_check(self._h, int(bool(on))))
 
     def close(self):
         if getattr(self, "_h", None):
