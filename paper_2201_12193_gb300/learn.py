@@ -5,12 +5,14 @@ forward/backward, Adam); this module only schedules them.  Labels are the
 paper's KXRCF decisions (eq. (KXRCF_)) on the first-stage input of steps of the
 method itself; KXRCF stays the fallback for low-confidence cells and the judge.
 
-  python -m paper_2201_12193_gb300.learn train --out params.npz
+  python -m paper_2201_12193_gb300.learn train      # writes data/mlp_indicator.npz
+  python -m paper_2201_12193_gb300.learn judge
 """
 from __future__ import annotations
 
 import argparse
 import math
+import os
 import time
 
 import numpy as np
@@ -26,31 +28,52 @@ def init_params(seed=0):
     return np.concatenate(parts).astype(np.float32)
 
 
-def training_problems(seed=0, n=256, count=6):
+PARAMS_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "mlp_indicator.npz")
+
+
+def training_problems(seed=0, n=256, count=6, ncircles=4):
     """Blast-circle and four-quadrant problems (the workload's data families)."""
     probs = []
     for k in range(count):
         if k % 2 == 0:
-            probs.append(W.blast_2d(n, seed=seed * 1000 + k, ncircles=4))
+            probs.append(W.blast_2d(n, seed=seed * 1000 + k, ncircles=ncircles))
         else:
             probs.append(W.four_quadrant_2d(n, seed=seed * 1000 + k))
     return probs
 
 
-def harvest(problems, steps=12, neg_ratio=3, seed=0, pos_weight=1.0):
-    """(X, y, w) on the GPU: all KXRCF-flagged cells of the first stage of each
-    step, plus unflagged cells (half next to flagged ones, half anywhere);
-    class weights balance the two labels, the troubled class then scaled by
-    pos_weight (missing a troubled cell costs more than a false alarm)."""
+# Default training recipe: blast data of the C4 family (8 circles) at three
+# resolutions plus four-quadrant Riemann data, so that the network sees the
+# h^2 scale of its features vary.  (grid size, blast seeds, four-quadrant seeds, steps)
+RECIPE = ((256, 6, 2, 40), (512, 4, 2, 30), (1024, 2, 0, 24))
+
+
+def recipe_problems(seed=1):
+    out = []
+    for n, nb, nq, steps in RECIPE:
+        for k in range(nb):
+            out.append((W.blast_2d(n, seed=seed * 10000 + n + k, ncircles=8), steps))
+        for k in range(nq):
+            out.append((W.four_quadrant_2d(n, seed=seed * 10000 + n + 100 + k), steps))
+    return out
+
+
+def harvest(problems, steps=12, neg_ratio=3, seed=0, pos_weight=1.0, max_pos=20000):
+    """(X, y, w) on the GPU: the KXRCF-flagged cells of the first stage of each
+    step (at most max_pos per step, drawn at random), plus unflagged cells (half
+    next to flagged ones, half anywhere); class weights balance the two labels,
+    the troubled class then scaled by pos_weight (missing a troubled cell costs
+    more than a false alarm).  problems: Problem objects or (Problem, steps)."""
     import torch
     rng = np.random.default_rng(seed)
     Xs, ys = [], []
-    for p in problems:
+    for item in problems:
+        p, nsteps = item if isinstance(item, tuple) else (item, steps)
         s = hweno.Solver.from_problem(p)
         s.set_positivity_check(False)     # the scheme's own transient p < 0 averages carry on
         s.set_moments(torch.from_numpy(p.m).cuda())
         U = torch.empty(s.shape, dtype=torch.float64, device="cuda")
-        for _ in range(steps):
+        for _ in range(nsteps):
             s.get_moments(U)
             Uc = U.clone()
             try:
@@ -59,6 +82,8 @@ def harvest(problems, steps=12, neg_ratio=3, seed=0, pos_weight=1.0):
             except hweno.HwenoError:
                 break
             pos = np.flatnonzero(mask)
+            if len(pos) > max_pos:
+                pos = rng.choice(pos, max_pos, replace=False)
             neg_all = np.flatnonzero(mask == 0)
             if len(neg_all) == 0:
                 continue
@@ -182,28 +207,46 @@ def judge(params, problems, steps=10, conf=0.9):
             "l1_drift_vs_kxrcf": drift_num / max(drift_den, 1e-300)}
 
 
+def load_params(path=None):
+    """The trained parameters (float32, flat layout of include/hweno.h)."""
+    with np.load(path or PARAMS_FILE) as z:
+        return np.ascontiguousarray(z["params"], dtype=np.float32)
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
-    t = sub.add_parser("train")
-    t.add_argument("--out", required=True)
-    t.add_argument("--n", type=int, default=256)
-    t.add_argument("--problems", type=int, default=8)
-    t.add_argument("--steps", type=int, default=16)
-    t.add_argument("--epochs", type=int, default=30)
+    t = sub.add_parser("train", help="harvest KXRCF labels, train on the GPU, judge on held-out data")
+    t.add_argument("--out", default=PARAMS_FILE)
+    t.add_argument("--epochs", type=int, default=40)
+    t.add_argument("--pos-weight", type=float, default=3.0)
+    t.add_argument("--seed", type=int, default=1)
+    j = sub.add_parser("judge", help="judge saved parameters on held-out blast data")
+    j.add_argument("--params", default=PARAMS_FILE)
+    j.add_argument("--n", type=int, default=1024)
+    j.add_argument("--steps", type=int, default=10)
     args = ap.parse_args()
     import torch
     torch.cuda.set_device(0)
+    held = [W.blast_2d(1024, seed=900 + k, ncircles=8) for k in range(2)]
+    if args.cmd == "judge":
+        held = [W.blast_2d(args.n, seed=900 + k, ncircles=8) for k in range(2)]
+        print(judge(load_params(args.params), held, steps=args.steps))
+        return
     t0 = time.time()
-    X, y, w = harvest(training_problems(seed=1, n=args.n, count=args.problems), steps=args.steps)
-    print(f"harvest: {X.shape[0]} samples ({int(y.sum())} flagged) in {time.time() - t0:.1f} s")
+    probs = recipe_problems(args.seed)
+    X, y, w = harvest(probs, pos_weight=args.pos_weight, seed=args.seed)
+    t_h = time.time() - t0
+    print(f"harvest: {X.shape[0]} samples ({int(y.sum())} flagged) in {t_h:.1f} s")
     t0 = time.time()
-    params, hist = train(X, y, w, epochs=args.epochs, log=print)
-    print(f"train: {time.time() - t0:.1f} s")
-    held = training_problems(seed=2, n=args.n, count=2)
-    rep = judge(params, held, steps=8)
+    params, hist = train(X, y, w, epochs=args.epochs, batch=8192, lr=3e-3, seed=args.seed)
+    t_t = time.time() - t0
+    print(f"train: {t_t:.1f} s, loss {hist[0]:.4f} -> {hist[-1]:.4f}")
+    rep = judge(params, held, steps=10)
     print(rep)
-    np.savez(args.out, params=params, loss=np.array(hist), **{k: v for k, v in rep.items()})
+    os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
+    np.savez(args.out, params=params, loss=np.array(hist), samples=X.shape[0], harvest_s=t_h, train_s=t_t,
+             recipe=np.array(RECIPE), **{"judge_" + k: v for k, v in rep.items()})
 
 
 if __name__ == "__main__":
