@@ -7,8 +7,11 @@ One bench step = one whole pass of the hot path: the CFL wave-speed reduction
 (hweno_max_dt) and one SSP-RK3 step (hweno_step: three stages of reconstruct,
 indicator + modification, troubled re-reconstruction, fluxes + quadrature +
 update).  value = cells * 3 stages * steps / device time, FP64 (the scheme as
-specified); the FP32-bulk form is timed beside it and reported under "forms"
-with its relative L1 difference to FP64.
+specified).  Under "forms": the FP32-bulk form (relative L1 difference to FP64),
+the batched form (256 problems of uneven size, one persistent launch per stage,
+CUDA graph), and the learned-indicator form on 4096^2 blast data against the
+plain scheme on the same data (throughputs, network roofline, recall / miss /
+false-alarm rates against KXRCF, L1 drift).
 
 Multi-GPU (torchrun): each rank advances its own independently seeded problem
 (weak scaling, no data-path collective); the timing barrier and the max over
@@ -67,6 +70,8 @@ def parse():
                     help="form of the main measurement (fp64 = the scheme as specified)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched form")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-indicator form")
+    ap.add_argument("--learned-n", type=int, default=4096, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
 
@@ -286,6 +291,133 @@ def run_batched(torch, hweno, args, world, rank):
     return out
 
 
+MLP_FLOP_PER_CELL = 2 * (108 * 64 + 64 * 64 + 64)    # 11,072 multiply-adds per cell
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def run_learned(torch, hweno, args, world, rank):
+    """The learned-indicator form on its own workload: 2D Euler blast data
+    (8 seeded circles, p in U[5,100] inside, 0.1 outside, rho = 1, at rest),
+    4096^2, FP64, CFL 0.6, against the plain KXRCF scheme on the same data and
+    the same dt sequence.  Reports both throughputs, the network pass's tensor
+    roofline, and the judge: recall / false-negative / false-positive rates of
+    the learned decisions against KXRCF on identical stage inputs, the share of
+    cell decisions the network took, the troubled re-reconstruction work, and
+    the relative L1 drift of the final state from the plain scheme's."""
+    from paper_2201_12193_gb300 import learn, workloads as W
+    n = args.learned_n
+    t0 = time.time()
+    p = W.blast_2d(n, seed=rank, ncircles=8)
+    gen_s = time.time() - t0
+    params = learn.load_params()
+    cells = p.nx * p.ny
+    steps, warm = args.steps, args.warmup
+    res = {}
+    dts = []
+    finals = {}
+    for mode in ("kxrcf", "mlp"):
+        s = hweno.Solver.from_problem(p, indicator=mode)
+        if mode == "mlp":
+            s.set_mlp(params, 0.9)
+        s.set_positivity_check(False)          # the scheme's transient p < 0 averages carry on
+        s.set_stream(torch.cuda.current_stream())
+        s.set_moments(torch.from_numpy(p.m).cuda())
+        for k in range(warm):
+            dt = s.max_dt(CFL)
+            if mode == "kxrcf":
+                dts.append(dt)
+            s.step(dts[k])
+        s.sync()
+        s.rerecon_count()
+        if mode == "mlp":
+            s.mlp_fallbacks()
+        s.profile(True)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(warm, warm + steps):
+            dt = s.max_dt(CFL)                 # the same reduction in both runs
+            if mode == "kxrcf":
+                dts.append(dt)
+            s.step(dts[k])                      # the plain run's dt sequence in both
+        e1.record()
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1), world)
+        prof = s.profile_read()
+        s.profile(False)
+        rer = s.rerecon_count()
+        fb = s.mlp_fallbacks() if mode == "mlp" else None
+        out = torch.empty(s.shape, dtype=torch.float64, device="cuda")
+        s.get_moments(out)
+        finals[mode] = out
+        res[mode] = {"value": cells * 3 * steps * world / (ms * 1e-3), "ms_per_step": ms / steps,
+                     "rerecon_cells_per_stage": rer / (3 * steps), "prof": prof, "fallbacks": fb}
+        s.close()
+    a, b = finals["mlp"], finals["kxrcf"]
+    drift = float((a - b).abs().sum() / b.abs().sum())
+    del finals, a, b
+    # judge on identical stage inputs: the initial state and the final plain state
+    judge = {"tp": 0, "fp": 0, "fn": 0, "tn": 0}
+    kx = hweno.Solver.from_problem(p)
+    ml = hweno.Solver.from_problem(p, indicator="mlp")
+    ml.set_mlp(params, 0.9)
+    U = torch.from_numpy(p.m).cuda()
+    Um, L = torch.empty_like(U), torch.empty_like(U)
+    mk = torch.empty((p.ny, p.nx), dtype=torch.uint8, device="cuda")
+    mm = torch.empty_like(mk)
+    kx.set_positivity_check(False)
+    kx.set_moments(U)
+    for k, dt in enumerate(dts):
+        if k in (0, len(dts) // 2, len(dts) - 1):
+            kx.get_moments(U)
+            kx.rhs(U, Um, L, mk)
+            ml.rhs(U, Um, L, mm)
+            x, y = mm.bool(), mk.bool()
+            judge["tp"] += int((x & y).sum()); judge["fp"] += int((x & ~y).sum())
+            judge["fn"] += int((~x & y).sum()); judge["tn"] += int((~x & ~y).sum())
+        kx.step(dt)
+    kx.close()
+    ml.close()
+    del U, Um, L
+    torch.cuda.empty_cache()
+    pos = max(judge["tp"] + judge["fn"], 1)
+    lp = res["mlp"]["prof"]
+    net_ms, net_n = lp["learned_indicator"]
+    tot = sum(v[0] for v in lp.values())
+    pk = _peaks()
+    peak = pk.get("bf16_tflops_sustained")
+    achieved = MLP_FLOP_PER_CELL * cells * net_n / (net_ms * 1e-3) / 1e12 if net_n else None
+    roof = {"bound": "tensor", "kernel": "mlpre2d (features + 108-64-64-1 BF16 mma.sync, FP32 accumulate)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if (achieved and peak) else None,
+            "peak_source": "MEASURED_PEAKS bf16_tflops_sustained (of measured)" if peak else None,
+            "avg_ms": net_ms / max(net_n, 1), "launches": net_n, "share": net_ms / tot if tot else None,
+            "flop_per_cell": MLP_FLOP_PER_CELL}
+    return {"learned_fp64": {
+        "workload": f"2d_euler_blast_{n}x{n}", "value": res["mlp"]["value"], "ms_per_step": res["mlp"]["ms_per_step"],
+        "plain_kxrcf_value": res["kxrcf"]["value"], "plain_kxrcf_ms_per_step": res["kxrcf"]["ms_per_step"],
+        "speedup_vs_plain": res["kxrcf"]["ms_per_step"] / res["mlp"]["ms_per_step"], "steps": steps, "warmup": warm,
+        "dtype": "f64 (network bf16 in, f32 accumulate)", "conf": 0.9,
+        "recall": judge["tp"] / pos, "false_negative_rate": judge["fn"] / pos,
+        "false_positive_rate": judge["fp"] / max(judge["fp"] + judge["tn"], 1),
+        "decided_by_network": 1.0 - res["mlp"]["fallbacks"] / (cells * 3 * steps),
+        "rerecon_cells_per_stage": {"mlp": res["mlp"]["rerecon_cells_per_stage"],
+                                    "kxrcf": res["kxrcf"]["rerecon_cells_per_stage"]},
+        "rel_l1_drift_vs_kxrcf": drift, "steps_compared": warm + steps,
+        "kernels_ms": {"mlp": {k: v[0] for k, v in lp.items()},
+                       "kxrcf": {k: v[0] for k, v in res["kxrcf"]["prof"].items()}},
+        "roofline_network": roof, "input_generation_s": gen_s}}
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -338,6 +470,9 @@ def run_ours(args, world, rank, local):
 
     if not args.no_forms and not args.no_batch:
         forms.update(run_batched(torch, hweno, args, world, rank))
+
+    if not args.no_forms and not args.no_learned:
+        forms.update(run_learned(torch, hweno, args, world, rank))
 
     e2e = None
     if not args.no_e2e:

@@ -241,9 +241,12 @@ hweno_status hweno_batch_status(hweno_t h, unsigned* bits, int n);
 /* Per-kernel timing (instrumentation; no counterpart in the paper).  With
  * enable != 0, every kernel launch of later steps is bracketed by CUDA events
  * on the handle's stream.  hweno_profile_read synchronises and writes, for the
- * nkinds >= 4 kernel kinds {0 reconstruct, 1 indicator + modification,
- * 2 reconstruct troubled cells, 3 fluxes + quadrature + Runge-Kutta update},
- * the summed device milliseconds and launch counts since the last read. */
+ * first nkinds (>= 4) kernel kinds {0 reconstruct, 1 indicator + modification
+ * (KXRCF, or its fallback pass after the learned indicator), 2 reconstruct
+ * troubled cells, 3 fluxes + quadrature + Runge-Kutta update, 4 learned
+ * indicator network pass}, the summed device milliseconds and launch counts
+ * since the last read (kinds past nkinds are dropped; slots past the last kind
+ * are zeroed). */
 hweno_status hweno_profile(hweno_t h, int enable);
 hweno_status hweno_profile_read(hweno_t h, double* ms, int* launches, int nkinds);
 

@@ -412,7 +412,7 @@ void stage_t(const Prob& P, const HostTabs& HT, const Weights<T>& W, const Beta2
     // the cells it flags are reconstructed again.
     int* ucnt = B.und_count + S.stage;
     cudaMemsetAsync(ucnt, 0, sizeof(int), st);
-    if (B.prof) B.prof->begin(1, st);
+    if (B.prof) B.prof->begin(4, st);
     run_mlpre2d(P, B.mlp, B.mlp_conf, S.Uin, S.mask, S.Mod, B.und, ucnt, B.mlp_stats, B.mlp_prob, st);
     if (B.prof) B.prof->end(st);
     if (B.prof) B.prof->begin(0, st);

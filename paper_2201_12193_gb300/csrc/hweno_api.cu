@@ -552,15 +552,17 @@ hweno_status hweno_profile(hweno_t h, int enable) {
   CK(h, cudaStreamSynchronize(h->stream));
   double ms[hw::Prof::KINDS];
   int n[hw::Prof::KINDS];
-  h->prof.read(ms, n);    // drop anything recorded so far
+  h->prof.read(ms, n, hw::Prof::KINDS);    // drop anything recorded so far
   h->B.prof = enable ? &h->prof : nullptr;
   return HWENO_OK;
 }
 
 hweno_status hweno_profile_read(hweno_t h, double* ms, int* launches, int nkinds) {
-  if (!h || !ms || !launches || nkinds < hw::Prof::KINDS) return fail(h, HWENO_EINVAL, "profile_read: need 4 slots");
+  if (!h) return HWENO_EINVAL;
+  if (!ms || !launches || nkinds < 4) return fail(h, HWENO_EINVAL, "profile_read: need at least 4 slots");
   CK(h, cudaStreamSynchronize(h->stream));
-  h->prof.read(ms, launches);
+  h->prof.read(ms, launches, std::min(nkinds, hw::Prof::KINDS));
+  for (int k = hw::Prof::KINDS; k < nkinds; ++k) { ms[k] = 0.0; launches[k] = 0; }
   CK(h, cudaGetLastError());
   return HWENO_OK;
 }

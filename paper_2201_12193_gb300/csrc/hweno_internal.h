@@ -23,7 +23,9 @@ struct HostTabs {
 // Optional per-kernel timing: CUDA events recorded around each launch on the
 // launching stream, read back (and summed per kernel kind) after a sync.
 struct Prof {
-  static constexpr int KINDS = 4;   // 0 reconstruct, 1 indicator + modify, 2 reconstruct troubled, 3 flux + update
+  // 0 reconstruct, 1 indicator + modify, 2 reconstruct troubled, 3 flux + update,
+  // 4 learned-indicator network pass
+  static constexpr int KINDS = 5;
   std::vector<cudaEvent_t> pool;
   std::vector<int> kinds;           // kind of each begin/end pair
   size_t used = 0;                  // events handed out
@@ -37,10 +39,11 @@ struct Prof {
   }
   void begin(int kind, cudaStream_t s) { kinds.push_back(kind); cudaEventRecord(next(), s); }
   void end(cudaStream_t s) { cudaEventRecord(next(), s); }
-  // Sum elapsed ms per kind into ms[KINDS] and launches[KINDS]; then reset.
-  void read(double* ms, int* launches) {
-    for (int k = 0; k < KINDS; ++k) { ms[k] = 0.0; launches[k] = 0; }
+  // Sum elapsed ms per kind into ms[n] and launches[n] (kinds >= n dropped); then reset.
+  void read(double* ms, int* launches, int n) {
+    for (int k = 0; k < n; ++k) { ms[k] = 0.0; launches[k] = 0; }
     for (size_t p = 0; p < kinds.size(); ++p) {
+      if (kinds[p] >= n) continue;
       float t = 0.f;
       cudaEventSynchronize(pool[2 * p + 1]);
       cudaEventElapsedTime(&t, pool[2 * p], pool[2 * p + 1]);

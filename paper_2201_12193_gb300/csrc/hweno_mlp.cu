@@ -17,7 +17,8 @@ namespace hw {
 namespace {
 
 constexpr int NIN = 108, NINP = 112, NH = 64;
-constexpr int S1 = 120;   // padded row stride (bf16) of 112-wide rows: conflict-free fragment loads
+constexpr int S1 = 114;   // row stride (bf16) of 112-wide rows: 57 words (odd), so per-row stores by
+                          // 32 threads and the fragment loads hit distinct banks
 constexpr int S2 = 72;    // padded row stride of 64-wide rows
 constexpr float CLIPF = 8.0f;
 
@@ -34,51 +35,85 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const unsigned (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+// erf by the rational approximation of Abramowitz & Stegun, Handbook of
+// Mathematical Functions, formula 7.1.26 (Hastings): for z >= 0,
+// erf z = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) exp(-z^2), t = 1 / (1 + p z),
+// with |error| <= 1.5e-7, odd extension for z < 0.  About a dozen instructions
+// (one reciprocal, one exponential), against the far longer erff: the hidden
+// activations are BF16-rounded (2^-9 relative) after this.
+__device__ __forceinline__ float erf_as(float z) {
+  const float a = fabsf(z);
+  const float t = __frcp_rn(fmaf(0.3275911f, a, 1.0f));
+  const float poly =
+      t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+  return copysignf(1.0f - poly * __expf(-a * a), z);
+}
+
+// GELU x Phi(x) = x (1 + erf(x / sqrt 2)) / 2 and its derivative Phi(x) + x phi(x).
+__device__ __forceinline__ float gelu(float x) { return 0.5f * x * (1.0f + erf_as(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float x) {
-  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * expf(-0.5f * x * x) * 0.39894228040143268f;
+  return 0.5f * (1.0f + erf_as(x * 0.70710678118654752f)) + x * __expf(-0.5f * x * x) * 0.39894228040143268f;
 }
 
 // ---------------------------------------------------------------- features
+// Double -> float by the IEEE-754 bit layout (sign, exponent rebias 1023 -> 127,
+// mantissa truncated to 23 bits): integer ALU only, no FP64 pipe.  Magnitudes
+// below 2^-126 become 0 (the features are normalised and BF16-rounded after
+// this, so the truncation's 2^-23 relative error is far below their rounding).
+__device__ __forceinline__ float d2f_trunc(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int e = (int)((hi >> 20) & 0x7FFu) - (1023 - 127);
+  if (e <= 0) return 0.0f;
+  if (e >= 255) return __uint_as_float((hi & 0x80000000u) | 0x7F800000u);
+  return __uint_as_float((hi & 0x80000000u) | ((unsigned)e << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29));
+}
+
+__device__ __forceinline__ float clipf(float x) { return fminf(CLIPF, fmaxf(-CLIPF, x)); }
+
 // 108 normalised features of cell (i, j): per variable and 3x3 cell k (paper
 // label order), (ubar_k - ubar_c, vbar_k, wbar_k) / D with
 // D = max |ubar_k - ubar_c| + h^2 max |ubar_k| + 1e-12 (h^2 |u| is the scale
 // KXRCF compares jumps against), the centre's own average slot holding
 // ubar_c / (max |ubar_k| + 1e-12); clipped to [-8, 8]; boundary images as in
-// the scheme.
-__device__ __forceinline__ void cell_features(const Prob& P, const double* __restrict__ U, int i, int j,
-                                              float (&f)[NIN]) {
+// the scheme.  The differences ubar_k - ubar_c are taken in FP64 (they cancel),
+// everything after in FP32.  emit(q, value) receives feature q.
+template <typename Emit>
+__device__ __forceinline__ void cell_features(const Prob& P, const double* __restrict__ U, int i, int j, Emit emit) {
   int xi[3], xs[3], yj[3], ys[3];
 #pragma unroll
   for (int o = -1; o <= 1; ++o) {
     const Img a = image(P, i + o, j), b = image(P, i, j + o);
     xi[o + 1] = a.i; xs[o + 1] = a.sx; yj[o + 1] = b.j; ys[o + 1] = b.sy;
   }
+  const float h2 = (float)(P.dx * P.dx);
 #pragma unroll 1
   for (int v = 0; v < 4; ++v) {
-    double u[9], vb[9], wb[9];
+    const double* U0 = U + (long long)(v * 3) * P.plane;
+    const double* U1 = U0 + P.plane;
+    const double* U2 = U1 + P.plane;
+    const long long oc = (long long)yj[1] * P.pitch + xi[1];
+    const double uc = U0[oc];
+    float du[9], vb[9], wb[9];
+    float D = 0.f, umax = 0.f;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       const int ox = k % 3, oy = k / 3;
       const long long so = (long long)yj[oy] * P.pitch + xi[ox];
-      u[k] = U[(long long)(v * 3) * P.plane + so];
-      vb[k] = xs[ox] * U[(long long)(v * 3 + 1) * P.plane + so];
-      wb[k] = ys[oy] * U[(long long)(v * 3 + 2) * P.plane + so];
+      const double uk = U0[so];
+      du[k] = d2f_trunc(uk - uc);
+      umax = fmaxf(umax, fabsf(d2f_trunc(uk)));
+      D = fmaxf(D, fabsf(du[k]));
+      const float a = d2f_trunc(U1[so]), b = d2f_trunc(U2[so]);
+      vb[k] = xs[ox] < 0 ? -a : a;
+      wb[k] = ys[oy] < 0 ? -b : b;
     }
-    double D = 0.0, umax = 0.0;
+    const float inv = 1.0f / (D + h2 * umax + 1e-12f);
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-      D = fmax(D, fabs(u[k] - u[4]));
-      umax = fmax(umax, fabs(u[k]));
+      emit(v * 27 + k, k == 4 ? clipf(d2f_trunc(uc) / (umax + 1e-12f)) : clipf(du[k] * inv));
+      emit(v * 27 + 9 + k, clipf(vb[k] * inv));
+      emit(v * 27 + 18 + k, clipf(wb[k] * inv));
     }
-    const double inv = 1.0 / (D + P.dx * P.dx * umax + 1e-12);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      f[v * 27 + k] = fminf(CLIPF, fmaxf(-CLIPF, (float)((u[k] - u[4]) * inv)));
-      f[v * 27 + 9 + k] = fminf(CLIPF, fmaxf(-CLIPF, (float)(vb[k] * inv)));
-      f[v * 27 + 18 + k] = fminf(CLIPF, fmaxf(-CLIPF, (float)(wb[k] * inv)));
-    }
-    f[v * 27 + 4] = fminf(CLIPF, fmaxf(-CLIPF, (float)(u[4] / (umax + 1e-12))));
   }
 }
 
@@ -87,10 +122,8 @@ __global__ void features_kernel(Prob P, const double* __restrict__ U, const int*
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const int c = cells[t];
-  float f[NIN];
-  cell_features(P, U, c % P.nx, c / P.nx, f);
-#pragma unroll 4
-  for (int q = 0; q < NIN; ++q) X[(long long)t * NIN + q] = f[q];
+  float* row = X + (long long)t * NIN;
+  cell_features(P, U, c % P.nx, c / P.nx, [&](int q, float x) { row[q] = x; });
 }
 
 // ---------------------------------------------------------------- parameters
@@ -98,12 +131,11 @@ __global__ void features_kernel(Prob P, const double* __restrict__ U, const int*
 constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NH * NIN, OFF_W2 = OFF_B1 + NH, OFF_B2 = OFF_W2 + NH * NH,
               OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NH, NPARAM = OFF_B3 + 1;
 
-// Weights staged in shared memory: BF16 W1 [64][S1] (K padded to 112), W2 and
-// W2^T [64][S2]; FP32 b1, b2, W3, b3.
+// Forward weights staged in shared memory: BF16 W1 [64][S1] (K padded to 112)
+// and W2 [64][S2]; FP32 b1, b2, W3, b3.  (Training adds W2^T.)
 struct WSmem {
   __nv_bfloat16 w1[NH * S1];
   __nv_bfloat16 w2[NH * S2];
-  __nv_bfloat16 w2t[NH * S2];
   float b1[NH], b2[NH], w3[NH], b3;
 };
 
@@ -115,7 +147,6 @@ __device__ void load_weights(const float* __restrict__ th, WSmem& S) {
   for (int q = threadIdx.x; q < NH * S2; q += blockDim.x) {
     const int o = q / S2, k = q % S2;
     S.w2[q] = __float2bfloat16_rn(k < NH ? th[OFF_W2 + o * NH + k] : 0.0f);
-    S.w2t[q] = __float2bfloat16_rn(k < NH ? th[OFF_W2 + k * NH + o] : 0.0f);
   }
   for (int q = threadIdx.x; q < NH; q += blockDim.x) {
     S.b1[q] = th[OFF_B1 + q];
@@ -234,6 +265,7 @@ constexpr int TT = 128, TR = 64;
 
 struct TSmem {
   WSmem W;
+  __nv_bfloat16 w2t[NH * S2];     // W2^T
   __nv_bfloat16 xs[TR * S1];      // X tile [row][feature]
   __nv_bfloat16 xt[NINP * S2];    // X^T [feature][row]
   __nv_bfloat16 h1t[NH * S2];     // h1^T
@@ -251,6 +283,10 @@ __global__ void __launch_bounds__(TT) mlp_train_kernel(const float* __restrict__
   extern __shared__ __align__(16) unsigned char smem[];
   TSmem& S = *reinterpret_cast<TSmem*>(smem);
   load_weights(th, S.W);
+  for (int q = threadIdx.x; q < NH * S2; q += TT) {
+    const int o = q / S2, k = q % S2;
+    S.w2t[q] = __float2bfloat16_rn(k < NH ? th[OFF_W2 + k * NH + o] : 0.0f);
+  }
   for (int q = threadIdx.x; q < NH * NINP; q += TT) S.gw1[q] = 0.f;
   for (int q = threadIdx.x; q < NH * NH; q += TT) S.gw2[q] = 0.f;
   for (int q = threadIdx.x; q < NH; q += TT) { S.gb1[q] = 0.f; S.gb2[q] = 0.f; S.gw3[q] = 0.f; }
@@ -335,7 +371,7 @@ __global__ void __launch_bounds__(TT) mlp_train_kernel(const float* __restrict__
     for (int kb = 0; kb < 4; ++kb)
 #pragma unroll
       for (int nb = 0; nb < 8; ++nb) {
-        const __nv_bfloat16* w = S.W.w2t + (nb * 8 + g) * S2 + kb * 16 + 2 * t;
+        const __nv_bfloat16* w = S.w2t + (nb * 8 + g) * S2 + kb * 16 + 2 * t;
         mma16816(dh1[nb], da2f[kb], *reinterpret_cast<const unsigned*>(w), *reinterpret_cast<const unsigned*>(w + 8));
       }
 #pragma unroll
@@ -457,14 +493,14 @@ __global__ void __launch_bounds__(MTN) mlpre2d_kernel(Prob P, const float* __res
     const bool valid = i < P.nx && j < P.ny;
     __syncthreads();   // the weights are staged; Xs / zs of the previous tile are free
     {
-      float f[NIN];
-      if (valid) cell_features(P, U, i, j, f);
-#pragma unroll 4
-      for (int q = 0; q < S1; q += 2) {
-        const float lo = (valid && q < NIN) ? f[q] : 0.f;
-        const float hi = (valid && q + 1 < NIN) ? f[q + 1] : 0.f;
-        *reinterpret_cast<unsigned*>(Xs + tid * S1 + q) = pack_bf16(lo, hi);
+      __nv_bfloat16* row = Xs + tid * S1;
+      if (valid) {
+        cell_features(P, U, i, j, [&](int q, float x) { row[q] = __float2bfloat16_rn(x); });
+      } else {
+        for (int q = 0; q < NIN; q += 2) *reinterpret_cast<unsigned*>(row + q) = 0u;
       }
+#pragma unroll
+      for (int q = NIN; q < NINP; q += 2) *reinterpret_cast<unsigned*>(row + q) = 0u;   // K padding
     }
     __syncthreads();
     {
@@ -561,7 +597,7 @@ cudaError_t run_mlpre2d(const Prob& P, const float* th, float conf, const double
                         int* und, int* und_count, int* stats, float* prob, cudaStream_t st) {
   const size_t sm = sizeof(WSmem) + MTN * S1 * sizeof(__nv_bfloat16) + MTN * sizeof(float);
   const long long ntiles = (long long)((P.nx + MTX - 1) / MTX) * ((P.ny + MTY - 1) / MTY);
-  const unsigned grd = (unsigned)std::min<long long>(ntiles, (long long)P.nsm * 3);
+  const unsigned grd = (unsigned)std::min<long long>(ntiles, (long long)P.nsm * 4);   // 4 blocks fit an SM
   cudaError_t e = cudaFuncSetAttribute(mlpre2d_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   mlpre2d_kernel<<<grd, MTN, sm, st>>>(P, th, conf, U, mask, Mod, und, und_count, stats, prob);

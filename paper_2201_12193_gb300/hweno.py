@@ -251,16 +251,17 @@ class Solver:
         self._check(lib().hweno_features(self._h, ctypes.c_void_p(_ptr(U)[0]), ctypes.c_void_p(_ptr(cells)[0]),
                                          int(cells.numel()), ctypes.c_void_p(_ptr(X)[0])))
 
-    KERNEL_KINDS = ("reconstruct", "indicator", "reconstruct_troubled", "update")
+    KERNEL_KINDS = ("reconstruct", "indicator", "reconstruct_troubled", "update", "learned_indicator")
 
     def profile(self, enable=True):
         self._check(lib().hweno_profile(self._h, int(bool(enable))))
 
     def profile_read(self):
         """{kind: (device ms, launches)} since the last read."""
-        ms = (ctypes.c_double * 4)()
-        n = (ctypes.c_int * 4)()
-        self._check(lib().hweno_profile_read(self._h, ms, n, 4))
+        k = len(self.KERNEL_KINDS)
+        ms = (ctypes.c_double * k)()
+        n = (ctypes.c_int * k)()
+        self._check(lib().hweno_profile_read(self._h, ms, n, k))
         return {k: (ms[i], n[i]) for i, k in enumerate(self.KERNEL_KINDS)}
 
     def run(self, t_end, cfl=0.6, dt=None, max_steps=10 ** 9):
