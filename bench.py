@@ -153,9 +153,16 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate(cells_per_rank, stages, steps, world, ms_max):
+    """Whole-job throughput: the cell-updates all ranks did over the slowest
+    rank's time (weak scaling: every rank advances its own problem)."""
+    return cells_per_rank * stages * steps * world / (ms_max * 1e-3)
 
 
 # ------------------------------------------------------------------ oracle timing (CPU)
@@ -280,7 +287,7 @@ def run_batched(torch, hweno, args, world, rank):
         s.sync()
         finals[prec] = [s.get_moments(k) for k in range(0, len(probs), 8)]
         s.close()
-        out[f"batched_{prec}"] = {"value": cells * 3 * steps * world / (ms * 1e-3), "ms_per_step": ms / steps,
+        out[f"batched_{prec}"] = {"value": aggregate(cells, 3, steps, world, ms), "ms_per_step": ms / steps,
                                   "problems": len(probs), "cells": cells, "graph": graph,
                                   "tile": autotune.VARIANTS[variant], "launches_per_step": 3}
     num = sum(float(np.abs(a - b).sum()) for a, b in zip(finals["fp32"], finals["fp64"]))
@@ -359,7 +366,7 @@ def run_learned(torch, hweno, args, world, rank):
         out = torch.empty(s.shape, dtype=torch.float64, device="cuda")
         s.get_moments(out)
         finals[mode] = out
-        res[mode] = {"value": cells * 3 * steps * world / (ms * 1e-3), "ms_per_step": ms / steps,
+        res[mode] = {"value": aggregate(cells, 3, steps, world, ms), "ms_per_step": ms / steps,
                      "rerecon_cells_per_stage": rer / (3 * steps), "prof": prof, "fallbacks": fb}
         s.close()
     a, b = finals["mlp"], finals["kxrcf"]
@@ -433,7 +440,7 @@ def run_ours(args, world, rank, local):
     s64, ms, prof, clk, out64 = run_solver(torch, hweno, p, args.precision, args.steps, args.warmup, world,
                                            profile=True, clocks=clocks)
     ms = max_over_ranks(ms, world)
-    value = cells * 3 * args.steps * world / (ms * 1e-3)
+    value = aggregate(cells, 3, args.steps, world, ms)
     ms_step = ms / args.steps
 
     # roofline of the dominant kernel (largest share of device time)
@@ -461,7 +468,7 @@ def run_ours(args, world, rank, local):
         ms32 = max_over_ranks(ms32, world)
         a = out32.cpu().numpy()
         b = out64.cpu().numpy()
-        forms["fp32bulk"] = {"value": cells * 3 * args.steps * world / (ms32 * 1e-3), "ms_per_step": ms32 / args.steps,
+        forms["fp32bulk"] = {"value": aggregate(cells, 3, args.steps, world, ms32), "ms_per_step": ms32 / args.steps,
                              "dtype": "f32 (state and RK accumulation f64)",
                              "rel_l1_vs_fp64_after_steps": float(np.abs(a - b).sum() / np.abs(b).sum()),
                              "steps_compared": args.warmup + args.steps,
@@ -545,11 +552,13 @@ def run_reference(args, world, rank):
 
 def main():
     args = parse()
-    world, rank, local = dist_init()
     if args.impl == "reference":
-        run_reference(args, world, rank)
-    else:
-        run_ours(args, world, rank, local)
+        # the oracle arm runs on rank 0 alone; other ranks exit without work
+        # (and without a process group: the arm has no collective)
+        run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
+        return
+    world, rank, local = dist_init()
+    run_ours(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
