@@ -192,6 +192,39 @@ def time_oracle(p, half, steps):
                                        f"{steps} SSP-RK3 step(s) ({cells * 3 * steps} cell-updates)"
 
 
+def _oracle_worker(args):
+    """One pool worker: the oracle on its own window, one SSP-RK3 step (spawned)."""
+    n, seed, half, start = args
+    import time as _t
+    from paper_2201_12193_gb300 import workloads as W
+    p = W.four_quadrant_2d(n, seed=seed)
+    oracle, cfg, m = oracle_window(p, half)
+    oracle.build()
+    while _t.time() < start:          # all workers start together
+        _t.sleep(0.001)
+    t0 = _t.perf_counter()
+    m, _, rc = oracle.step(cfg, m, oracle.max_dt(cfg, m, CFL))
+    return (2 * half) ** 2 * 3, _t.perf_counter() - t0, rc
+
+
+def time_oracle_all_cores(n, half):
+    """The oracle as it stands, one process per host core (spawned pool), each
+    on the same-size window for one step; value = all cell-updates over the
+    slowest worker's time."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(int, range(cores))    # workers up before the clock starts
+        start = time.time() + 3.0
+        res = pool.map(_oracle_worker, [(n, 0, half, start)] * cores)
+    if any(r[2] != 0 for r in res):
+        raise RuntimeError("oracle step failed")
+    work = sum(r[0] for r in res)
+    slow = max(r[1] for r in res)
+    return work / slow, cores, slow
+
+
 # ------------------------------------------------------------------ our arm
 
 def run_solver(torch, hweno, p, precision, steps, warmup, world, profile=False, clocks=None):
@@ -299,6 +332,27 @@ def run_batched(torch, hweno, args, world, rank):
 
 
 MLP_FLOP_PER_CELL = 2 * (108 * 64 + 64 * 64 + 64)    # 11,072 multiply-adds per cell
+
+
+def _rec_traffic_per_cell():
+    """DRAM bytes per cell of one rec2d launch from the committed ncu summary, or
+    None when the kernel sources changed since that capture."""
+    import hashlib
+    import re
+    try:
+        with open(os.path.join(ROOT, "profiles", "rec2d_fp64_four_quadrant_traffic.md")) as f:
+            txt = f.read()
+    except OSError:
+        return None
+    m1 = re.search(r"^bytes_per_cell: ([0-9.]+)$", txt, re.M)
+    m2 = re.search(r"^source_sha256: ([0-9a-f]{64})$", txt, re.M)
+    if not (m1 and m2):
+        return None
+    h = hashlib.sha256()
+    for f in ("hweno_2d.cu", "hweno_device.cuh", "hweno_parity.h", "hweno_internal.h"):
+        with open(os.path.join(ROOT, "paper_2201_12193_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return float(m1.group(1)) if h.hexdigest() == m2.group(1) else None
 
 
 def _peaks():
@@ -454,6 +508,10 @@ def run_ours(args, world, rank, local):
                 "peak": FP64_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_NOMINAL,
                 "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (recipe table); FMA probe measured 1.05",
                 "traffic": None, "launches": kn, "avg_ms": kms / kn, "share": kms / total_kernel_ms}
+        bpc = _rec_traffic_per_cell() if args.precision == "fp64" else None
+        if bpc:
+            roof["traffic"] = bpc * cells
+            roof["traffic_unit"] = "bytes per launch (ncu dram read+write, profiles/rec2d_fp64_four_quadrant_traffic.md)"
     kernels = {k: {"ms": v[0], "launches": v[1], "share": v[0] / total_kernel_ms} for k, v in prof.items()}
     hbm = {"algorithmic_GBps": ALGO_BYTES_PER_CELL_STAGE * cells * 3 * args.steps / (ms * 1e-3) / 1e9,
            "peak_GBps": 6796.2}
@@ -506,6 +564,12 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu:
         v, secs, sample = time_oracle(p, 128, 1)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, "seconds": secs}
+        try:
+            va, cores, slow = time_oracle_all_cores(p.nx, 64)
+            cpu["all_cores"] = {"value": va, "unit": UNIT, "cores": cores, "seconds": slow,
+                                "sample": f"{cores} processes, each one SSP-RK3 step of a 128x128 centre window"}
+        except Exception as e:     # the single-core figure stands on its own
+            cpu["all_cores"] = {"unavailable": str(e)[:200]}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
