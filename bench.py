@@ -532,6 +532,22 @@ def run_ours(args, world, rank, local):
                              "steps_compared": args.warmup + args.steps,
                              "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof32.items()}}
         s32.close()
+        sx, msx, profx, _, outx = run_solver(torch, hweno, p, "df64", args.steps, args.warmup, world, profile=True)
+        msx = max_over_ranks(msx, world)
+        a = outx.cpu().numpy()
+        forms["df64"] = {"value": aggregate(cells, 3, args.steps, world, msx), "ms_per_step": msx / args.steps,
+                         "dtype": "f32x2 double-float (48-bit significand; state and RK accumulation f64)",
+                         "rel_l1_vs_fp64_after_steps": float(np.abs(a - b).sum() / np.abs(b).sum()),
+                         "steps_compared": args.warmup + args.steps,
+                         "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in profx.items()}}
+        kx, (kxms, kxn) = "reconstruct", profx["reconstruct"]
+        if kxn:
+            ach = _rec_flop_per_cell(4) * cells * kxn / (kxms * 1e-3)
+            forms["df64"]["roofline_reconstruct"] = {
+                "bound": "alu", "achieved_fp64_equiv_tflops": ach / 1e12,
+                "note": "algorithmic FP64-equivalent flop of the reconstruction per second; the FP32 pipe "
+                        "executes ~6-15 FP32 instructions per double-float operation"}
+        sx.close()
 
     if not args.no_forms and not args.no_batch:
         forms.update(run_batched(torch, hweno, args, world, rank))

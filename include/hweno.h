@@ -69,7 +69,10 @@ typedef enum { HWENO_IND_NONE = 0, HWENO_IND_KXRCF = 1, HWENO_IND_ALL = 2, HWENO
  *   eq: advection (f = adv_a u, g = adv_b u), Burgers (f = g = u^2/2) or Euler.
  *   precision: 0 = FP64 throughout; 1 = FP32 reconstruction, indicator, flux
  *   and quadrature with FP64 state, FP64 Runge-Kutta accumulation and FP64
- *   differences of the face fluxes in the cell-average equation.
+ *   differences of the face fluxes in the cell-average equation; 2 = the same
+ *   split with double-float arithmetic (pairs of FP32 numbers, a 48-bit
+ *   significand and FP32's exponent range; magnitudes below 2^-74 keep FP32
+ *   precision) in place of FP32 (single-problem handles only).
  *   indicator: HWENO_IND_KXRCF is the scheme (HWENO6-M5-I); NONE gives HWENO6
  *   (no modification); ALL gives HWENO6-M5-NI (every cell modified) (Sec. 3);
  *   MLP: the learned indicator with KXRCF fallback (see below; 2D Euler).

@@ -47,8 +47,8 @@ __global__ void __launch_bounds__(RB) rec1d_kernel(Prob P, Weights<T> W, Beta1<T
       T d[6];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        d[c] = T(load_mom1<FLAGGED>(P, U, mask, Mod, v, 0, nb[c]));
-        d[3 + c] = T(load_mom1<FLAGGED>(P, U, mask, Mod, v, 1, nb[c]));
+        d[c] = from_double<T>(load_mom1<FLAGGED>(P, U, mask, Mod, v, 0, nb[c]));
+        d[3 + c] = from_double<T>(load_mom1<FLAGGED>(P, U, mask, Mod, v, 1, nb[c]));
       }
       T out[4];
       recon1d<T>(W, B, d, out);
@@ -231,12 +231,14 @@ void stage_t(const Prob& P, const Weights<T>& W, const Beta1<T>& Bt, const Bufs&
 
 }  // namespace
 
-void run_stage_1d(const Prob& P, const HostTabs& T, int fp32, const Bufs& B, const StageCall& S, cudaStream_t st) {
+void run_stage_1d(const Prob& P, const HostTabs& T, int prec, const Bufs& B, const StageCall& S, cudaStream_t st) {
   if (P.nvar == 3) {
-    if (fp32) stage_t<float, 3>(P, T.wf, T.b1f, B, S, st);
+    if (prec == PREC_FP32) stage_t<float, 3>(P, T.wf, T.b1f, B, S, st);
+    else if (prec == PREC_DF64) stage_t<df64, 3>(P, T.wx, T.b1x, B, S, st);
     else stage_t<double, 3>(P, T.wd, T.b1d, B, S, st);
   } else {
-    if (fp32) stage_t<float, 1>(P, T.wf, T.b1f, B, S, st);
+    if (prec == PREC_FP32) stage_t<float, 1>(P, T.wf, T.b1f, B, S, st);
+    else if (prec == PREC_DF64) stage_t<df64, 1>(P, T.wx, T.b1x, B, S, st);
     else stage_t<double, 1>(P, T.wd, T.b1d, B, S, st);
   }
 }

@@ -85,7 +85,7 @@ __device__ __forceinline__ void rec2d_cell(const Prob& P, const Weights<T>& W, c
     for (int c = 0; c < 23; ++c) {
       int kind, ox, oy;
       d4_slot(c, kind, ox, oy);
-      d[c] = T(load_mom<MODE>(P, U, mask, Mod, nb, v, kind, ox, oy, usemod));
+      d[c] = from_double<T>(load_mom<MODE>(P, U, mask, Mod, nb, v, kind, ox, oy, usemod));
     }
     T out[16];
     recon2d<T>(W, B, d, out);
@@ -102,7 +102,7 @@ __device__ __forceinline__ void rec2d_cell(const Prob& P, const Weights<T>& W, c
             T x[12], r[12];
 #pragma unroll
             for (int q = 0; q < 12; ++q) x[q] = out[bp[q]];
-            batch_inverse<12, T>(x, r);
+            batch_inverse_ranged<12, T>(x, r);
 #pragma unroll
             for (int q = 0; q < 12; ++q) rinv[bp[q]] = r[q];
           } else {
@@ -324,7 +324,7 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
     T rho[16], inv[16];
 #pragma unroll
     for (int p = 0; p < 16; ++p) rho[p] = G[(long long)p * P.gplane + goff(P, i, j)];
-    batch_inverse<16, T>(rho, inv);
+    batch_inverse_ranged<16, T>(rho, inv);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
@@ -627,12 +627,14 @@ cudaError_t run_batch_stage(const HostTabs& T, int fp32, int tile_variant, const
 namespace {
 }  // namespace
 
-void run_stage_2d(const Prob& P, const HostTabs& T, int fp32, const Bufs& B, const StageCall& S, cudaStream_t st) {
+void run_stage_2d(const Prob& P, const HostTabs& T, int prec, const Bufs& B, const StageCall& S, cudaStream_t st) {
   if (P.nvar == 4) {
-    if (fp32) stage_t<float, 4>(P, T, T.wf, T.b2f, B, S, st);
+    if (prec == PREC_FP32) stage_t<float, 4>(P, T, T.wf, T.b2f, B, S, st);
+    else if (prec == PREC_DF64) stage_t<df64, 4>(P, T, T.wx, T.b2x, B, S, st);
     else stage_t<double, 4>(P, T, T.wd, T.b2d, B, S, st);
   } else {
-    if (fp32) stage_t<float, 1>(P, T, T.wf, T.b2f, B, S, st);
+    if (prec == PREC_FP32) stage_t<float, 1>(P, T, T.wf, T.b2f, B, S, st);
+    else if (prec == PREC_DF64) stage_t<df64, 1>(P, T, T.wx, T.b2x, B, S, st);
     else stage_t<double, 1>(P, T, T.wd, T.b2d, B, S, st);
   }
 }

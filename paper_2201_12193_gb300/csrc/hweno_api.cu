@@ -21,7 +21,7 @@ struct hweno_s {
   cudaStream_t stream = nullptr;
   Prob P{};
   hw::HostTabs T{};
-  int fp32 = 0;
+  int fp32 = 0;                  // compute precision (hw::PREC_*)
   double* U[3] = {nullptr, nullptr, nullptr};
   int cur = 0, prev = 0;
   bool have_state = false, stepped = false;
@@ -79,6 +79,12 @@ size_t nstate(const hweno_s* h) { return (size_t)h->P.nvar * h->P.nmom * ncell(h
 
 // Linear weights of eq. (linear-weight) and the smoothness-indicator rows of
 // eq. (beta) / (2D-beta) for p_l = (S_l q_l - S_{l-1} q_{l-1}) / g_l.
+// A long double as a double-float pair (hi = nearest float, lo = nearest float of the rest).
+hw::df64 dfx(long double v) {
+  const float hi = (float)v;
+  return hw::df64(hi, (float)(v - (long double)hi));
+}
+
 void build_tables(hweno_s* h) {
   const double* g = h->g.gamma_bar;
   long double S[5] = {0, 0, 0, 0, 0};
@@ -92,9 +98,13 @@ void build_tables(hweno_s* h) {
     wf.gam[l - 1] = (float)wd.gam[l - 1];
     wf.sg[l - 1] = (float)wd.sg[l - 1];
     wf.s1g[l - 1] = (float)wd.s1g[l - 1];
+    h->T.wx.gam[l - 1] = dfx(g[l - 1] / S[4]);
+    h->T.wx.sg[l - 1] = dfx(S[l] / g[l - 1]);
+    h->T.wx.s1g[l - 1] = dfx(S[l - 1] / g[l - 1]);
   }
   wd.eps = 1e-10;
   wf.eps = 1e-10f;
+  h->T.wx.eps = dfx(1e-10L);
   auto coef = [&](int l, long double& a, long double& b) {
     if (h->g.beta_of_q) { a = 1.0L; b = 0.0L; return; }
     a = S[l] / g[l - 1];
@@ -102,22 +112,23 @@ void build_tables(hweno_s* h) {
   };
   long double a, b;
   // flat rows: B_l[k] = a_l RC_l_l[k] + b_l RC_l_(l-1)[k]; q_1 is constant, so level 2 has no b part
-  auto fill = [&](int l, const double* rl, const double* rm, int n, double* outd, float* outf) {
+  auto fill = [&](int l, const double* rl, const double* rm, int n, double* outd, float* outf, hw::df64* outx) {
     coef(l, a, b);
     for (int k = 0; k < n; ++k) {
       const long double v = a * rl[k] + (rm ? b * rm[k] : 0.0L);
       outd[k] = (double)v;
       outf[k] = (float)v;
+      outx[k] = dfx(v);
     }
   };
   if (h->g.dim == 1) {
-    fill(2, hwp::D1P_RC2_2, nullptr, hwp::D1_NB2, h->T.b1d.B2, h->T.b1f.B2);
-    fill(3, hwp::D1P_RC3_3, hwp::D1P_RC3_2, hwp::D1_NB3, h->T.b1d.B3, h->T.b1f.B3);
-    fill(4, hwp::D1P_RC4_4, hwp::D1P_RC4_3, hwp::D1_NB4, h->T.b1d.B4, h->T.b1f.B4);
+    fill(2, hwp::D1P_RC2_2, nullptr, hwp::D1_NB2, h->T.b1d.B2, h->T.b1f.B2, h->T.b1x.B2);
+    fill(3, hwp::D1P_RC3_3, hwp::D1P_RC3_2, hwp::D1_NB3, h->T.b1d.B3, h->T.b1f.B3, h->T.b1x.B3);
+    fill(4, hwp::D1P_RC4_4, hwp::D1P_RC4_3, hwp::D1_NB4, h->T.b1d.B4, h->T.b1f.B4, h->T.b1x.B4);
   } else {
-    fill(2, hwp::D2P_RC2_2, nullptr, hwp::D2_NB2, h->T.b2d.B2, h->T.b2f.B2);
-    fill(3, hwp::D2P_RC3_3, hwp::D2P_RC3_2, hwp::D2_NB3, h->T.b2d.B3, h->T.b2f.B3);
-    fill(4, hwp::D2P_RC4_4, hwp::D2P_RC4_3, hwp::D2_NB4, h->T.b2d.B4, h->T.b2f.B4);
+    fill(2, hwp::D2P_RC2_2, nullptr, hwp::D2_NB2, h->T.b2d.B2, h->T.b2f.B2, h->T.b2x.B2);
+    fill(3, hwp::D2P_RC3_3, hwp::D2P_RC3_2, hwp::D2_NB3, h->T.b2d.B3, h->T.b2f.B3, h->T.b2x.B3);
+    fill(4, hwp::D2P_RC4_4, hwp::D2P_RC4_3, hwp::D2_NB4, h->T.b2d.B4, h->T.b2f.B4, h->T.b2x.B4);
   }
 }
 
@@ -130,7 +141,9 @@ hweno_status validate(const hweno_grid* g, const hweno_bc* bc, double gamma, std
     why = "empty or non-finite domain"; return HWENO_EINVAL;
   }
   if (g->eq < 0 || g->eq > 2) { why = "eq must be advection, burgers or euler"; return HWENO_EINVAL; }
-  if (g->precision != 0 && g->precision != 1) { why = "precision must be 0 (fp64) or 1 (fp32 bulk)"; return HWENO_EINVAL; }
+  if (g->precision < 0 || g->precision > 2) {
+    why = "precision must be 0 (fp64), 1 (fp32 bulk) or 2 (double-float)"; return HWENO_EINVAL;
+  }
   if (g->indicator < 0 || g->indicator > 3) { why = "indicator must be none, kxrcf, all or mlp"; return HWENO_EINVAL; }
   if (g->indicator == 3 && (g->dim != 2 || g->eq != HWENO_EULER)) {
     why = "the learned indicator is defined for 2D Euler"; return HWENO_EINVAL;
@@ -264,7 +277,7 @@ hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gam
   build_tables(h);
 
   const size_t npt = h->g.dim == 1 ? 4 : 16;
-  const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
+  const size_t esz = h->fp32 == hw::PREC_FP32 ? sizeof(float) : sizeof(double);   // df64 is 8 bytes
   const size_t sbytes = (size_t)P.nvar * P.nmom * P.plane * sizeof(double);
   const size_t mbytes = (size_t)P.nvar * (P.nmom - 1) * P.plane * sizeof(double);
   const size_t nc = (size_t)P.nx * P.ny;
@@ -613,8 +626,9 @@ hweno_status hweno_create_batch(const hweno_grid* grids, const hweno_bc* bcs, in
               "indicator and linear weights\n", k);
       return HWENO_EINVAL;
     }
-    if (g.indicator == HWENO_IND_MLP) {
-      fprintf(stderr, "hweno_create_batch: the learned indicator runs on single-problem handles\n");
+    if (g.indicator == HWENO_IND_MLP || g.precision == 2) {
+      fprintf(stderr, "hweno_create_batch: the learned indicator and the double-float precision run on "
+              "single-problem handles\n");
       return HWENO_EINVAL;
     }
   }
@@ -648,7 +662,7 @@ hweno_status hweno_create_batch(const hweno_grid* grids, const hweno_bc* bcs, in
   h->P = h->probs[0].P;
   build_tables(h);
   layout_batch(h);
-  const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
+  const size_t esz = h->fp32 == hw::PREC_FP32 ? sizeof(float) : sizeof(double);   // df64 is 8 bytes
   bool ok = true;
   for (int k = 0; k < 3; ++k) ok = ok && cudaMalloc(&h->U[k], tu * sizeof(double)) == cudaSuccess;
   ok = ok && cudaMalloc(&h->B.G, tg * esz) == cudaSuccess;

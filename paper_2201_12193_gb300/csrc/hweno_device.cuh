@@ -3,14 +3,16 @@
 // Scheme: moment-based multi-resolution HWENO, Li, Shu & Qiu (arXiv 2201.12193).
 // Section and equation names below are the paper's.
 //
-// Precision: T = double (FP64 path) or T = float (FP32-bulk path).  The state,
-// the Runge-Kutta combination and the conservation sums stay FP64 in both.
+// Precision: T = double (FP64 path), float (FP32-bulk path) or df64 (double-float
+// path, df64.cuh).  The state, the Runge-Kutta combination and the conservation
+// sums stay FP64 in all three.
 #pragma once
 
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "hweno_parity.h"
+#include "df64.cuh"
 
 namespace hw {
 
@@ -152,6 +154,31 @@ __device__ __forceinline__ void batch_inverse(const T (&x)[N], T (&inv)[N]) {
   inv[0] = r;
 }
 
+// Reciprocals for the FP64-class types.  FP64: one division for all N.
+// Double-float carries FP32's exponent range, where a product of 12 or 16
+// densities can underflow, so it inverts groups of 4.
+template <int N, typename T>
+__device__ __forceinline__ void batch_inverse_ranged(const T (&x)[N], T (&inv)[N]) {
+  if constexpr (is_df64<T>::value) {
+    static_assert(N % 4 == 0, "groups of four");
+#pragma unroll
+    for (int g = 0; g < N; g += 4) {
+      const T xs[4] = {x[g], x[g + 1], x[g + 2], x[g + 3]};
+      T r[4];
+      batch_inverse<4, T>(xs, r);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) inv[g + k] = r[k];
+    }
+  } else {
+    batch_inverse<N, T>(x, inv);
+  }
+}
+
+// One common denominator for the nonlinear weights is safe in FP64 only: it
+// multiplies four (beta + eps) factors (eps^4 = 1e-40 is below FP32's range,
+// which double-float shares).
+template <typename T> struct one_division { static constexpr bool value = sizeof(T) == 8 && !is_df64<T>::value; };
+
 // Velocity seen by the KXRCF indicator for scalar laws (Remarks 2, 3): f'(u), g'(u).
 template <typename T>
 __device__ __forceinline__ T scalar_velocity(const Prob& P, T u, int dir) {
@@ -255,7 +282,7 @@ __device__ __forceinline__ void combine_weights(const Weights<T>& W, const T bet
   const T tau4s = tabs(beta[3] - beta[0]) + tabs(beta[3] - beta[1]) + tabs(beta[3] - beta[2]);
   const T tau4 = (tau4s * T(1.0 / 3.0)) * (tau4s * T(1.0 / 3.0));
   T om[4];
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (one_division<T>::value) {
     // FP64: one division.  With x_l = beta_l + eps, wbar_l = gamma_l (x_l + tau)/x_l;
     // scaling every wbar_l by prod_m x_m gives N_l = gamma_l (x_l + tau) prod_{m!=l} x_m
     // and omega_l = N_l / sum_m N_m.
@@ -339,7 +366,7 @@ __device__ __forceinline__ void recon2d(const Weights<T>& W, const Beta2<T>& B, 
       for (int l = k + 1; l < 4; ++l) ts += tabs(b1[k] - b1[l]);
     const T t1 = (ts * T(1.0 / 6.0)) * (ts * T(1.0 / 6.0));
     T gx = T(0), gy = T(0);
-    if constexpr (sizeof(T) == 8) {   // common denominator: one division
+    if constexpr (one_division<T>::value) {   // common denominator: one division
       const T y0 = b1[0] + W.eps, y1 = b1[1] + W.eps, y2 = b1[2] + W.eps, y3 = b1[3] + W.eps;
       const T p01 = y0 * y1, p23 = y2 * y3;
       const T n[4] = {(y0 + t1) * (y1 * p23), (y1 + t1) * (y0 * p23), (y2 + t1) * (p01 * y3), (y3 + t1) * (p01 * y2)};

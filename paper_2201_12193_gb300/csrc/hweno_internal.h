@@ -14,11 +14,17 @@ namespace hw {
 struct HostTabs {
   Weights<double> wd;
   Weights<float> wf;
+  Weights<df64> wx;      // double-float (precision 2)
   Beta1<double> b1d;
   Beta1<float> b1f;
+  Beta1<df64> b1x;
   Beta2<double> b2d;
   Beta2<float> b2f;
+  Beta2<df64> b2x;
 };
+
+// Compute precision of a handle: 0 FP64, 1 FP32 bulk, 2 double-float (FP32 pairs).
+enum { PREC_FP64 = 0, PREC_FP32 = 1, PREC_DF64 = 2 };
 
 // Optional per-kernel timing: CUDA events recorded around each launch on the
 // launching stream, read back (and summed per kernel kind) after a sync.
@@ -93,7 +99,7 @@ struct StageCall {
   double* aleph;           // optional: KXRCF values [ny*nx]
 };
 
-void run_stage_1d(const Prob& P, const HostTabs& T, int fp32, const Bufs& B, const StageCall& S, cudaStream_t st);
+void run_stage_1d(const Prob& P, const HostTabs& T, int prec, const Bufs& B, const StageCall& S, cudaStream_t st);
 
 // ---------------------------------------------------------------- batched 2D problems
 // One problem of a batch: its description and the offsets of its arrays inside
@@ -147,7 +153,7 @@ cudaError_t run_mlp_train(const float* th, const float* X, const float* y, const
 cudaError_t run_adam(float* th, const float* grad, float* m1, float* m2, int step, float lr, cudaStream_t st);
 cudaError_t run_mlpre2d(const Prob& P, const float* th, float conf, const double* U, uint8_t* mask, double* Mod,
                         int* und, int* und_count, int* stats, float* prob, cudaStream_t st);
-void run_stage_2d(const Prob& P, const HostTabs& T, int fp32, const Bufs& B, const StageCall& S, cudaStream_t st);
+void run_stage_2d(const Prob& P, const HostTabs& T, int prec, const Bufs& B, const StageCall& S, cudaStream_t st);
 
 // Reductions over the cell averages (FP64): maximum wave speeds per direction
 // and totals sum(ubar) per variable.  partials needs reduce_partials_len(P)

@@ -296,3 +296,51 @@ def test_nonphysical_step_rolls_back():
     assert e.value.status == -3
     np.testing.assert_array_equal(s.get_moments(), m)
     s.close()
+
+
+# ------------------------------------------------------------------ double-float precision
+
+@pytest.mark.parametrize("name,make", [
+    ("shu_osher", lambda: W.shu_osher_1d(300)),
+    ("lax", lambda: W.lax_1d(200)),
+    ("four_quadrant_ragged", lambda: W.four_quadrant_2d(70, seed=3, ny=45)),
+    ("vortex_periodic", lambda: W.vortex_2d(48, seed=2)),
+    ("burgers_2d", lambda: W.burgers_2d(40)),
+], ids=["shu_osher", "lax", "four_quadrant", "vortex", "burgers_2d"])
+def test_df64_rhs_parity(orc, name, make):
+    """Double-float path: one evaluation of L against the FP64 oracle, with
+    the FP64 path's own bars (modified state 1e-12 relative L1, L to 1e-11 of
+    its L1 norm plus 1e-9 per entry, identical masks, KXRCF values to 1e-9)."""
+    p = make()
+    s = solver_of(p, precision="df64")
+    for seed in (0, 1):
+        U = p.m if seed == 0 else _perturbed(p, seed)
+        Um_g, L_g, mask_g, aleph_g = gpu_rhs(s, U)
+        Um_o, L_o, mask_o, aleph_o, rc = orc.rhs(cfg_of(orc, p), U)
+        assert rc == 0
+        assert not (np.abs(aleph_o - 1.0) < 1e-10).any()
+        assert np.array_equal(mask_g, mask_o)
+        assert rel_l1(Um_g, Um_o) <= TOL
+        assert np.abs(L_g - L_o).sum() <= 1e-11 * np.abs(L_o).sum() + 1e-9 * L_o.size, rel_l1(L_g, L_o)
+        np.testing.assert_allclose(aleph_g, aleph_o, rtol=1e-9, atol=1e-9)
+    s.close()
+
+
+@pytest.mark.parametrize("name,make,nsteps", [
+    ("shu_osher", lambda: W.shu_osher_1d(300), 10),
+    ("four_quadrant_ragged", lambda: W.four_quadrant_2d(70, seed=3, ny=45), 5),
+], ids=["shu_osher", "four_quadrant"])
+def test_df64_steps_parity(orc, name, make, nsteps):
+    p = make()
+    s = solver_of(p, precision="df64")
+    s.set_moments(p.m)
+    cfg = cfg_of(orc, p)
+    m = p.m
+    for _ in range(nsteps):
+        dt = s.max_dt(0.6)
+        s.step(dt)
+        m, masks, rc = orc.step(cfg, m, dt)
+        assert rc == 0
+        assert np.array_equal(s.troubled_mask().reshape(3, -1), masks)
+    assert rel_l1(s.get_moments(), m) <= TOL
+    s.close()
