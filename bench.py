@@ -71,6 +71,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched form")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-indicator form")
+    ap.add_argument("--no-1d", action="store_true", help="skip the 1D Shu-Osher full run")
     ap.add_argument("--learned-n", type=int, default=4096, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -363,6 +364,39 @@ def _peaks():
         return {}
 
 
+def run_shu_osher(torch, hweno, world):
+    """The 1D Shu-Osher problem (N = 4000, transmissive, to t = 1.8, CFL 0.6, FP64):
+    a latency-bound run of ~5,600 small steps (192 KB of state).  Timed whole,
+    device-driven (hweno_advance: dt formed on the device, graph replays of 12
+    steps) against the host-driven loop (hweno_max_dt + hweno_step)."""
+    from paper_2201_12193_gb300 import workloads as W
+    p = W.shu_osher_1d(4000)
+    out = {}
+    finals = {}
+    for mode in ("advance", "host_loop"):
+        s = hweno.Solver.from_problem(p)
+        s.set_stream(torch.cuda.current_stream())
+        s.set_moments(torch.from_numpy(p.m).cuda())
+        s.advance(0.01) if mode == "advance" else s.run(0.01)      # warm-up (graph capture)
+        s.set_moments(torch.from_numpy(p.m).cuda())
+        s.sync()
+        barrier(world)
+        t0 = time.perf_counter()
+        if mode == "advance":
+            t, n = s.advance(1.8, CFL)
+        else:
+            n = s.run(1.8, CFL)
+        secs = max_over_ranks(time.perf_counter() - t0, world)
+        finals[mode] = s.get_moments()
+        out[mode] = {"value": aggregate(p.nx, 3, n, world, secs * 1e3), "steps": n, "seconds": secs,
+                     "us_per_step": secs * 1e6 / n}
+        s.close()
+    same = bool(np.array_equal(finals["advance"], finals["host_loop"]))
+    return {"shu_osher_1d_full_run": {"workload": "1d_euler_shu_osher_4000_to_t1.8", "dtype": "f64",
+                                      "value": out["advance"]["value"], "unit": UNIT, "device_driven": out["advance"],
+                                      "host_driven": out["host_loop"], "identical_states": same}}
+
+
 def run_learned(torch, hweno, args, world, rank):
     """The learned-indicator form on its own workload: 2D Euler blast data
     (8 seeded circles, p in U[5,100] inside, 0.1 outside, rho = 1, at rest),
@@ -548,6 +582,9 @@ def run_ours(args, world, rank, local):
                 "note": "algorithmic FP64-equivalent flop of the reconstruction per second; the FP32 pipe "
                         "executes ~6-15 FP32 instructions per double-float operation"}
         sx.close()
+
+    if not args.no_forms and not args.no_1d:
+        forms.update(run_shu_osher(torch, hweno, world))
 
     if not args.no_forms and not args.no_batch:
         forms.update(run_batched(torch, hweno, args, world, rank))

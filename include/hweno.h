@@ -192,6 +192,20 @@ hweno_status hweno_mlp_loss_grad(const float* params, const float* X, const floa
 hweno_status hweno_mlp_adam(float* params, const float* grad, float* m1, float* m2, int step, float lr,
                             void* stream);
 
+/* Advance by t_end (>= 0) with the CFL step length (cfl > 0, the rule of
+ * hweno_max_dt) computed on the device each step, the last step clipped so that
+ * the run ends at t_end exactly, at most max_steps steps.  Steps run in groups
+ * of 12 replayed from a CUDA graph (no host round trip per step); steps left
+ * over in the last group once t_end or max_steps is reached are skipped (the
+ * state passes through unchanged).  Writes the time reached and the steps taken
+ * (either pointer may be NULL).  The result equals hweno_max_dt + hweno_step
+ * driven from the host, bit for bit.  A non-physical state stops the call with
+ * HWENO_ENONPHYSICAL and is not rolled back (several steps per replay);
+ * hweno_troubled_mask afterwards holds the flags of the group's last step, which
+ * may be a skipped one.  Single-problem handles; synchronises. */
+hweno_status hweno_advance(hweno_t h, double t_end, double cfl, long long max_steps, double* t_done,
+                           long long* steps_done);
+
 /* Positivity check of hweno_step / hweno_step_batch (no counterpart in the
  * paper, which has no positivity treatment): on (default), a stage whose new
  * cell averages have rho <= 0 or p <= 0 (Euler) fails the step with

@@ -130,6 +130,7 @@ struct Rk1 {
   double dt, cA, cB;
   double* Lout; double* Umod;
   unsigned* status;
+  const double* dtp;     // dt on the device (overrides dt); < 0: skip, Uout = Uin
 };
 
 template <typename T, int NV>
@@ -146,6 +147,14 @@ __global__ void __launch_bounds__(RB) update1d_kernel(Prob P, const T* __restric
   const int i0 = blockIdx.x * RB;
   const int i = i0 + t;
   const bool live = i < P.nx;
+  if (S.dtp) {
+    S.dt = *S.dtp;
+    if (S.dt < 0.0) {   // a skipped step (block-uniform): the state passes through unchanged
+      if (live && !S.Lout)
+        for (int q = 0; q < NV * 2; ++q) S.Uout[(long long)q * P.plane + i] = S.Uin[(long long)q * P.plane + i];
+      return;
+    }
+  }
   const Img self{i, 0, 1, 1};
   // fx[c] is the face left of cell i0 + c; one call site computes every face so
   // that faces shared by two blocks get bitwise the same flux.
@@ -223,7 +232,7 @@ void stage_t(const Prob& P, const Weights<T>& W, const Beta1<T>& Bt, const Bufs&
                                                    B.rerec);
     if (B.prof) B.prof->end(st);
   }
-  Rk1 r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status};
+  Rk1 r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status, S.dtp};
   if (B.prof) B.prof->begin(3, st);
   update1d_kernel<T, NV><<<blocks, RB, 0, st>>>(P, (const T*)B.G, r);
   if (B.prof) B.prof->end(st);

@@ -265,6 +265,7 @@ struct Rk {
   double dt, cA, cB;
   double* Lout; double* Umod;
   unsigned* status;
+  const double* dtp;     // dt on the device (overrides dt); < 0: skip, Uout = Uin
 };
 
 // Step 3 for the TXV x TYV tile at (i0, j0): face fluxes into shared memory, then
@@ -395,6 +396,18 @@ template <typename T, int NV>
 __global__ void __launch_bounds__(TX * TY) update2d_kernel(Prob P, const T* __restrict__ G, Rk S) {
   __shared__ T xf[TY][TX + 1][4][NV];
   __shared__ T yf[TY + 1][TX][4][NV];
+  if (S.dtp) {
+    S.dt = *S.dtp;
+    if (S.dt < 0.0) {   // a skipped step (block-uniform): the state passes through unchanged
+      const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
+      if (i < P.nx && j < P.ny && !S.Lout)
+        for (int q = 0; q < NV * 3; ++q) {
+          const long long si = (long long)q * P.plane + (long long)j * P.pitch + i;
+          S.Uout[si] = S.Uin[si];
+        }
+      return;
+    }
+  }
   update2d_tile<T, NV, TX, TY>(P, G, S, blockIdx.x * TX, blockIdx.y * TY, threadIdx.y * TX + threadIdx.x, xf, yf);
 }
 
@@ -441,7 +454,7 @@ void stage_t(const Prob& P, const HostTabs& HT, const Weights<T>& W, const Beta2
                                                              nullptr, B.rerec);
     if (B.prof) B.prof->end(st);
   }
-  Rk r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status};
+  Rk r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status, S.dtp};
   if (B.prof) B.prof->begin(3, st);
   update2d_kernel<T, NV><<<grd, blk, 0, st>>>(P, (const T*)B.G, r);
   if (B.prof) B.prof->end(st);

@@ -33,6 +33,9 @@ struct hweno_s {
   double* red_out = nullptr;     // reduction results (device)
   double* host_buf = nullptr;    // pinned: reduction results + status
   hw::Prof prof;                 // per-kernel event timing (hweno_profile)
+  double* adv = nullptr;         // hweno_advance: device {T, cfl, max_steps, t, dt, steps}
+  cudaGraphExec_t agraphs[3] = {nullptr, nullptr, nullptr};   // hweno_advance, one per state rotation
+  bool adv_graph = true;         // capture works here (else direct launches)
   float* mlp = nullptr;          // learned indicator parameters (device)
   int* mlp_stats = nullptr;      // fallback counter (device)
   bool have_mlp = false;
@@ -167,8 +170,10 @@ hweno_status validate(const hweno_grid* g, const hweno_bc* bc, double gamma, std
 }
 
 void drop_graphs(hweno_s* h) {
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 3; ++k) {
     if (h->graphs[k]) { cudaGraphExecDestroy(h->graphs[k]); h->graphs[k] = nullptr; }
+    if (h->agraphs[k]) { cudaGraphExecDestroy(h->agraphs[k]); h->agraphs[k] = nullptr; }
+  }
 }
 
 void free_all(hweno_s* h) {
@@ -178,6 +183,7 @@ void free_all(hweno_s* h) {
   cudaFree(h->B.und);
   cudaFree(h->B.und_count);
   cudaFree(h->B.rerec);
+  cudaFree(h->adv);
   cudaFree(h->dprobs);
   cudaFree(h->blist);
   cudaFree(h->speeds);
@@ -401,6 +407,98 @@ hweno_status hweno_sync(hweno_t h) {
   return check_status(h);
 }
 
+namespace {
+
+constexpr int ADV_K = 12;   // steps per replay (a multiple of 3: the buffer rotation closes)
+
+// ADV_K steps with the step length computed on the device, from rotation a.
+cudaError_t advance_steps(hweno_t h, int a, cudaStream_t st) {
+  const size_t nc = ncell(h);
+  double* par = h->adv;
+  double* stt = h->adv + 3;
+  for (int k = 0; k < ADV_K; ++k) {
+    const int b = (a + 1) % 3, c = (a + 2) % 3;
+    hw::run_wavespeed(h->P, h->U[a], h->red_part, h->red_out, st);
+    hw::run_advance_dt(h->P, h->red_out, par, stt, h->B.status, st);
+    auto run = [&](const hw::StageCall& S) {
+      if (h->g.dim == 1) hw::run_stage_1d(h->P, h->T, h->fp32, h->B, S, st);
+      else hw::run_stage_2d(h->P, h->T, h->fp32, h->B, S, st);
+    };
+    hw::StageCall S{};
+    S.dtp = stt + 1;
+    S.stage = 0; S.Uin = h->U[a]; S.Un = h->U[a]; S.Uout = h->U[b]; S.cA = 0.0; S.cB = 1.0;
+    S.mask = h->mask3; S.Mod = h->ModN; S.maskN = nullptr; S.ModN = nullptr;
+    run(S);
+    S.stage = 1; S.Uin = h->U[b]; S.Un = h->U[a]; S.Uout = h->U[c]; S.cA = 0.75; S.cB = 0.25;
+    S.mask = h->mask3 + nc; S.Mod = h->ModK; S.maskN = h->mask3; S.ModN = h->ModN;
+    run(S);
+    S.stage = 2; S.Uin = h->U[c]; S.Un = h->U[a]; S.Uout = h->U[b]; S.cA = 1.0 / 3.0; S.cB = 2.0 / 3.0;
+    S.mask = h->mask3 + 2 * nc; S.Mod = h->ModK;
+    run(S);
+    a = b;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t advance_graph(hweno_t h, int a, cudaGraphExec_t* out) {
+  cudaStream_t cs;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    e = advance_steps(h, a, cs);
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) *out = nullptr;
+  return e;
+}
+
+}  // namespace
+
+hweno_status hweno_advance(hweno_t h, double t_end, double cfl, long long max_steps, double* t_done,
+                           long long* steps_done) {
+  if (!h) return HWENO_EINVAL;
+  if (h->batch) return fail(h, HWENO_ESTATE, "advance: single-problem handles only");
+  if (!h->have_state) return fail(h, HWENO_ESTATE, "advance: no moments set");
+  if (h->g.indicator == 3 && !h->have_mlp) return fail(h, HWENO_ESTATE, "advance: learned indicator not set");
+  if (!(t_end >= 0.0) || !isfinite(t_end) || !(cfl > 0.0) || !isfinite(cfl) || max_steps < 0)
+    return fail(h, HWENO_EINVAL, "advance: need t_end >= 0, cfl > 0 and max_steps >= 0");
+  hweno_status s0 = check_status(h);
+  if (s0 != HWENO_OK) return s0;
+  if (!h->adv) CK(h, cudaMalloc(&h->adv, 6 * sizeof(double)));
+  double* hb = h->host_buf + 8;
+  hb[0] = t_end; hb[1] = cfl; hb[2] = (double)max_steps; hb[3] = 0.0; hb[4] = 0.0; hb[5] = 0.0;
+  CK(h, cudaMemcpyAsync(h->adv, hb, 6 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  h->stepped = false;     // several steps per replay: no single-step roll-back
+  double t = 0.0, steps = 0.0;
+  while (steps < (double)max_steps && t_end - t > 1e-14 * fmax(1.0, fabs(t_end))) {
+    const int a = h->cur;
+    const bool use_graph = h->adv_graph && !h->B.prof;
+    if (use_graph && !h->agraphs[a] && advance_graph(h, a, &h->agraphs[a]) != cudaSuccess) {
+      h->adv_graph = false;     // capture unavailable here: launch directly
+      cudaGetLastError();
+    }
+    if (h->adv_graph && !h->B.prof && h->agraphs[a]) CK(h, cudaGraphLaunch(h->agraphs[a], h->stream));
+    else CK(h, advance_steps(h, a, h->stream));
+    CK(h, cudaMemcpyAsync(hb + 3, h->adv + 3, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    const hweno_status s = check_status(h);
+    if (s != HWENO_OK) return s;
+    const double before = steps;
+    t = hb[3];
+    steps = hb[5];
+    if (steps == before) break;           // nothing advanced (dt could not be formed)
+  }
+  if (t_done) *t_done = t;
+  if (steps_done) *steps_done = (long long)steps;
+  return HWENO_OK;
+}
+
 hweno_status hweno_max_dt(hweno_t h, double cfl, double* dt_out) {
   if (!h || !dt_out) return HWENO_EINVAL;
   if (!h->have_state) return fail(h, HWENO_ESTATE, "max_dt: no moments set");
@@ -477,6 +575,7 @@ hweno_status hweno_set_mlp(hweno_t h, const float* params, int on_device, float 
   const size_t nb = hw::mlp_nparam() * sizeof(float);
   CK(h, cudaMemcpyAsync(h->mlp, params, nb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
+  drop_graphs(h);
   h->B.mlp = h->mlp;
   h->B.mlp_conf = conf;
   h->B.mlp_stats = h->mlp_stats;
@@ -507,6 +606,7 @@ hweno_status hweno_set_positivity_check(hweno_t h, int on) {
   if (!h) return HWENO_EINVAL;
   h->positivity = on != 0;
   h->P.positivity = on != 0;
+  drop_graphs(h);
   if (h->batch) {
     for (auto& q : h->probs) q.P.positivity = on != 0;
     CK(h, cudaMemcpyAsync(h->dprobs, h->probs.data(), h->probs.size() * sizeof(hw::BProb), cudaMemcpyHostToDevice,

@@ -94,6 +94,7 @@ struct StageCall {
   double* Mod;             // out: modified first moments of flagged cells [nvar][nmom-1][plane]
   const uint8_t* maskN;    // first-stage flags (for Un'); nullptr = Un unmodified
   const double* ModN;      // first-stage modified first moments
+  const double* dtp;       // optional: dt read on the device (hweno_advance); < 0 = skip the step (Uout = Uin)
   double* Lout;            // optional: write L(Uin') (state layout) instead of the RK update
   double* Umod;            // optional (with Lout): write Uin'
   double* aleph;           // optional: KXRCF values [ny*nx]
@@ -160,6 +161,8 @@ void run_stage_2d(const Prob& P, const HostTabs& T, int prec, const Bufs& B, con
 // doubles; out gets {ax, ay} or the nvar totals (unscaled sums).
 int reduce_partials_len(const Prob& P);
 void run_wavespeed(const Prob& P, const double* U, double* partials, double* out, cudaStream_t st);
+void run_advance_dt(const Prob& P, const double* speeds, const double* par, double* st, unsigned* status,
+                    cudaStream_t s);
 void run_totals(const Prob& P, const double* U, double* partials, double* out, cudaStream_t st);
 
 }  // namespace hw

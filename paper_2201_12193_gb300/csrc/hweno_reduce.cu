@@ -106,7 +106,39 @@ int first_pass_blocks(const Prob& P) {
   return (int)std::min<long long>(MAXB, (n + RT - 1) / RT);
 }
 
+// The step length of hweno_advance on the device, from the wave-speed maxima in
+// sp[0..1]: the CFL rule of the host's hweno_max_dt (same expressions), clipped
+// to the remaining time; st[0] = t, st[1] = dt, st[2] = steps taken,
+// par = {T, cfl, max_steps}.  dt = -1 marks a step to skip (done, step budget
+// spent, or a non-physical average, which also sets ST_NONPOSITIVE).
+__global__ void advance_dt_kernel(Prob P, const double* __restrict__ sp, const double* __restrict__ par,
+                                  double* __restrict__ st, unsigned* __restrict__ status) {
+  const double ax = sp[0], ay = sp[1];
+  const double T = par[0], cfl = par[1], maxs = par[2];
+  double dtc;
+  if (P.nmom == 2) dtc = ax > 0.0 ? cfl * P.dx / ax : INFINITY;
+  else {
+    const double r = ax / P.dx + ay / P.dy;
+    dtc = r > 0.0 ? cfl / r : INFINITY;
+  }
+  const double t = st[0], rem = T - t;
+  double dt = -1.0;
+  if (!(dtc > 0.0) || isnan(dtc)) {
+    atomicOr(status, ST_NONPOSITIVE);
+  } else if (st[2] < maxs && rem > 1e-14 * fmax(1.0, fabs(T))) {
+    dt = fmin(dtc, rem);
+    st[0] = dtc >= rem ? T : t + dt;
+    st[2] += 1.0;
+  }
+  st[1] = dt;
+}
+
 }  // namespace
+
+void run_advance_dt(const Prob& P, const double* speeds, const double* par, double* st, unsigned* status,
+                    cudaStream_t s) {
+  advance_dt_kernel<<<1, 1, 0, s>>>(P, speeds, par, st, status);
+}
 
 int reduce_partials_len(const Prob&) { return 4 * MAXB; }
 

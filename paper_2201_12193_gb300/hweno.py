@@ -84,6 +84,8 @@ def lib():
         L.hweno_mlp_loss_grad.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int] + [ctypes.c_void_p] * 3
         L.hweno_mlp_adam.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int, ctypes.c_float, ctypes.c_void_p]
         L.hweno_mlp_probe.argtypes = [H, ctypes.c_void_p]
+        L.hweno_advance.argtypes = [H, ctypes.c_double, ctypes.c_double, ctypes.c_longlong,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
         L.hweno_rerecon_count.argtypes = [H, ctypes.POINTER(ctypes.c_longlong)]
         L.hweno_set_positivity_check.argtypes = [H, ctypes.c_int]
         L.hweno_last_error.argtypes = [H]
@@ -263,6 +265,15 @@ class Solver:
         n = (ctypes.c_int * k)()
         self._check(lib().hweno_profile_read(self._h, ms, n, k))
         return {k: (ms[i], n[i]) for i, k in enumerate(self.KERNEL_KINDS)}
+
+    def advance(self, t_end, cfl=0.6, max_steps=10 ** 12):
+        """Advance by t_end with the CFL dt formed on the device (graph replays of
+        12 steps, no host round trip per step). Returns (time reached, steps)."""
+        t = ctypes.c_double()
+        n = ctypes.c_longlong()
+        self._check(lib().hweno_advance(self._h, float(t_end), float(cfl), int(max_steps), ctypes.byref(t),
+                                        ctypes.byref(n)))
+        return t.value, n.value
 
     def run(self, t_end, cfl=0.6, dt=None, max_steps=10 ** 9):
         """Advance to t_end (CFL dt unless dt is given), clipping the last step."""

@@ -344,3 +344,35 @@ def test_df64_steps_parity(orc, name, make, nsteps):
         assert np.array_equal(s.troubled_mask().reshape(3, -1), masks)
     assert rel_l1(s.get_moments(), m) <= TOL
     s.close()
+
+
+# ------------------------------------------------------------------ device-driven stepping
+
+@pytest.mark.parametrize("name,make,t_end", [
+    ("shu_osher", lambda: W.shu_osher_1d(400), 0.3),
+    ("four_quadrant", lambda: W.four_quadrant_2d(64, seed=1), 0.05),
+    ("vortex_df64", lambda: W.vortex_2d(48, seed=2), 0.6),
+], ids=["shu_osher", "four_quadrant", "vortex_df64"])
+def test_advance_equals_host_driven_run(name, make, t_end):
+    """hweno_advance (dt formed on the device, graph replays of 12 steps, the
+    remainder of the last group skipped) against max_dt + step from the host:
+    the same number of steps and bitwise the same state."""
+    p = make()
+    prec = "df64" if name.endswith("df64") else "fp64"
+    a = solver_of(p, precision=prec)
+    a.set_moments(p.m)
+    t, n = a.advance(t_end, 0.6)
+    b = solver_of(p, precision=prec)
+    b.set_moments(p.m)
+    nb = b.run(t_end, 0.6)
+    assert n == nb and n > 12 and t == pytest.approx(t_end, rel=1e-14)
+    assert np.array_equal(a.get_moments(), b.get_moments())
+    # a step budget stops the run where the host loop would stop
+    a.set_moments(p.m)
+    b.set_moments(p.m)
+    t5, n5 = a.advance(t_end, 0.6, max_steps=5)
+    b.run(t_end, 0.6, max_steps=5)
+    assert n5 == 5 and t5 < t_end
+    assert np.array_equal(a.get_moments(), b.get_moments())
+    a.close()
+    b.close()
