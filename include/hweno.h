@@ -59,7 +59,7 @@ typedef enum {
 } hweno_status;
 
 typedef enum { HWENO_ADVECTION = 0, HWENO_BURGERS = 1, HWENO_EULER = 2 } hweno_eq;
-typedef enum { HWENO_BC_PERIODIC = 0, HWENO_BC_TRANSMISSIVE = 1 } hweno_bc_kind;
+typedef enum { HWENO_BC_PERIODIC = 0, HWENO_BC_TRANSMISSIVE = 1, HWENO_BC_REFLECTIVE = 2 } hweno_bc_kind;
 typedef enum { HWENO_IND_NONE = 0, HWENO_IND_KXRCF = 1, HWENO_IND_ALL = 2, HWENO_IND_MLP = 3 } hweno_indicator;
 
 /* Uniform mesh and scheme options.

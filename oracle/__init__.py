@@ -26,7 +26,7 @@ _lib = None
 
 EQ = {"advection": 0, "burgers": 1, "euler": 2}
 IND = {"none": 0, "kxrcf": 1, "all": 2, "given": 3}
-BC = {"periodic": 0, "transmissive": 1}
+BC = {"periodic": 0, "transmissive": 1, "reflective": 2}
 
 
 def build(force: bool = False) -> str:

@@ -52,7 +52,7 @@ typedef struct {
   int indicator;    /* 0 none (HWENO6), 1 KXRCF (M5-I), 2 all cells (M5-NI),
                        3 given decisions with KXRCF for the deferred cells */
   double gbar[4];   /* positive linear-weight seeds, eq. (linear-weight) */
-  int bc[4];        /* x-lo, x-hi, y-lo, y-hi: 0 periodic, 1 transmissive */
+  int bc[4];        /* x-lo, x-hi, y-lo, y-hi: 0 periodic, 1 transmissive, 2 reflective (Euler) */
 } orc_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -453,23 +453,31 @@ static void recon_cell(int dim, double dx, double dy, const double gbar[4],
 /* Reading: a ghost cell is, throughout a stage, the image of an interior
  * cell: periodic = wrap; transmissive = mirror about the boundary face, so
  * the mirrored direction's first moment changes sign and its point values
- * are reversed in that direction.  Ghost flags and modified moments are those
- * of the image cell. */
-typedef struct { int i, j, sx, sy; } image_t;
+ * are reversed in that direction; reflective (a solid wall, Euler only) = the
+ * transmissive mirror with the wall-normal momentum negated as well (all its
+ * moments and point values).  Ghost flags and modified moments are those of
+ * the image cell. */
+typedef struct { int i, j, sx, sy, rx, ry; } image_t;
 
 static image_t cell_image(const orc_cfg *c, int i, int j) {
-  image_t r = {i, j, 1, 1};
+  image_t r = {i, j, 1, 1, 0, 0};
   if (i < 0 || i >= c->nx) {
     int side = i < 0 ? 0 : 1;
     if (c->bc[side] == 0) { r.i = ((i % c->nx) + c->nx) % c->nx; }
-    else { r.i = i < 0 ? -1 - i : 2 * c->nx - 1 - i; r.sx = -1; }
+    else { r.i = i < 0 ? -1 - i : 2 * c->nx - 1 - i; r.sx = -1; r.rx = c->bc[side] == 2; }
   }
   if (c->dim == 2 && (j < 0 || j >= c->ny)) {
     int side = j < 0 ? 2 : 3;
     if (c->bc[side] == 0) { r.j = ((j % c->ny) + c->ny) % c->ny; }
-    else { r.j = j < 0 ? -1 - j : 2 * c->ny - 1 - j; r.sy = -1; }
+    else { r.j = j < 0 ? -1 - j : 2 * c->ny - 1 - j; r.sy = -1; r.ry = c->bc[side] == 2; }
   }
   return r;
+}
+
+/* -1 for the wall-normal momentum of a reflective image (variable 1 = x
+ * momentum; variable 2 = y momentum in 2D), +1 otherwise */
+static double wall_sign(const image_t *im, int var) {
+  return ((var == 1 && im->rx) || (var == 2 && im->ry)) ? -1.0 : 1.0;
 }
 
 static int nvars(const orc_cfg *c) { return c->eq == 2 ? (c->dim == 1 ? 3 : 4) : 1; }
@@ -486,7 +494,7 @@ static double mom_at(const orc_cfg *c, const double *m, int var, int mom, int i,
   double v = *MOM(c, (double *)m, var, mom, im.i, im.j);
   if (mom == 1) v *= im.sx;
   if (mom == 2) v *= im.sy;
-  return v;
+  return v * wall_sign(&im, var);
 }
 
 /* GL values array G[cell][var][16]; value of any (possibly ghost) cell at node (k,l) */
@@ -496,7 +504,7 @@ static double gl_at(const orc_cfg *c, const double *G, int var, int i, int j, in
   if (im.sy < 0) l = 3 - l;
   size_t cell = (size_t)im.j * c->nx + im.i;
   int nv = nvars(c);
-  return G[(cell * nv + var) * 16 + (c->dim == 1 ? k : k * 4 + l)];
+  return wall_sign(&im, var) * G[(cell * nv + var) * 16 + (c->dim == 1 ? k : k * 4 + l)];
 }
 
 /* ------------------------------------------------------------------ */

@@ -5,7 +5,8 @@ forward and backward kernels; the library never calls it.
 
 Features (108 per cell): for each of the 4 conserved variables of 2D Euler and
 each cell k of the 3x3 neighbourhood (boundary images as in the scheme:
-periodic wrap or mirror with the mirrored first moment negated), the triple
+periodic wrap, or mirror with the mirrored first moment negated and, at a
+reflective wall, the wall-normal momentum negated), the triple
 (ubar_k - ubar_c, vbar_k, wbar_k) / D with
     D = max_k |ubar_k - ubar_c| + h^2 max_k |ubar_k| + 1e-12,
 h = dx, except that the centre's own (always zero) average slot carries
@@ -70,12 +71,13 @@ def gelu_grad(x):
     return 0.5 * (1.0 + erf(x / math.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
 
 
-def _image(i, n, periodic):
+def _image(i, n, kind):
+    """(image index, mirror sign, wall flag) of index i under boundary kind."""
     if 0 <= i < n:
-        return i, 1
-    if periodic:
-        return i % n, 1
-    return (-1 - i, -1) if i < 0 else (2 * n - 1 - i, -1)
+        return i, 1, False
+    if kind == "periodic":
+        return i % n, 1, False
+    return ((-1 - i) if i < 0 else (2 * n - 1 - i)), -1, kind == "reflective"
 
 
 def features(m, cells, bc, h):
@@ -87,13 +89,14 @@ def features(m, cells, bc, h):
         for v in range(nv):
             vals = np.zeros((3, 9))
             for oy in (-1, 0, 1):
-                jj, sy = _image(j + oy, ny, bc[2] == "periodic")
+                jj, sy, wy = _image(j + oy, ny, bc[2] if j + oy < 0 else bc[3])
                 for ox in (-1, 0, 1):
-                    ii, sx = _image(i + ox, nx, bc[0] == "periodic")
+                    ii, sx, wx = _image(i + ox, nx, bc[0] if i + ox < 0 else bc[1])
                     k = (oy + 1) * 3 + ox + 1
-                    vals[0, k] = m[v, 0, jj, ii]
-                    vals[1, k] = sx * m[v, 1, jj, ii]
-                    vals[2, k] = sy * m[v, 2, jj, ii]
+                    g = -1.0 if (v == 1 and wx) or (v == 2 and wy) else 1.0   # wall: normal momentum negated
+                    vals[0, k] = g * m[v, 0, jj, ii]
+                    vals[1, k] = g * sx * m[v, 1, jj, ii]
+                    vals[2, k] = g * sy * m[v, 2, jj, ii]
             u0 = vals[0, 4]
             umax = np.max(np.abs(vals[0]))
             D = np.max(np.abs(vals[0] - u0)) + h * h * umax + 1e-12

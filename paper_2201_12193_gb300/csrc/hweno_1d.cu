@@ -22,11 +22,12 @@ __device__ __forceinline__ int mpt1(const Img& m, int k) { return m.sx < 0 ? 3 -
 template <bool FLAGGED>
 __device__ __forceinline__ double load_mom1(const Prob& P, const double* __restrict__ U, const uint8_t* __restrict__ mask,
                                             const double* __restrict__ Mod, int var, int kind, const Img& m) {
-  if (kind == 0) return U[sidx(P, var, 0, m.i, 0)];
+  const int g = vsign(m, var);      // reflective wall: the normal momentum negated
+  if (kind == 0) return g * U[sidx(P, var, 0, m.i, 0)];
   double v;
   if (FLAGGED && mask[m.i]) v = Mod[(long long)var * P.plane + m.i];
   else v = U[sidx(P, var, 1, m.i, 0)];
-  return m.sx < 0 ? -v : v;
+  return m.sx < 0 ? -g * v : g * v;
 }
 
 template <typename T, int NV, bool FLAGGED>
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(RB) flag1d_kernel(Prob P, Weights<T> W, const 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = i < P.nx;
   bool flag = false;
-  Img L{0, 0, 1, 1}, R{0, 0, 1, 1};
+  Img L{0, 0, 1, 1, 0}, R{0, 0, 1, 1, 0};
   if (valid) {
     L = image(P, i - 1, 0);
     R = image(P, i + 1, 0);
@@ -93,8 +94,9 @@ __global__ void __launch_bounds__(RB) flag1d_kernel(Prob P, Weights<T> W, const 
       flag = true;
     } else if (P.indicator == IND_KXRCF) {
       // face velocities: average of both sides' velocities at the face
-      const T vl = T(0.5) * (aux[(L.sx < 0 ? 0 : 1) * P.gplane + L.i] + aux[0 * P.gplane + i]);
-      const T vr = T(0.5) * (aux[1 * P.gplane + i] + aux[(R.sx < 0 ? 1 : 0) * P.gplane + R.i]);
+      const T al = aux[(L.sx < 0 ? 0 : 1) * P.gplane + L.i], ar = aux[(R.sx < 0 ? 1 : 0) * P.gplane + R.i];
+      const T vl = T(0.5) * ((L.neg & 2 ? -al : al) + aux[0 * P.gplane + i]);
+      const T vr = T(0.5) * (aux[1 * P.gplane + i] + (R.neg & 2 ? -ar : ar));
       const T jl = G[0 * P.gplane + i] - G[(long long)mpt1(L, 3) * P.gplane + L.i];
       const T jr = G[3 * P.gplane + i] - G[(long long)mpt1(R, 0) * P.gplane + R.i];
       const T s = jl * (vl > T(KX_VDEAD) ? T(1) : T(0)) + jr * (-vr > T(KX_VDEAD) ? T(1) : T(0));
@@ -118,8 +120,9 @@ __global__ void __launch_bounds__(RB) flag1d_kernel(Prob P, Weights<T> W, const 
   if (!flag) return;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const double uL = U[sidx(P, v, 0, L.i, 0)], uR = U[sidx(P, v, 0, R.i, 0)];
-    const double vL = L.sx * U[sidx(P, v, 1, L.i, 0)], vR = R.sx * U[sidx(P, v, 1, R.i, 0)];
+    const int gL = vsign(L, v), gR = vsign(R, v);
+    const double uL = gL * U[sidx(P, v, 0, L.i, 0)], uR = gR * U[sidx(P, v, 0, R.i, 0)];
+    const double vL = gL * L.sx * U[sidx(P, v, 1, L.i, 0)], vR = gR * R.sx * U[sidx(P, v, 1, R.i, 0)];
     Mod[(long long)v * P.plane + i] = MOD_WU * (uR - uL) + MOD_WV * (vL + vR);
   }
 }
@@ -137,7 +140,10 @@ template <typename T, int NV>
 __device__ __forceinline__ void gl1(const Prob& P, const T* __restrict__ G, const Img& m, int k, T (&u)[NV]) {
   const int p = mpt1(m, k);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) u[v] = G[(long long)(v * 4 + p) * P.gplane + m.i];
+  for (int v = 0; v < NV; ++v) {
+    const T x = G[(long long)(v * 4 + p) * P.gplane + m.i];
+    u[v] = (m.neg >> v) & 1 ? -x : x;
+  }
 }
 
 template <typename T, int NV>

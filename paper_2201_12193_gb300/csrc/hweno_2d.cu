@@ -30,16 +30,22 @@ constexpr int RB = 128;          // threads per block of the per-cell kernels
 struct Nbr {
   int xi[3], xs[3];     // image column and sign of the x first moment, for ox = -1, 0, 1
   int yj[3], ys[3];     // image row and sign of the y first moment, for oy = -1, 0, 1
+  int neg[3][3];        // variables negated by reflective walls, [oy + 1][ox + 1]
 };
 
 __device__ __forceinline__ Nbr neighbours(const Prob& P, int i, int j) {
   Nbr n;
+  int nx[3], ny[3];
 #pragma unroll
   for (int o = -1; o <= 1; ++o) {
     const Img a = image(P, i + o, j), b = image(P, i, j + o);
-    n.xi[o + 1] = a.i; n.xs[o + 1] = a.sx;
-    n.yj[o + 1] = b.j; n.ys[o + 1] = b.sy;
+    n.xi[o + 1] = a.i; n.xs[o + 1] = a.sx; nx[o + 1] = a.neg;
+    n.yj[o + 1] = b.j; n.ys[o + 1] = b.sy; ny[o + 1] = b.neg;
   }
+#pragma unroll
+  for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+    for (int ox = 0; ox < 3; ++ox) n.neg[oy][ox] = nx[ox] | ny[oy];
   return n;
 }
 
@@ -58,13 +64,18 @@ __device__ __forceinline__ double load_mom(const Prob& P, const double* __restri
                                            int oy, bool usemod) {
   const int ci = n.xi[ox + 1], cj = n.yj[oy + 1];
   const long long so = (long long)cj * P.pitch + ci;
-  if (kind == 0) return U[(long long)(var * 3) * P.plane + so];
+  if (kind == 0) {
+    const double u = U[(long long)(var * 3) * P.plane + so];
+    return (n.neg[oy + 1][ox + 1] >> var) & 1 ? -u : u;
+  }
   double v;
   if (MODE != REC_PLAIN && usemod && mask[(long long)cj * P.nx + ci] == 1)
     v = Mod[(long long)(var * 2 + kind - 1) * P.plane + so];
   else
     v = U[(long long)(var * 3 + kind) * P.plane + so];
-  return (kind == 1 ? n.xs[ox + 1] : n.ys[oy + 1]) < 0 ? -v : v;
+  if (kind == 1 && n.xs[ox + 1] < 0) v = -v;
+  if (kind == 2 && n.ys[oy + 1] < 0) v = -v;
+  return (n.neg[oy + 1][ox + 1] >> var) & 1 ? -v : v;
 }
 
 template <typename T, int NV, int MODE>
@@ -185,10 +196,11 @@ __device__ __forceinline__ void modify2d_cell(const Prob& P, const double* __res
   const long long o = (long long)j * P.pitch + i;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const double uL = U[sidx(P, v, 0, L.i, L.j)], uR = U[sidx(P, v, 0, R.i, R.j)];
-    const double vL = L.sx * U[sidx(P, v, 1, L.i, L.j)], vR = R.sx * U[sidx(P, v, 1, R.i, R.j)];
-    const double uB = U[sidx(P, v, 0, Bo.i, Bo.j)], uT = U[sidx(P, v, 0, Tp.i, Tp.j)];
-    const double wB = Bo.sy * U[sidx(P, v, 2, Bo.i, Bo.j)], wT = Tp.sy * U[sidx(P, v, 2, Tp.i, Tp.j)];
+    const int gL = vsign(L, v), gR = vsign(R, v), gB = vsign(Bo, v), gT = vsign(Tp, v);
+    const double uL = gL * U[sidx(P, v, 0, L.i, L.j)], uR = gR * U[sidx(P, v, 0, R.i, R.j)];
+    const double vL = gL * L.sx * U[sidx(P, v, 1, L.i, L.j)], vR = gR * R.sx * U[sidx(P, v, 1, R.i, R.j)];
+    const double uB = gB * U[sidx(P, v, 0, Bo.i, Bo.j)], uT = gT * U[sidx(P, v, 0, Tp.i, Tp.j)];
+    const double wB = gB * Bo.sy * U[sidx(P, v, 2, Bo.i, Bo.j)], wT = gT * Tp.sy * U[sidx(P, v, 2, Tp.i, Tp.j)];
     Mod[(long long)(v * 2 + 0) * P.plane + o] = MOD_WU * (uR - uL) + MOD_WV * (vL + vR);
     Mod[(long long)(v * 2 + 1) * P.plane + o] = MOD_WU * (uT - uB) + MOD_WV * (wB + wT);
   }
@@ -256,7 +268,10 @@ __device__ __forceinline__ void gl_state(const Prob& P, const T* __restrict__ G,
   const long long o = goff(P, m.i, m.j);
   const int p = mpt(m, k, l);
 #pragma unroll
-  for (int v = 0; v < NV; ++v) u[v] = G[(long long)(v * 16 + p) * P.gplane + o];
+  for (int v = 0; v < NV; ++v) {
+    const T x = G[(long long)(v * 16 + p) * P.gplane + o];
+    u[v] = (m.neg >> v) & 1 ? -x : x;
+  }
 }
 
 struct Rk {

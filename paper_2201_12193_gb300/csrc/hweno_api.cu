@@ -155,7 +155,11 @@ hweno_status validate(const hweno_grid* g, const hweno_bc* bc, double gamma, std
     if (!(g->gamma_bar[l] > 0.0) || !isfinite(g->gamma_bar[l])) { why = "gamma_bar must be positive"; return HWENO_EINVAL; }
   const int k[4] = {bc->xlo, bc->xhi, bc->ylo, bc->yhi};
   for (int s = 0; s < (g->dim == 2 ? 4 : 2); ++s)
-    if (k[s] != HWENO_BC_PERIODIC && k[s] != HWENO_BC_TRANSMISSIVE) { why = "unknown boundary kind"; return HWENO_EINVAL; }
+    if (k[s] != HWENO_BC_PERIODIC && k[s] != HWENO_BC_TRANSMISSIVE && k[s] != HWENO_BC_REFLECTIVE) {
+      why = "unknown boundary kind"; return HWENO_EINVAL;
+    } else if (k[s] == HWENO_BC_REFLECTIVE && g->eq != HWENO_EULER) {
+      why = "reflective walls need the Euler equations"; return HWENO_EINVAL;
+    }
   if ((bc->xlo == HWENO_BC_PERIODIC) != (bc->xhi == HWENO_BC_PERIODIC) ||
       (g->dim == 2 && (bc->ylo == HWENO_BC_PERIODIC) != (bc->yhi == HWENO_BC_PERIODIC))) {
     why = "periodic sides must come in pairs"; return HWENO_EINVAL;

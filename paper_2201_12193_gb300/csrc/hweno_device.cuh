@@ -17,7 +17,7 @@
 namespace hw {
 
 constexpr int EQ_ADV = 0, EQ_BURGERS = 1, EQ_EULER = 2;
-constexpr int BC_PERIODIC = 0, BC_TRANSMISSIVE = 1;
+constexpr int BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2;
 constexpr int IND_NONE = 0, IND_KXRCF = 1, IND_ALL = 2, IND_MLP = 3;
 
 // device status word bits
@@ -81,18 +81,31 @@ template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b
 // A ghost cell is the image of an interior cell: periodic wrap, or (transmissive)
 // the mirror about the boundary face, under which the mirrored direction's first
 // moment changes sign and point values are reversed along that direction.
-struct Img { int i, j, sx, sy; };
+// A reflective boundary (a solid wall, Euler only) is the transmissive mirror
+// with the wall-normal momentum negated as well (all its moments and point
+// values): neg has bit v set for each variable v the image negates
+// (variable 1 = x momentum, 2 = y momentum in 2D).
+struct Img { int i, j, sx, sy, neg; };
 
 __device__ __forceinline__ int wrap(int i, int n) { i %= n; return i < 0 ? i + n : i; }
 
 __device__ __forceinline__ Img image(const Prob& P, int i, int j) {
-  Img r{i, j, 1, 1};
-  if (i < 0) { if (P.bc[0] == BC_PERIODIC) r.i = wrap(i, P.nx); else { r.i = -1 - i; r.sx = -1; } }
-  else if (i >= P.nx) { if (P.bc[1] == BC_PERIODIC) r.i = wrap(i, P.nx); else { r.i = 2 * P.nx - 1 - i; r.sx = -1; } }
-  if (j < 0) { if (P.bc[2] == BC_PERIODIC) r.j = wrap(j, P.ny); else { r.j = -1 - j; r.sy = -1; } }
-  else if (j >= P.ny) { if (P.bc[3] == BC_PERIODIC) r.j = wrap(j, P.ny); else { r.j = 2 * P.ny - 1 - j; r.sy = -1; } }
+  Img r{i, j, 1, 1, 0};
+  if (i < 0 || i >= P.nx) {
+    const int k = P.bc[i < 0 ? 0 : 1];
+    if (k == BC_PERIODIC) r.i = wrap(i, P.nx);
+    else { r.i = i < 0 ? -1 - i : 2 * P.nx - 1 - i; r.sx = -1; if (k == BC_REFLECTIVE) r.neg |= 2; }
+  }
+  if (j < 0 || j >= P.ny) {
+    const int k = P.bc[j < 0 ? 2 : 3];
+    if (k == BC_PERIODIC) r.j = wrap(j, P.ny);
+    else { r.j = j < 0 ? -1 - j : 2 * P.ny - 1 - j; r.sy = -1; if (k == BC_REFLECTIVE) r.neg |= 4; }
+  }
   return r;
 }
+
+// Sign of variable v of an image cell (reflective walls)
+__device__ __forceinline__ int vsign(const Img& m, int v) { return (m.neg >> v) & 1 ? -1 : 1; }
 
 __device__ __forceinline__ long long sidx(const Prob& P, int var, int mom, int i, int j) {
   return (long long)(var * P.nmom + mom) * P.plane + (long long)j * P.pitch + i;
@@ -432,10 +445,13 @@ __device__ __forceinline__ T kxrcf2d(const Prob& P, const Weights<T>& W, const T
   const long long o = goff(P, i, j);
   const Img L = image(P, i - 1, j), R = image(P, i + 1, j), Bo = image(P, i, j - 1), Tp = image(P, i, j + 1);
   const long long oL = goff(P, L.i, L.j), oR = goff(P, R.i, R.j), oB = goff(P, Bo.i, Bo.j), oT = goff(P, Tp.i, Tp.j);
-  const T vxl = T(0.5) * (aux[(L.sx < 0 ? 0 : 1) * P.gplane + oL] + aux[0 * P.gplane + o]);
-  const T vxr = T(0.5) * (aux[1 * P.gplane + o] + aux[(R.sx < 0 ? 1 : 0) * P.gplane + oR]);
-  const T vyb = T(0.5) * (aux[(Bo.sy < 0 ? 2 : 3) * P.gplane + oB] + aux[2 * P.gplane + o]);
-  const T vyt = T(0.5) * (aux[3 * P.gplane + o] + aux[(Tp.sy < 0 ? 3 : 2) * P.gplane + oT]);
+  // the neighbours' face velocities (the x ones negated through an x wall, the y ones through a y wall)
+  const T axl = aux[(L.sx < 0 ? 0 : 1) * P.gplane + oL], axr = aux[(R.sx < 0 ? 1 : 0) * P.gplane + oR];
+  const T ayb = aux[(Bo.sy < 0 ? 2 : 3) * P.gplane + oB], ayt = aux[(Tp.sy < 0 ? 3 : 2) * P.gplane + oT];
+  const T vxl = T(0.5) * ((L.neg & 2 ? -axl : axl) + aux[0 * P.gplane + o]);
+  const T vxr = T(0.5) * (aux[1 * P.gplane + o] + (R.neg & 2 ? -axr : axr));
+  const T vyb = T(0.5) * ((Bo.neg & 4 ? -ayb : ayb) + aux[2 * P.gplane + o]);
+  const T vyt = T(0.5) * (aux[3 * P.gplane + o] + (Tp.neg & 4 ? -ayt : ayt));
   const T dx = T(P.dx), dy = T(P.dy);
   T s = T(0), len = T(0);
   if (vxl > T(KX_VDEAD)) {

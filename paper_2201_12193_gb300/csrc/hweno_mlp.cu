@@ -79,11 +79,11 @@ __device__ __forceinline__ float clipf(float x) { return fminf(CLIPF, fmaxf(-CLI
 // everything after in FP32.  emit(q, value) receives feature q.
 template <typename Emit>
 __device__ __forceinline__ void cell_features(const Prob& P, const double* __restrict__ U, int i, int j, Emit emit) {
-  int xi[3], xs[3], yj[3], ys[3];
+  int xi[3], xs[3], yj[3], ys[3], xn[3], yn[3];
 #pragma unroll
   for (int o = -1; o <= 1; ++o) {
     const Img a = image(P, i + o, j), b = image(P, i, j + o);
-    xi[o + 1] = a.i; xs[o + 1] = a.sx; yj[o + 1] = b.j; ys[o + 1] = b.sy;
+    xi[o + 1] = a.i; xs[o + 1] = a.sx; yj[o + 1] = b.j; ys[o + 1] = b.sy; xn[o + 1] = a.neg; yn[o + 1] = b.neg;
   }
   const float h2 = (float)(P.dx * P.dx);
 #pragma unroll 1
@@ -99,11 +99,13 @@ __device__ __forceinline__ void cell_features(const Prob& P, const double* __res
     for (int k = 0; k < 9; ++k) {
       const int ox = k % 3, oy = k / 3;
       const long long so = (long long)yj[oy] * P.pitch + xi[ox];
-      const double uk = U0[so];
+      const bool wall = ((xn[ox] | yn[oy]) >> v) & 1;     // reflective image: normal momentum negated
+      const double uk = wall ? -U0[so] : U0[so];
       du[k] = d2f_trunc(uk - uc);
       umax = fmaxf(umax, fabsf(d2f_trunc(uk)));
       D = fmaxf(D, fabsf(du[k]));
-      const float a = d2f_trunc(U1[so]), b = d2f_trunc(U2[so]);
+      float a = d2f_trunc(U1[so]), b = d2f_trunc(U2[so]);
+      if (wall) { a = -a; b = -b; }
       vb[k] = xs[ox] < 0 ? -a : a;
       wb[k] = ys[oy] < 0 ? -b : b;
     }
@@ -541,10 +543,11 @@ __global__ void __launch_bounds__(MTN) mlpre2d_kernel(Prob P, const float* __res
         const long long o = (long long)j * P.pitch + i;
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          const double uL = U[sidx(P, v, 0, L.i, L.j)], uR = U[sidx(P, v, 0, R.i, R.j)];
-          const double vL = L.sx * U[sidx(P, v, 1, L.i, L.j)], vR = R.sx * U[sidx(P, v, 1, R.i, R.j)];
-          const double uB = U[sidx(P, v, 0, Bo.i, Bo.j)], uT = U[sidx(P, v, 0, Tp.i, Tp.j)];
-          const double wB = Bo.sy * U[sidx(P, v, 2, Bo.i, Bo.j)], wT = Tp.sy * U[sidx(P, v, 2, Tp.i, Tp.j)];
+          const int gL = vsign(L, v), gR = vsign(R, v), gB = vsign(Bo, v), gT = vsign(Tp, v);
+          const double uL = gL * U[sidx(P, v, 0, L.i, L.j)], uR = gR * U[sidx(P, v, 0, R.i, R.j)];
+          const double vL = gL * L.sx * U[sidx(P, v, 1, L.i, L.j)], vR = gR * R.sx * U[sidx(P, v, 1, R.i, R.j)];
+          const double uB = gB * U[sidx(P, v, 0, Bo.i, Bo.j)], uT = gT * U[sidx(P, v, 0, Tp.i, Tp.j)];
+          const double wB = gB * Bo.sy * U[sidx(P, v, 2, Bo.i, Bo.j)], wT = gT * Tp.sy * U[sidx(P, v, 2, Tp.i, Tp.j)];
           Mod[(long long)(v * 2 + 0) * P.plane + o] = MOD_WU * (uR - uL) + MOD_WV * (vL + vR);
           Mod[(long long)(v * 2 + 1) * P.plane + o] = MOD_WU * (uT - uB) + MOD_WV * (wB + wT);
         }

@@ -19,7 +19,7 @@ _lib = None
 STATUS = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "ENONPHYSICAL", -4: "ETIMEOUT", -5: "ESTATE", -6: "ENOMEM"}
 EQ = {"advection": 0, "burgers": 1, "euler": 2}
 IND = {"none": 0, "kxrcf": 1, "all": 2, "mlp": 3}
-BC = {"periodic": 0, "transmissive": 1}
+BC = {"periodic": 0, "transmissive": 1, "reflective": 2}
 PREC = {"fp64": 0, "fp32": 1, "df64": 2}
 
 

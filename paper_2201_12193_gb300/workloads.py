@@ -157,6 +157,19 @@ def sod_1d(nx=200):
     return riemann_1d((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), nx, name="sod_1d", t_end=0.2)
 
 
+def blast_wave_1d(nx=800):
+    """Interacting blast waves (Example 3.7) on [0, 1], to t = 0.038: pressure
+    1000 / 0.01 / 100 split at 0.1 and 0.9, rho = 1, at rest.  The paper does not
+    state the boundary; reflective walls at both ends (the problem's usual
+    setting).  Faces at 0.1 and 0.9 are cell faces when nx is a multiple of 10,
+    so the moments are exact."""
+    def f(x):
+        p = np.where(x < 0.1, 1000.0, np.where(x < 0.9, 0.01, 100.0))
+        return prim_to_cons_1d(np.ones_like(x), np.zeros_like(x), p)
+    m = moments_1d(f, 0.0, 1.0, nx)
+    return Problem("blast_wave_1d", 1, nx, 1, 0.0, 1.0, 0.0, 1.0, "euler", ("reflective",) * 4, m, t_end=0.038)
+
+
 def shu_osher_1d(nx=4000):
     """Shock / density-wave interaction on [-5, 5] (Example 3.6), transmissive ends."""
     def f(x):
@@ -243,6 +256,14 @@ def vortex_2d(n=128, seed=0, L=10.0, npts=8):
     m = moments_2d(f, 0.0, L, 0.0, L, n, n, npts=npts)
     return Problem("vortex_2d", 2, n, n, 0.0, L, 0.0, L, "euler", ("periodic",) * 4, m, seed=seed,
                    meta={"eps": eps, "xc": xc, "yc": yc})
+
+
+def walled_blast_2d(n=64, seed=0, ncircles=2, walls=("reflective",) * 4):
+    """blast_2d data in a box with the given boundary kinds (xlo, xhi, ylo, yhi)."""
+    p = blast_2d(n, seed=seed, ncircles=ncircles)
+    p.bc = tuple(walls)
+    p.name = "walled_blast_2d"
+    return p
 
 
 def blast_2d(n=4096, seed=0, ncircles=8):

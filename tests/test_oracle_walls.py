@@ -1,0 +1,115 @@
+"""CPU pins of the reflective-wall boundary (a solid wall: the transmissive
+mirror with the wall-normal momentum negated) in the oracle.
+
+* No mass and no energy cross a wall: the cell sums of L for rho and E vanish
+  to rounding with walls on every side (they do not with transmissive sides).
+* A wall is a symmetry plane: a mirror-symmetric problem on [0, 1] with walls
+  equals, on [0, 1/2], the half problem with a wall at 1/2 (one step, 1D and 2D).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_2201_12193_gb300 import workloads as W
+
+
+def _state_1d(n, rng):
+    x = (np.arange(n) + 0.5) / n
+    rho = 1.0 + 0.3 * rng.random(n)
+    mu = 0.5 * rng.standard_normal(n)
+    p = 1.0 + rng.random(n)
+    m = np.zeros((3, 2, 1, n))
+    m[:, 0, 0] = W.prim_to_cons_1d(rho, mu, p)
+    m[:, 1, 0] = 0.02 * rng.standard_normal((3, n))
+    return m
+
+
+def test_no_mass_or_energy_through_walls_1d(orc):
+    rng = np.random.default_rng(1)
+    n = 40
+    m = _state_1d(n, rng)
+    for bc, zero in (("reflective", True), ("transmissive", False)):
+        cfg = orc.make_cfg(1, n, dx=1.0 / n, eq="euler", bc=(bc,) * 4)
+        _, L, _, _, rc = orc.rhs(cfg, m)
+        assert rc == 0
+        for v in (0, 2):
+            tot, scale = L[v, 0].sum(), np.abs(L[v, 0]).sum()
+            if zero:
+                assert abs(tot) <= 1e-13 * scale, (v, tot, scale)
+            else:
+                assert abs(tot) > 1e-6 * scale
+
+
+def test_no_mass_or_energy_through_walls_2d(orc):
+    p = W.walled_blast_2d(24, seed=3, ncircles=2)
+    rng = np.random.default_rng(2)
+    m = p.m.copy()
+    m[1:3, 0] += 0.1 * rng.standard_normal(m[1:3, 0].shape)        # moving fluid everywhere
+    m[:, 1:] += 1e-3 * rng.standard_normal(m[:, 1:].shape)
+    cfg = orc.make_cfg(2, p.nx, p.ny, dx=p.dx, dy=p.dy, eq="euler", bc=p.bc)
+    _, L, _, _, rc = orc.rhs(cfg, m)
+    assert rc == 0
+    for v in (0, 3):
+        assert abs(L[v, 0].sum()) <= 1e-13 * np.abs(L[v, 0]).sum()
+
+
+def _mirror_1d(half):
+    """Extend a state on [0, 1/2] to its mirror image on [0, 1] about x = 1/2."""
+    full = np.concatenate([half, half[..., ::-1]], axis=-1)
+    n = half.shape[-1]
+    full[1, 0, :, n:] *= -1.0            # momentum average: antisymmetric
+    full[0, 1, :, n:] *= -1.0            # first moments of rho and E: antisymmetric
+    full[2, 1, :, n:] *= -1.0
+    return full
+
+
+def test_wall_is_a_symmetry_plane_1d(orc):
+    rng = np.random.default_rng(4)
+    n = 50
+    half = _state_1d(n, rng)
+    full = _mirror_1d(half)
+    c_half = orc.make_cfg(1, n, dx=0.5 / n, eq="euler", bc=("reflective",) * 4)
+    c_full = orc.make_cfg(1, 2 * n, dx=0.5 / n, eq="euler", bc=("reflective",) * 4)
+    dt = 0.5 * orc.max_dt(c_full, full, 0.6)
+    h, mh, rc1 = orc.step(c_half, half, dt)
+    f, mf, rc2 = orc.step(c_full, full, dt)
+    assert rc1 == 0 and rc2 == 0
+    np.testing.assert_allclose(f[..., :n], h, rtol=0, atol=1e-12 * np.abs(h).max())
+    assert np.array_equal(mf[:, :n], mh)
+
+
+def _contact_state_2d(nx, ny, rng):
+    """A density jump (a contact, KXRCF active) over smooth pressure and velocity."""
+    x = (np.arange(nx) + 0.5) / nx
+    y = (np.arange(ny) + 0.5) / nx
+    X, Y = np.meshgrid(x, y)
+    rho = 1.0 + 0.5 * (X > 0.4) + 0.1 * np.sin(3 * Y)
+    u = 0.2 * np.cos(2 * X) + 0.05 * Y
+    v = 0.1 * np.sin(4 * X) * (1 + Y)
+    p = 1.0 + 0.2 * np.cos(3 * X + Y)
+    m = np.zeros((4, 3, ny, nx))
+    m[:, 0] = W.prim_to_cons_2d(rho, u, v, p)
+    m[:, 1:] = 1e-3 * rng.standard_normal(m[:, 1:].shape)
+    return m
+
+
+def test_wall_is_a_symmetry_plane_2d(orc):
+    """Mirror in y about y = 1/2: the half box with a wall at the top."""
+    rng = np.random.default_rng(6)
+    half = _contact_state_2d(16, 8, rng)
+    p = W.walled_blast_2d(16, seed=5, ncircles=2)     # grid spacing only
+    full = np.concatenate([half, half[:, :, ::-1, :]], axis=2)
+    full[2, 0, 8:] *= -1.0               # y momentum: antisymmetric
+    for v in (0, 1, 3):
+        full[v, 2, 8:] *= -1.0           # y first moments of the symmetric variables
+    full[2, 1, 8:] *= -1.0               # x first moment of the y momentum: antisymmetric
+    bc = ("transmissive", "transmissive", "reflective", "reflective")
+    c_half = orc.make_cfg(2, 16, 8, dx=p.dx, dy=p.dy, eq="euler", bc=bc)
+    c_full = orc.make_cfg(2, 16, 16, dx=p.dx, dy=p.dy, eq="euler", bc=bc)
+    dt = 0.5 * orc.max_dt(c_full, full, 0.6)
+    h, mh, rc1 = orc.step(c_half, half, dt)
+    f, mf, rc2 = orc.step(c_full, full, dt)
+    assert rc1 == 0 and rc2 == 0
+    assert mh.sum() > 0                  # the indicator takes part
+    np.testing.assert_allclose(f[:, :, :8], h, rtol=0, atol=1e-12 * np.abs(h).max())
+    assert np.array_equal(mf.reshape(3, 16, 16)[:, :8], mh.reshape(3, 8, 16))
