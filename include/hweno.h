@@ -60,7 +60,9 @@ typedef enum {
 
 typedef enum { HWENO_ADVECTION = 0, HWENO_BURGERS = 1, HWENO_EULER = 2 } hweno_eq;
 typedef enum { HWENO_BC_PERIODIC = 0, HWENO_BC_TRANSMISSIVE = 1, HWENO_BC_REFLECTIVE = 2 } hweno_bc_kind;
-typedef enum { HWENO_IND_NONE = 0, HWENO_IND_KXRCF = 1, HWENO_IND_ALL = 2, HWENO_IND_MLP = 3 } hweno_indicator;
+typedef enum {
+  HWENO_IND_NONE = 0, HWENO_IND_KXRCF = 1, HWENO_IND_ALL = 2, HWENO_IND_MLP = 3, HWENO_IND_TVB = 4
+} hweno_indicator;
 
 /* Uniform mesh and scheme options.
  *   dim 1 or 2; nx, ny >= 4 (ny ignored in 1D); 2D cells must be square
@@ -76,11 +78,17 @@ typedef enum { HWENO_IND_NONE = 0, HWENO_IND_KXRCF = 1, HWENO_IND_ALL = 2, HWENO
  *   indicator: HWENO_IND_KXRCF is the scheme (HWENO6-M5-I); NONE gives HWENO6
  *   (no modification); ALL gives HWENO6-M5-NI (every cell modified) (Sec. 3);
  *   MLP: the learned indicator with KXRCF fallback (see below; 2D Euler).
+ *   TVB: the minmod-based TVB indicator of Remark 2 on the indicator variable
+ *   (u, or rho for Euler), acting on the cell's linear polynomial of its
+ *   moments: troubled when the modified minmod (identity for |a| <= tvb_m dx^2)
+ *   changes a = 6 vbar (6 wbar in y), the polynomial's face deviation, against
+ *   the forward and backward differences of the averages in that direction.
  *   gamma_bar: positive linear-weight seeds of eq. (linear-weight)
  *   (gamma_{l1,l2} = gamma_bar[l1-1] / sum_{l<=l2} gamma_bar[l-1]); the paper
  *   uses {1, 10, 100, 1000}.
  *   beta_of_q: 0 = smoothness indicators of p_l as eq. (beta) states (default);
- *   1 = of q_l (the variant for which Remark 1's expansion holds for every l). */
+ *   1 = of q_l (the variant for which Remark 1's expansion holds for every l).
+ *   tvb_m: the TVB constant M (>= 0) of indicator TVB; ignored otherwise. */
 typedef struct {
   int dim;
   int nx, ny;
@@ -91,6 +99,7 @@ typedef struct {
   int indicator;
   double gamma_bar[4];
   int beta_of_q;
+  double tvb_m;
 } hweno_grid;
 
 /* Boundary kinds of the four sides.  Periodic sides must come in pairs.

@@ -25,7 +25,7 @@ _lock = threading.Lock()
 _lib = None
 
 EQ = {"advection": 0, "burgers": 1, "euler": 2}
-IND = {"none": 0, "kxrcf": 1, "all": 2, "given": 3}
+IND = {"none": 0, "kxrcf": 1, "all": 2, "given": 3, "tvb": 4}
 BC = {"periodic": 0, "transmissive": 1, "reflective": 2}
 
 
@@ -43,11 +43,12 @@ class Cfg(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("eq", ctypes.c_int),
                 ("adv_a", ctypes.c_double), ("adv_b", ctypes.c_double), ("gamma", ctypes.c_double),
-                ("indicator", ctypes.c_int), ("gbar", ctypes.c_double * 4), ("bc", ctypes.c_int * 4)]
+                ("indicator", ctypes.c_int), ("gbar", ctypes.c_double * 4), ("bc", ctypes.c_int * 4),
+                ("tvb_m", ctypes.c_double)]
 
 
 def make_cfg(dim, nx, ny=1, dx=1.0, dy=1.0, eq="euler", adv=(1.0, 0.0), gamma=1.4,
-             indicator="kxrcf", gbar=(1.0, 10.0, 100.0, 1000.0), bc=("periodic",) * 4) -> Cfg:
+             indicator="kxrcf", gbar=(1.0, 10.0, 100.0, 1000.0), bc=("periodic",) * 4, tvb_m=0.0) -> Cfg:
     c = Cfg()
     c.dim, c.nx, c.ny = dim, nx, (ny if dim == 2 else 1)
     c.dx, c.dy = dx, (dy if dim == 2 else 1.0)
@@ -55,6 +56,7 @@ def make_cfg(dim, nx, ny=1, dx=1.0, dy=1.0, eq="euler", adv=(1.0, 0.0), gamma=1.
     c.adv_a, c.adv_b = adv
     c.gamma = gamma
     c.indicator = IND[indicator] if isinstance(indicator, str) else int(indicator)
+    c.tvb_m = tvb_m
     for k in range(4):
         c.gbar[k] = gbar[k]
         b = bc[k]

@@ -50,9 +50,11 @@ typedef struct {
   double adv_a, adv_b; /* advection speeds (f = a u, g = b u) */
   double gamma;     /* ratio of specific heats (Euler) */
   int indicator;    /* 0 none (HWENO6), 1 KXRCF (M5-I), 2 all cells (M5-NI),
-                       3 given decisions with KXRCF for the deferred cells */
+                       3 given decisions with KXRCF for the deferred cells,
+                       4 the minmod-based TVB indicator (Remark 2) */
   double gbar[4];   /* positive linear-weight seeds, eq. (linear-weight) */
   int bc[4];        /* x-lo, x-hi, y-lo, y-hi: 0 periodic, 1 transmissive, 2 reflective (Euler) */
+  double tvb_m;     /* TVB constant M of indicator 4 */
 } orc_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -699,6 +701,35 @@ static int finite_state(const orc_cfg *c, const double *m) {
   return 1;
 }
 
+/* The minmod-based TVB indicator named in Remark 2 (Cockburn & Shu's TVB
+ * limiter, used as a troubled-cell indicator) on the indicator variable (u, or
+ * rho for Euler).  Reading: it acts on the cell's own linear polynomial fixed by
+ * its zeroth and first moments, u = ubar + 12 vbar (x - x_i)/dx (+ 12 wbar
+ * (y - y_j)/dy in 2D), whose face deviations from the average are +-6 vbar
+ * (6 wbar); the cell is troubled when the modified minmod
+ *   m(a, b, c) = a if |a| <= M h^2, else minmod(a, b, c)
+ * changes a = 6 vbar (or 6 wbar) against the forward and backward differences
+ * of the averages in that direction; h = dx, M = tvb_m. */
+static int tvb_changes(double a, double b, double cc, double bound) {
+  if (fabs(a) <= bound) return 0;
+  double mm = 0.0;
+  if (a > 0.0 && b > 0.0 && cc > 0.0) mm = fmin(a, fmin(b, cc));
+  else if (a < 0.0 && b < 0.0 && cc < 0.0) mm = fmax(a, fmax(b, cc));
+  return mm != a;
+}
+
+static int tvb_flag(const orc_cfg *c, const double *U, int i, int j) {
+  const double bound = c->tvb_m * c->dx * c->dx;
+  const double u0 = mom_at(c, U, 0, 0, i, j);
+  const double ax = 6.0 * mom_at(c, U, 0, 1, i, j);
+  const double dxp = mom_at(c, U, 0, 0, i + 1, j) - u0, dxm = u0 - mom_at(c, U, 0, 0, i - 1, j);
+  if (tvb_changes(ax, dxp, dxm, bound)) return 1;
+  if (c->dim == 1) return 0;
+  const double ay = 6.0 * mom_at(c, U, 0, 2, i, j);
+  const double dyp = mom_at(c, U, 0, 0, i, j + 1) - u0, dym = u0 - mom_at(c, U, 0, 0, i, j - 1);
+  return tvb_changes(ay, dyp, dym, bound);
+}
+
 /* Step 2.2: modified first moments of the selected cells (eq. (vi), applied
  * dimension by dimension in 2D) written into Umod.  Reading: every new value
  * is computed from the pre-modification moments U (Jacobi). */
@@ -775,6 +806,7 @@ int orc_rhs(const orc_cfg *c, const double *U, double *Umod, double *Lout,
         if (c->indicator == 1) a = kxrcf_aleph(c, G, i, j);
         if (aleph) aleph[cell] = a;
         flag[cell] = c->indicator == 2 ? 1 : (c->indicator == 1 && a > 1.0);
+        if (c->indicator == 4) flag[cell] = (unsigned char)tvb_flag(c, U, i, j);
       }
     /* Step 2.2: modify the first moments of troubled cells */
     modify_cells(c, U, Umod, flag);

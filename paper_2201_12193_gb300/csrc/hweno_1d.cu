@@ -92,6 +92,8 @@ __global__ void __launch_bounds__(RB) flag1d_kernel(Prob P, Weights<T> W, const 
     R = image(P, i + 1, 0);
     if (P.indicator == IND_ALL) {
       flag = true;
+    } else if (P.indicator == IND_TVB) {
+      flag = tvb_cell(P, U, i, 0);
     } else if (P.indicator == IND_KXRCF) {
       // face velocities: average of both sides' velocities at the face
       const T al = aux[(L.sx < 0 ? 0 : 1) * P.gplane + L.i], ar = aux[(R.sx < 0 ? 1 : 0) * P.gplane + R.i];

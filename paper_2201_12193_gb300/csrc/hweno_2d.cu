@@ -178,9 +178,11 @@ __global__ void __launch_bounds__(RB, (is_df64<T>::value ? 4 : 1)) rec2d_kernel(
 
 // Step 2.1 for one cell: the troubled-cell decision of the configured indicator.
 template <typename T>
-__device__ __forceinline__ bool flag2d_cell(const Prob& P, const Weights<T>& W, const T* __restrict__ G,
-                                            const T* __restrict__ aux, int i, int j, double* __restrict__ aleph) {
+__device__ __forceinline__ bool flag2d_cell(const Prob& P, const Weights<T>& W, const double* __restrict__ U,
+                                            const T* __restrict__ G, const T* __restrict__ aux, int i, int j,
+                                            double* __restrict__ aleph) {
   if (P.indicator == IND_ALL) return true;
+  if (P.indicator == IND_TVB) return tvb_cell(P, U, i, j);
   if (P.indicator != IND_KXRCF) return false;
   const T a = kxrcf2d<T>(P, W, G, aux, i, j);
   if (aleph) aleph[(long long)j * P.nx + i] = double(a);
@@ -227,7 +229,7 @@ __global__ void __launch_bounds__(TX * TY) flag2d_kernel(Prob P, Weights<T> W, c
                                                         double* __restrict__ aleph) {
   const int i = blockIdx.x * TX + threadIdx.x, j = blockIdx.y * TY + threadIdx.y;
   const bool valid = i < P.nx && j < P.ny;
-  const bool flag = valid && flag2d_cell<T>(P, W, G, aux, i, j, aleph);
+  const bool flag = valid && flag2d_cell<T>(P, W, U, G, aux, i, j, aleph);
   warp_append<int>(flag, j * P.nx + i, list, count);   // a warp is one tile row
   if (!valid) return;
   mask[(long long)j * P.nx + i] = flag ? 1 : 0;
@@ -577,7 +579,7 @@ __global__ void __launch_bounds__(TXV * TYV) batch_stage_kernel(BatchStage A, We
     const int cell = (it - Q.rec_first) * RB + tid;
     const bool valid = cell < Q.P.nx * Q.P.ny;
     const int i = cell % Q.P.nx, j = cell / Q.P.nx;
-    const bool flag = valid && flag2d_cell<T>(Q.P, W, G + Q.goff, aux + Q.aoff, i, j, nullptr);
+    const bool flag = valid && flag2d_cell<T>(Q.P, W, A.Uin + Q.uoff, G + Q.goff, aux + Q.aoff, i, j, nullptr);
     warp_append<unsigned long long>(flag, ((unsigned long long)p << 32) | (unsigned)cell, A.list, A.count);
     if (valid) {
       A.mask[Q.coff + cell] = flag ? 1 : 0;

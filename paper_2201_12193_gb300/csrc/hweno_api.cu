@@ -147,7 +147,8 @@ hweno_status validate(const hweno_grid* g, const hweno_bc* bc, double gamma, std
   if (g->precision < 0 || g->precision > 2) {
     why = "precision must be 0 (fp64), 1 (fp32 bulk) or 2 (double-float)"; return HWENO_EINVAL;
   }
-  if (g->indicator < 0 || g->indicator > 3) { why = "indicator must be none, kxrcf, all or mlp"; return HWENO_EINVAL; }
+  if (g->indicator < 0 || g->indicator > 4) { why = "indicator must be none, kxrcf, all, mlp or tvb"; return HWENO_EINVAL; }
+  if (g->indicator == 4 && !(g->tvb_m >= 0.0 && isfinite(g->tvb_m))) { why = "tvb_m must be finite and >= 0"; return HWENO_EINVAL; }
   if (g->indicator == 3 && (g->dim != 2 || g->eq != HWENO_EULER)) {
     why = "the learned indicator is defined for 2D Euler"; return HWENO_EINVAL;
   }
@@ -272,6 +273,7 @@ hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gam
   P.nmom = h->g.dim == 1 ? 2 : 3;
   P.eq = h->g.eq;
   P.indicator = h->g.indicator;
+  P.tvb_m = h->g.tvb_m;
   P.bc[0] = bc->xlo; P.bc[1] = bc->xhi;
   P.bc[2] = h->g.dim == 2 ? bc->ylo : HWENO_BC_PERIODIC;
   P.bc[3] = h->g.dim == 2 ? bc->yhi : HWENO_BC_PERIODIC;
@@ -754,7 +756,7 @@ hweno_status hweno_create_batch(const hweno_grid* grids, const hweno_bc* bcs, in
     P.nx = g.nx; P.ny = g.ny;
     P.pitch = (P.nx + 31) / 32 * 32; P.plane = (long long)P.ny * P.pitch;
     P.gpitch = P.pitch; P.gplane = P.plane;
-    P.nvar = 4; P.nmom = 3; P.eq = HWENO_EULER; P.indicator = g.indicator;
+    P.nvar = 4; P.nmom = 3; P.eq = HWENO_EULER; P.indicator = g.indicator; P.tvb_m = g.tvb_m;
     P.bc[0] = bcs[k].xlo; P.bc[1] = bcs[k].xhi; P.bc[2] = bcs[k].ylo; P.bc[3] = bcs[k].yhi;
     P.dx = (g.x1 - g.x0) / P.nx; P.dy = (g.y1 - g.y0) / P.ny;
     P.gamma = gamma; P.adv_a = 0.0; P.adv_b = 0.0; P.nsm = nsm; P.positivity = 1;

@@ -18,7 +18,7 @@ namespace hw {
 
 constexpr int EQ_ADV = 0, EQ_BURGERS = 1, EQ_EULER = 2;
 constexpr int BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2;
-constexpr int IND_NONE = 0, IND_KXRCF = 1, IND_ALL = 2, IND_MLP = 3;
+constexpr int IND_NONE = 0, IND_KXRCF = 1, IND_ALL = 2, IND_MLP = 3, IND_TVB = 4;
 
 // device status word bits
 constexpr unsigned ST_NONFINITE = 1u;     // a non-finite value in the new state
@@ -38,6 +38,7 @@ struct Prob {
   double gamma;           // ratio of specific heats
   double adv_a, adv_b;    // linear advection speeds
   int nsm;                // multiprocessors of the device (grid sizing)
+  double tvb_m;           // TVB constant M (indicator IND_TVB)
   int positivity;         // 1: rho <= 0 or p <= 0 averages are non-physical; 0: p is
                           //    clamped at 0 in the sound speed (only rho <= 0 / non-finite fail)
 };
@@ -477,6 +478,34 @@ __device__ __forceinline__ T kxrcf2d(const Prob& P, const Weights<T>& W, const T
   const T nrm = aux[4 * P.gplane + o];
   if (len == T(0) || nrm == T(0)) return T(0);
   return tabs(s) / len / (T(P.dx * P.dx) * nrm);   // h^{(l+1)/3}, l = 5, h = dx
+}
+
+// ---------------------------------------------------------------- TVB indicator
+// The minmod-based TVB indicator named in Remark 2 (Cockburn & Shu's TVB
+// limiter used as a troubled-cell indicator) on the indicator variable
+// (variable 0), acting on the cell's linear polynomial fixed by its moments:
+// its face deviations are +-6 vbar (x) and +-6 wbar (y).  The cell is troubled
+// when the modified minmod m(a, b, c) = a if |a| <= M h^2, else minmod(a, b, c)
+// changes a = 6 vbar (6 wbar) against the forward and backward differences of
+// the averages in that direction.  FP64: it reads only the FP64 state.
+__device__ __forceinline__ bool tvb_changes(double a, double b, double c, double bound) {
+  if (!(fabs(a) > bound)) return false;
+  double mm = 0.0;
+  if (a > 0.0 && b > 0.0 && c > 0.0) mm = fmin(a, fmin(b, c));
+  else if (a < 0.0 && b < 0.0 && c < 0.0) mm = fmax(a, fmax(b, c));
+  return mm != a;
+}
+
+__device__ __forceinline__ bool tvb_cell(const Prob& P, const double* __restrict__ U, int i, int j) {
+  const double bound = P.tvb_m * P.dx * P.dx;
+  const double u0 = U[sidx(P, 0, 0, i, j)];
+  const Img L = image(P, i - 1, j), R = image(P, i + 1, j);
+  const double ax = 6.0 * U[sidx(P, 0, 1, i, j)];
+  if (tvb_changes(ax, U[sidx(P, 0, 0, R.i, R.j)] - u0, u0 - U[sidx(P, 0, 0, L.i, L.j)], bound)) return true;
+  if (P.nmom == 2) return false;
+  const Img Bo = image(P, i, j - 1), Tp = image(P, i, j + 1);
+  const double ay = 6.0 * U[sidx(P, 0, 2, i, j)];
+  return tvb_changes(ay, U[sidx(P, 0, 0, Tp.i, Tp.j)] - u0, u0 - U[sidx(P, 0, 0, Bo.i, Bo.j)], bound);
 }
 
 }  // namespace hw

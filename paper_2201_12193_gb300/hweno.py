@@ -18,7 +18,7 @@ _lib = None
 
 STATUS = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "ENONPHYSICAL", -4: "ETIMEOUT", -5: "ESTATE", -6: "ENOMEM"}
 EQ = {"advection": 0, "burgers": 1, "euler": 2}
-IND = {"none": 0, "kxrcf": 1, "all": 2, "mlp": 3}
+IND = {"none": 0, "kxrcf": 1, "all": 2, "mlp": 3, "tvb": 4}
 BC = {"periodic": 0, "transmissive": 1, "reflective": 2}
 PREC = {"fp64": 0, "fp32": 1, "df64": 2}
 
@@ -34,7 +34,7 @@ class Grid(ctypes.Structure):
                 ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
                 ("eq", ctypes.c_int), ("adv_a", ctypes.c_double), ("adv_b", ctypes.c_double),
                 ("precision", ctypes.c_int), ("indicator", ctypes.c_int), ("gamma_bar", ctypes.c_double * 4),
-                ("beta_of_q", ctypes.c_int)]
+                ("beta_of_q", ctypes.c_int), ("tvb_m", ctypes.c_double)]
 
 
 class Bc(ctypes.Structure):
@@ -120,7 +120,7 @@ class Solver:
 
     def __init__(self, dim, nx, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, eq="euler", adv=(1.0, 0.0),
                  precision="fp64", indicator="kxrcf", gamma_bar=(1.0, 10.0, 100.0, 1000.0), beta_of_q=False,
-                 bc=("transmissive",) * 4, gamma=1.4, stream=None):
+                 bc=("transmissive",) * 4, gamma=1.4, stream=None, tvb_m=0.0):
         g = Grid()
         g.dim, g.nx, g.ny = dim, nx, (ny if dim == 2 else 1)
         g.x0, g.x1, g.y0, g.y1 = x0, x1, y0, y1
@@ -131,6 +131,7 @@ class Solver:
         for k in range(4):
             g.gamma_bar[k] = gamma_bar[k]
         g.beta_of_q = int(bool(beta_of_q))
+        g.tvb_m = float(tvb_m)
         b = Bc(*[BC[k] for k in bc])
         h = ctypes.c_void_p()
         st = lib().hweno_create(ctypes.byref(g), ctypes.byref(b), float(gamma), ctypes.byref(h))

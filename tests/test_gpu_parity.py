@@ -85,15 +85,16 @@ PROBS_2D = [
 
 
 @pytest.mark.parametrize("name,make", PROBS_1D + PROBS_2D, ids=[n for n, _ in PROBS_1D + PROBS_2D])
-@pytest.mark.parametrize("indicator", ["kxrcf", "none", "all"])
+@pytest.mark.parametrize("indicator", ["kxrcf", "none", "all", "tvb"])
 def test_rhs_parity(orc, name, make, indicator):
     """One evaluation of L with the troubled-cell steps on identical input."""
     p = make()
-    s = solver_of(p, indicator=indicator)
+    kw = {"tvb_m": 1.0} if indicator == "tvb" else {}
+    s = solver_of(p, indicator=indicator, **kw)
     for seed in (0, 1):
         U = p.m if seed == 0 else _perturbed(p, seed)
         Um_g, L_g, mask_g, aleph_g = gpu_rhs(s, U)
-        Um_o, L_o, mask_o, aleph_o, rc = orc.rhs(cfg_of(orc, p, indicator=indicator), U)
+        Um_o, L_o, mask_o, aleph_o, rc = orc.rhs(cfg_of(orc, p, indicator=indicator, **kw), U)
         assert rc == 0
         near = np.abs(aleph_o - 1.0) < 1e-10
         assert not near.any()

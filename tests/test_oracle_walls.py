@@ -146,3 +146,57 @@ def test_2d_operator_is_mirror_equivariant(orc):
             np.testing.assert_allclose(Lm, _mirror(L, axis), rtol=0, atol=1e-12 * np.abs(L).max())
             mk2 = mk.reshape(24, 24)
             assert np.array_equal(mkm.reshape(24, 24), mk2[:, ::-1] if axis == "x" else mk2[::-1, :])
+
+
+# ------------------------------------------------------------------ TVB indicator (Remark 2)
+# Reading: the TVB test acts on the cell's linear polynomial of its moments,
+# whose face deviation is a = 6 vbar; troubled when the modified minmod
+# (identity for |a| <= M h^2) changes a against the neighbour differences.
+
+def _euler_1d_lin(n, slope, vbar_scale=1.0):
+    """rho = 1 + slope x with its exact first moments (times vbar_scale)."""
+    x = (np.arange(n) + 0.5) / n
+    m = np.zeros((3, 2, 1, n))
+    rho = 1.0 + slope * x
+    m[:, 0, 0] = W.prim_to_cons_1d(rho, np.full(n, 0.3), np.ones(n))
+    m[0, 1, 0] = vbar_scale * slope / n / 12.0          # vbar of a linear function: slope dx / 12
+    return m
+
+
+def test_tvb_indicator_pins(orc):
+    n = 40
+    cfg = lambda M: orc.make_cfg(1, n, dx=1.0 / n, eq="euler", bc=("periodic",) * 4, indicator="tvb", tvb_m=M)
+    interior = slice(2, n - 2)
+    # consistent linear data: a = half the neighbour differences, same sign: not troubled
+    _, _, mk, _, rc = orc.rhs(cfg(0.0), _euler_1d_lin(n, 0.5))
+    assert rc == 0 and mk[interior].sum() == 0
+    # first moments three times too steep: a = 1.5 x the differences, changed by the minmod
+    _, _, mk, _, _ = orc.rhs(cfg(0.0), _euler_1d_lin(n, 0.5, 3.0))
+    assert mk[interior].all()
+    # ... unless M h^2 exceeds |a|
+    _, _, mk, _, _ = orc.rhs(cfg(1e6), _euler_1d_lin(n, 0.5, 3.0))
+    assert mk.sum() == 0
+    # a first moment against the trend of the averages: minmod 0
+    _, _, mk, _, _ = orc.rhs(cfg(0.0), _euler_1d_lin(n, 0.5, -1.0))
+    assert mk[interior].all()
+
+
+def test_tvb_indicator_2d_sees_both_directions(orc):
+    """The x first moment triggers it through x differences, the y first moment
+    through y differences."""
+    n = 16
+    x = (np.arange(n) + 0.5) / n
+    X, Y = np.meshgrid(x, x)
+    for axis, mom in (("x", 1), ("y", 2)):
+        rho = 1.0 + 0.5 * (X if axis == "x" else Y)
+        m = np.zeros((4, 3, n, n))
+        m[:, 0] = W.prim_to_cons_2d(rho, np.full_like(rho, 0.2), np.full_like(rho, 0.1), np.ones_like(rho))
+        c = orc.make_cfg(2, n, n, dx=1.0 / n, dy=1.0 / n, eq="euler", bc=("periodic",) * 4, indicator="tvb",
+                         tvb_m=0.0)
+        m[0, mom] = 0.5 / n / 12.0                        # consistent: not troubled
+        _, _, mk, _, rc = orc.rhs(c, m)
+        inner = mk.reshape(n, n)[2:-2, 2:-2]
+        assert rc == 0 and inner.sum() == 0
+        m[0, mom] *= 3.0                                  # too steep in that direction: troubled
+        _, _, mk, _, _ = orc.rhs(c, m)
+        assert mk.reshape(n, n)[2:-2, 2:-2].all()
