@@ -294,12 +294,12 @@ def run_batched(torch, hweno, args, world, rank):
     variant, tune_ms = autotune.tune_batch(probs, precision="fp32", steps=2)
     out = {}
     finals = {}
-    for prec in ("fp32", "fp64"):
+    for prec in ("fp32", "fp64", "df64"):
         s = hweno.BatchSolver(probs, precision=prec, stream=torch.cuda.current_stream())
         s.set_tile(variant)
         for k, p in enumerate(probs):
             s.set_moments(k, torch.from_numpy(p.m).cuda())
-        steps = args.steps if prec == "fp32" else max(2, args.steps // 3)
+        steps = args.steps if prec != "fp64" else max(2, args.steps // 3)
         for _ in range(args.warmup):
             s.step()
         s.sync()
@@ -324,9 +324,10 @@ def run_batched(torch, hweno, args, world, rank):
         out[f"batched_{prec}"] = {"value": aggregate(cells, 3, steps, world, ms), "ms_per_step": ms / steps,
                                   "problems": len(probs), "cells": cells, "graph": graph,
                                   "tile": autotune.VARIANTS[variant], "launches_per_step": 3}
-    num = sum(float(np.abs(a - b).sum()) for a, b in zip(finals["fp32"], finals["fp64"]))
     den = sum(float(np.abs(b).sum()) for b in finals["fp64"])
-    out["batched_fp32"]["rel_l1_vs_fp64_after_steps"] = num / den
+    for prec in ("fp32", "df64"):
+        num = sum(float(np.abs(a - b).sum()) for a, b in zip(finals[prec], finals["fp64"]))
+        out[f"batched_{prec}"]["rel_l1_vs_fp64_after_steps"] = num / den
     out["batched_fp32"]["tune_ms_per_step"] = {autotune.VARIANTS[int(k)]: v for k, v in tune_ms.items()}
     out["batched_fp32"]["rejected_seeds"] = rejected
     return out

@@ -74,7 +74,7 @@ typedef enum {
  *   differences of the face fluxes in the cell-average equation; 2 = the same
  *   split with double-float arithmetic (pairs of FP32 numbers, a 48-bit
  *   significand and FP32's exponent range; magnitudes below 2^-74 keep FP32
- *   precision) in place of FP32 (single-problem handles only).
+ *   precision) in place of FP32.
  *   indicator: HWENO_IND_KXRCF is the scheme (HWENO6-M5-I); NONE gives HWENO6
  *   (no modification); ALL gives HWENO6-M5-NI (every cell modified) (Sec. 3);
  *   MLP: the learned indicator with KXRCF fallback (see below; 2D Euler).

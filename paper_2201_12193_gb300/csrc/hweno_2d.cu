@@ -646,10 +646,15 @@ cudaError_t launch_batch(const Weights<T>& W, const Beta2<T>& Bt, const BatchSta
 cudaError_t run_batch_stage(const HostTabs& T, int fp32, int tile_variant, const BatchStage& S, int nsm,
                             cudaStream_t st) {
   // tile shapes of the update phase (all 128 threads): 0: 32x4, 1: 16x8, 2: 64x2
-  if (fp32) {
+  if (fp32 == PREC_FP32) {
     if (tile_variant == 1) return launch_batch<float, 16, 8>(T.wf, T.b2f, S, nsm, st);
     if (tile_variant == 2) return launch_batch<float, 64, 2>(T.wf, T.b2f, S, nsm, st);
     return launch_batch<float, 32, 4>(T.wf, T.b2f, S, nsm, st);
+  }
+  if (fp32 == PREC_DF64) {
+    if (tile_variant == 1) return launch_batch<df64, 16, 8>(T.wx, T.b2x, S, nsm, st);
+    if (tile_variant == 2) return launch_batch<df64, 64, 2>(T.wx, T.b2x, S, nsm, st);
+    return launch_batch<df64, 32, 4>(T.wx, T.b2x, S, nsm, st);
   }
   if (tile_variant == 1) return launch_batch<double, 16, 8>(T.wd, T.b2d, S, nsm, st);
   if (tile_variant == 2) return launch_batch<double, 64, 2>(T.wd, T.b2d, S, nsm, st);

@@ -732,9 +732,8 @@ hweno_status hweno_create_batch(const hweno_grid* grids, const hweno_bc* bcs, in
               "indicator and linear weights\n", k);
       return HWENO_EINVAL;
     }
-    if (g.indicator == HWENO_IND_MLP || g.precision == 2) {
-      fprintf(stderr, "hweno_create_batch: the learned indicator and the double-float precision run on "
-              "single-problem handles\n");
+    if (g.indicator == HWENO_IND_MLP) {
+      fprintf(stderr, "hweno_create_batch: the learned indicator runs on single-problem handles\n");
       return HWENO_EINVAL;
     }
   }

@@ -97,3 +97,26 @@ def test_autotuner_picks_a_variant(tmp_path, monkeypatch):
     assert best in (0, 1, 2) and len(times) == 3
     best2, _ = autotune.tune_batch(small_batch(), precision="fp32", steps=1)
     assert best2 == best and (tmp_path / "tune.json").exists()
+
+
+def test_batch_df64_meets_the_fp64_bar(orc):
+    """Double-float batches: bitwise the single-problem double-float path, and
+    within the FP64 parity bar (1e-12 relative L1) of the FP64 oracle."""
+    probs = small_batch()
+    got, dts, masks = run_batch(probs, 2, precision="df64")
+    for k, p in enumerate(probs):
+        s = hweno.Solver.from_problem(p, precision="df64")
+        s.set_moments(p.m)
+        for st in range(2):
+            assert s.max_dt(0.6) == dts[st][k]
+            s.step(dts[st][k])
+            np.testing.assert_array_equal(s.troubled_mask(), masks[st][k])
+        np.testing.assert_array_equal(s.get_moments(), got[k])
+        s.close()
+    for k, p in enumerate(probs[:3]):
+        cfg = orc.make_cfg(2, p.nx, p.ny, dx=p.dx, dy=p.dy, eq="euler", bc=p.bc)
+        m = p.m
+        for st in range(2):
+            m, _, rc = orc.step(cfg, m, dts[st][k])
+            assert rc == 0
+        assert rel_l1(got[k], m) <= 1e-12
