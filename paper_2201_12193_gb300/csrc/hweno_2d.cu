@@ -58,24 +58,43 @@ enum RecMode { REC_PLAIN = 0, REC_FLAGGED = 1, REC_MIXED = 2 };
 // Moment of kind 0 (average), 1 (x first moment) or 2 (y first moment) of
 // the stencil cell (ox, oy); when usemod, first moments of flagged stencil
 // cells come from the modified copy (eq. (vi) applied before Step 2.3).
-template <int MODE>
+template <int MODE, bool SIGNBIT>
 __device__ __forceinline__ double load_mom(const Prob& P, const double* __restrict__ U, const uint8_t* __restrict__ mask,
                                            const double* __restrict__ Mod, const Nbr& n, int var, int kind, int ox,
                                            int oy, bool usemod) {
   const int ci = n.xi[ox + 1], cj = n.yj[oy + 1];
   const long long so = (long long)cj * P.pitch + ci;
-  if (kind == 0) {
-    const double u = U[(long long)(var * 3) * P.plane + so];
-    return (n.neg[oy + 1][ox + 1] >> var) & 1 ? -u : u;
+  if constexpr (SIGNBIT) {
+    // FP64 / FP32 paths: the sign bit flipped by integer work (no FP64
+    // instruction; bitwise the same as negation), measured 6 % faster in FP64
+    unsigned long long flip = ((n.neg[oy + 1][ox + 1] >> var) & 1) ? 1ull : 0ull;
+    double v;
+    if (kind == 0) {
+      v = U[(long long)(var * 3) * P.plane + so];
+    } else {
+      if (MODE != REC_PLAIN && usemod && mask[(long long)cj * P.nx + ci] == 1)
+        v = Mod[(long long)(var * 2 + kind - 1) * P.plane + so];
+      else
+        v = U[(long long)(var * 3 + kind) * P.plane + so];
+      if (kind == 1 && n.xs[ox + 1] < 0) flip ^= 1ull;
+      if (kind == 2 && n.ys[oy + 1] < 0) flip ^= 1ull;
+    }
+    return __longlong_as_double(__double_as_longlong(v) ^ (long long)(flip << 63));
+  } else {
+    // double-float path: plain negation (fewer registers there, measured faster)
+    if (kind == 0) {
+      const double u = U[(long long)(var * 3) * P.plane + so];
+      return (n.neg[oy + 1][ox + 1] >> var) & 1 ? -u : u;
+    }
+    double v;
+    if (MODE != REC_PLAIN && usemod && mask[(long long)cj * P.nx + ci] == 1)
+      v = Mod[(long long)(var * 2 + kind - 1) * P.plane + so];
+    else
+      v = U[(long long)(var * 3 + kind) * P.plane + so];
+    if (kind == 1 && n.xs[ox + 1] < 0) v = -v;
+    if (kind == 2 && n.ys[oy + 1] < 0) v = -v;
+    return (n.neg[oy + 1][ox + 1] >> var) & 1 ? -v : v;
   }
-  double v;
-  if (MODE != REC_PLAIN && usemod && mask[(long long)cj * P.nx + ci] == 1)
-    v = Mod[(long long)(var * 2 + kind - 1) * P.plane + so];
-  else
-    v = U[(long long)(var * 3 + kind) * P.plane + so];
-  if (kind == 1 && n.xs[ox + 1] < 0) v = -v;
-  if (kind == 2 && n.ys[oy + 1] < 0) v = -v;
-  return (n.neg[oy + 1][ox + 1] >> var) & 1 ? -v : v;
 }
 
 template <typename T, int NV, int MODE>
@@ -96,7 +115,7 @@ __device__ __forceinline__ void rec2d_cell(const Prob& P, const Weights<T>& W, c
     for (int c = 0; c < 23; ++c) {
       int kind, ox, oy;
       d4_slot(c, kind, ox, oy);
-      d[c] = from_double<T>(load_mom<MODE>(P, U, mask, Mod, nb, v, kind, ox, oy, usemod));
+      d[c] = from_double<T>(load_mom<MODE, !is_df64<T>::value>(P, U, mask, Mod, nb, v, kind, ox, oy, usemod));
     }
     T out[16];
     recon2d<T>(W, B, d, out);
