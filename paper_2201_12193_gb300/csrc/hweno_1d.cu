@@ -16,6 +16,7 @@ namespace hw {
 namespace {
 
 constexpr int RB = 128;
+constexpr int UB = RB + 32;   // update threads: one per face (RB + 1) then one per cell (RB)
 
 __device__ __forceinline__ int mpt1(const Img& m, int k) { return m.sx < 0 ? 3 - k : k; }
 
@@ -30,56 +31,46 @@ __device__ __forceinline__ double load_mom1(const Prob& P, const double* __restr
   return m.sx < 0 ? -g * v : g * v;
 }
 
+// One thread per (cell, variable): the variables of a cell are independent in
+// Step 1, and the 1D problems are small, so spreading them over threads cuts
+// the latency of the pass (the KXRCF face velocities and norm are formed from
+// the point values in the indicator pass).
 template <typename T, int NV, bool FLAGGED>
 __global__ void __launch_bounds__(RB) rec1d_kernel(Prob P, Weights<T> W, Beta1<T> B, const double* __restrict__ U,
                                                   const uint8_t* __restrict__ mask, const double* __restrict__ Mod,
                                                   const int* __restrict__ list, const int* __restrict__ count,
-                                                  T* __restrict__ G, T* __restrict__ aux,
-                                                  unsigned long long* __restrict__ rerec) {
+                                                  T* __restrict__ G, unsigned long long* __restrict__ rerec) {
   const int n = FLAGGED ? *count : P.nx;
   if (FLAGGED && rerec && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(rerec, (unsigned long long)n);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
-    const int i = FLAGGED ? list[t] : t;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n * NV; t += gridDim.x * blockDim.x) {
+    const int v = t / n, e = t - v * n;
+    const int i = FLAGGED ? list[e] : e;
     const Img nb[3] = {image(P, i - 1, 0), image(P, i, 0), image(P, i + 1, 0)};
-    T vals0[4];
-    T pl = T(0), pr = T(0);
-#pragma unroll 1
-    for (int v = 0; v < NV; ++v) {
-      T d[6];
+    T d[6];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        d[c] = from_double<T>(load_mom1<FLAGGED>(P, U, mask, Mod, v, 0, nb[c]));
-        d[3 + c] = from_double<T>(load_mom1<FLAGGED>(P, U, mask, Mod, v, 1, nb[c]));
-      }
-      T out[4];
-      recon1d<T>(W, B, d, out);
-#pragma unroll
-      for (int p = 0; p < 4; ++p) G[(long long)(v * 4 + p) * P.gplane + i] = out[p];
-      if (!FLAGGED) {
-        if (v == 0) {
-#pragma unroll
-          for (int p = 0; p < 4; ++p) vals0[p] = out[p];
-          if (NV == 1) { pl = scalar_velocity(P, out[0], 0); pr = scalar_velocity(P, out[3], 0); }
-        } else if (v == 1) {
-          pl = out[0] / vals0[0];
-          pr = out[3] / vals0[3];
-        }
-      }
+    for (int c = 0; c < 3; ++c) {
+      d[c] = from_double<T>(load_mom1<FLAGGED>(P, U, mask, Mod, v, 0, nb[c]));
+      d[3 + c] = from_double<T>(load_mom1<FLAGGED>(P, U, mask, Mod, v, 1, nb[c]));
     }
-    if (!FLAGGED) {
-      T nrm = T(0);
+    T out[4];
+    recon1d<T>(W, B, d, out);
 #pragma unroll
-      for (int p = 0; p < 4; ++p) nrm = tmax(nrm, tabs(vals0[p]));
-      aux[0 * P.gplane + i] = pl;
-      aux[1 * P.gplane + i] = pr;
-      aux[2 * P.gplane + i] = nrm;
-    }
+    for (int p = 0; p < 4; ++p) G[(long long)(v * 4 + p) * P.gplane + i] = out[p];
   }
+}
+
+// KXRCF face velocity of a cell at its left (side 0) or right (side 1) face,
+// from its own point values: u at the face (scalars, f'(u)) or (rho u)/rho (Euler).
+template <typename T, int NV>
+__device__ __forceinline__ T face_vel1(const Prob& P, const T* __restrict__ G, int c, int side) {
+  const int p = side ? 3 : 0;
+  if constexpr (NV == 1) return scalar_velocity(P, G[(long long)p * P.gplane + c], 0);
+  else return G[(long long)(4 + p) * P.gplane + c] / G[(long long)p * P.gplane + c];
 }
 
 template <typename T, int NV>
 __global__ void __launch_bounds__(RB) flag1d_kernel(Prob P, Weights<T> W, const double* __restrict__ U,
-                                                   const T* __restrict__ G, const T* __restrict__ aux,
+                                                   const T* __restrict__ G,
                                                    uint8_t* __restrict__ mask, double* __restrict__ Mod,
                                                    int* __restrict__ list, int* __restrict__ count,
                                                    double* __restrict__ aleph) {
@@ -96,13 +87,15 @@ __global__ void __launch_bounds__(RB) flag1d_kernel(Prob P, Weights<T> W, const 
       flag = tvb_cell(P, U, i, 0);
     } else if (P.indicator == IND_KXRCF) {
       // face velocities: average of both sides' velocities at the face
-      const T al = aux[(L.sx < 0 ? 0 : 1) * P.gplane + L.i], ar = aux[(R.sx < 0 ? 1 : 0) * P.gplane + R.i];
-      const T vl = T(0.5) * ((L.neg & 2 ? -al : al) + aux[0 * P.gplane + i]);
-      const T vr = T(0.5) * (aux[1 * P.gplane + i] + (R.neg & 2 ? -ar : ar));
+      const T al = face_vel1<T, NV>(P, G, L.i, L.sx < 0 ? 0 : 1), ar = face_vel1<T, NV>(P, G, R.i, R.sx < 0 ? 1 : 0);
+      const T vl = T(0.5) * ((L.neg & 2 ? -al : al) + face_vel1<T, NV>(P, G, i, 0));
+      const T vr = T(0.5) * (face_vel1<T, NV>(P, G, i, 1) + (R.neg & 2 ? -ar : ar));
       const T jl = G[0 * P.gplane + i] - G[(long long)mpt1(L, 3) * P.gplane + L.i];
       const T jr = G[3 * P.gplane + i] - G[(long long)mpt1(R, 0) * P.gplane + R.i];
       const T s = jl * (vl > T(KX_VDEAD) ? T(1) : T(0)) + jr * (-vr > T(KX_VDEAD) ? T(1) : T(0));
-      const T nrm = aux[2 * P.gplane + i];
+      T nrm = T(0);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) nrm = tmax(nrm, tabs(G[(long long)p * P.gplane + i]));
       const T a = nrm == T(0) ? T(0) : tabs(s) / (T(P.dx * P.dx) * nrm);   // h^{(l+1)/3}, l = 5
       if (aleph) aleph[i] = double(a);
       flag = a > T(1);
@@ -149,12 +142,12 @@ __device__ __forceinline__ void gl1(const Prob& P, const T* __restrict__ G, cons
 }
 
 template <typename T, int NV>
-__global__ void __launch_bounds__(RB) update1d_kernel(Prob P, const T* __restrict__ G, Rk1 S) {
+__global__ void __launch_bounds__(UB) update1d_kernel(Prob P, const T* __restrict__ G, Rk1 S) {
   __shared__ T fx[RB + 1][NV];
   const int t = threadIdx.x;
   const int i0 = blockIdx.x * RB;
   const int i = i0 + t;
-  const bool live = i < P.nx;
+  const bool live = t < RB && i < P.nx;
   if (S.dtp) {
     S.dt = *S.dtp;
     if (S.dt < 0.0) {   // a skipped step (block-uniform): the state passes through unchanged
@@ -166,7 +159,7 @@ __global__ void __launch_bounds__(RB) update1d_kernel(Prob P, const T* __restric
   const Img self{i, 0, 1, 1};
   // fx[c] is the face left of cell i0 + c; one call site computes every face so
   // that faces shared by two blocks get bitwise the same flux.
-  for (int c = t; c <= RB; c += RB) {
+  for (int c = t; c <= RB; c += UB) {     // UB > RB: at most one face per thread
     const int il = i0 + c - 1;
     if (il >= P.nx) continue;
     T uL[NV], uR[NV];
@@ -179,13 +172,29 @@ __global__ void __launch_bounds__(RB) update1d_kernel(Prob P, const T* __restric
   T F[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) F[v] = T(0);
+  if constexpr (NV == 3 && one_division<T>::value) {
+    // Euler, FP64: the four reciprocal densities with one division
+    T rho[4], inv[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {     // eq. (F)
-    T u[NV], f[NV];
-    gl1<T, NV>(P, G, self, k, u);
-    phys_flux<T, NV>(P, u, 0, f);
+    for (int k = 0; k < 4; ++k) rho[k] = G[(long long)k * P.gplane + i];
+    batch_inverse<4, T>(rho, inv);
 #pragma unroll
-    for (int v = 0; v < NV; ++v) F[v] += gl_w<T>(k) * f[v];
+    for (int k = 0; k < 4; ++k) {     // eq. (F)
+      T u[NV], f[NV];
+      gl1<T, NV>(P, G, self, k, u);
+      euler_flux_inv<T, NV>(P, u, inv[k], 0, f);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) F[v] += gl_w<T>(k) * f[v];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {     // eq. (F)
+      T u[NV], f[NV];
+      gl1<T, NV>(P, G, self, k, u);
+      phys_flux<T, NV>(P, u, 0, f);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) F[v] += gl_w<T>(k) * f[v];
+    }
   }
   const double idx = 1.0 / P.dx;
   const T tidx = T(idx);
@@ -225,24 +234,23 @@ template <typename T, int NV>
 void stage_t(const Prob& P, const Weights<T>& W, const Beta1<T>& Bt, const Bufs& B, const StageCall& S, cudaStream_t st) {
   int* cnt = B.count + S.stage;
   cudaMemsetAsync(cnt, 0, sizeof(int), st);
-  const int blocks = (P.nx + RB - 1) / RB;
+  const int blocks = (P.nx + RB - 1) / RB, rblocks = (P.nx * NV + RB - 1) / RB;
   if (B.prof) B.prof->begin(0, st);
-  rec1d_kernel<T, NV, false><<<blocks, RB, 0, st>>>(P, W, Bt, S.Uin, nullptr, nullptr, nullptr, nullptr, (T*)B.G,
-                                                    (T*)B.aux, nullptr);
+  rec1d_kernel<T, NV, false><<<rblocks, RB, 0, st>>>(P, W, Bt, S.Uin, nullptr, nullptr, nullptr, nullptr, (T*)B.G,
+                                                     nullptr);
   if (B.prof) B.prof->end(st);
   if (B.prof) B.prof->begin(1, st);
-  flag1d_kernel<T, NV><<<blocks, RB, 0, st>>>(P, W, S.Uin, (const T*)B.G, (const T*)B.aux, S.mask, S.Mod, B.list, cnt,
+  flag1d_kernel<T, NV><<<blocks, RB, 0, st>>>(P, W, S.Uin, (const T*)B.G, S.mask, S.Mod, B.list, cnt,
                                               S.aleph);
   if (B.prof) B.prof->end(st);
   if (P.indicator != IND_NONE) {
     if (B.prof) B.prof->begin(2, st);
-    rec1d_kernel<T, NV, true><<<blocks, RB, 0, st>>>(P, W, Bt, S.Uin, S.mask, S.Mod, B.list, cnt, (T*)B.G, nullptr,
-                                                   B.rerec);
+    rec1d_kernel<T, NV, true><<<rblocks, RB, 0, st>>>(P, W, Bt, S.Uin, S.mask, S.Mod, B.list, cnt, (T*)B.G, B.rerec);
     if (B.prof) B.prof->end(st);
   }
   Rk1 r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status, S.dtp};
   if (B.prof) B.prof->begin(3, st);
-  update1d_kernel<T, NV><<<blocks, RB, 0, st>>>(P, (const T*)B.G, r);
+  update1d_kernel<T, NV><<<blocks, UB, 0, st>>>(P, (const T*)B.G, r);
   if (B.prof) B.prof->end(st);
 }
 
