@@ -405,3 +405,70 @@ def test_blast_wave_run_conserves_mass_and_energy():
     m = s.get_moments()
     assert np.isfinite(m).all() and (m[0, 0] > 0).all()
     s.close()
+
+
+# ------------------------------------------------------------------ full-size forms of the bench
+
+@pytest.mark.parametrize("precision,tol", [("df64", TOL), ("fp32", 5e-6)])
+def test_full_size_forms_sampled(orc, precision, tol):
+    """The double-float and FP32-bulk forms at the benchmark's 2048^2 size and
+    launch configuration: one step, sampled cells against oracle windows (the
+    double-float form at the FP64 bar, FP32 bulk at its stated tolerance)."""
+    p = W.four_quadrant_2d(2048, seed=0)
+    s = solver_of(p, precision=precision)
+    s.set_moments(torch.from_numpy(p.m).cuda())
+    dt = s.max_dt(0.6)
+    s.step(dt)
+    got = s.get_moments()
+    rng = np.random.default_rng(1)
+    picks = [(1024, 1024), (1023, 1023), (0, 0), (2047, 0), (1024, 2047)]
+    picks += [(int(a), int(b)) for a in rng.integers(1000, 1048, 4) for b in rng.integers(0, 2048, 1)]
+    for ci, cj in picks:
+        want = _window_oracle(orc, p, p.m, ci, cj, 14, dt, 1)
+        g = got[:, :, cj, ci]
+        assert np.abs(g - want).sum() <= tol * np.abs(want).sum(), (ci, cj, g, want)
+    s.close()
+
+
+def test_full_size_learned_indicator_sampled(orc):
+    """The learned-indicator form at its 4096^2 blast size: one evaluation of L
+    with the shipped network, sampled cells against the oracle's given-decision
+    mode on windows, the decisions taken from the kernel's own probabilities."""
+    from paper_2201_12193_gb300 import learn
+    p = W.blast_2d(4096, seed=0, ncircles=8)
+    conf = 0.9
+    s = solver_of(p, indicator="mlp")
+    s.set_mlp(learn.load_params(), conf)
+    prob = torch.empty(p.nx * p.ny, dtype=torch.float32, device="cuda")
+    s.mlp_probe(prob)
+    Ud = torch.from_numpy(p.m).cuda()
+    Um, L = torch.empty_like(Ud), torch.empty_like(Ud)
+    mask = torch.empty((p.ny, p.nx), dtype=torch.uint8, device="cuda")
+    s.rhs(Ud, Um, L, mask)
+    torch.cuda.synchronize()
+    pr = prob.cpu().numpy().reshape(p.ny, p.nx).astype(np.float32)
+    dec = np.where(np.maximum(pr, np.float32(1) - pr) >= np.float32(conf), (pr > np.float32(0.5)).astype(np.uint8),
+                   np.uint8(2))
+    Lh = L.cpu().numpy()
+    mk = mask.cpu().numpy()
+    # cells on circle edges (where the indicators act), plus the domain corners
+    edge = np.argwhere(np.abs(np.diff(p.m[3, 0], axis=1)) > 1.0)
+    rng = np.random.default_rng(2)
+    picks = [(int(e[1]), int(e[0])) for e in edge[rng.choice(len(edge), 6, replace=False)]] + [(0, 0), (4095, 4095)]
+    half = 12
+    for ci, cj in picks:
+        i0, i1 = max(0, ci - half), min(p.nx, ci + half)
+        j0, j1 = max(0, cj - half), min(p.ny, cj + half)
+        sub = np.ascontiguousarray(p.m[:, :, j0:j1, i0:i1])
+        bc = [p.bc[0] if i0 == 0 else "transmissive", p.bc[1] if i1 == p.nx else "transmissive",
+              p.bc[2] if j0 == 0 else "transmissive", p.bc[3] if j1 == p.ny else "transmissive"]
+        cfg = orc.make_cfg(2, i1 - i0, j1 - j0, dx=p.dx, dy=p.dy, eq="euler", gamma=p.gamma, bc=bc, indicator="given")
+        _, Lo, mo, _, rc = orc.rhs(cfg, sub, decisions=np.ascontiguousarray(dec[j0:j1, i0:i1]))
+        assert rc == 0
+        want = Lo.reshape(4, 3, j1 - j0, i1 - i0)[:, :, cj - j0, ci - i0]
+        g = Lh[:, :, cj, ci]
+        assert mo.reshape(j1 - j0, i1 - i0)[cj - j0, ci - i0] == mk[cj, ci]
+        # the bar of test_rhs_parity, with the window's magnitude as the scale
+        # (a cell's L can nearly cancel between large fluxes)
+        assert np.abs(g - want).sum() <= 12 * (1e-11 * np.abs(Lo).max() + 1e-9), (ci, cj, g, want)
+    s.close()
