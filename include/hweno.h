@@ -88,7 +88,13 @@ typedef enum {
  *   uses {1, 10, 100, 1000}.
  *   beta_of_q: 0 = smoothness indicators of p_l as eq. (beta) states (default);
  *   1 = of q_l (the variant for which Remark 1's expansion holds for every l).
- *   tvb_m: the TVB constant M (>= 0) of indicator TVB; ignored otherwise. */
+ *   tvb_m: the TVB constant M (>= 0) of indicator TVB; ignored otherwise.
+ *   charwise: 0 = reconstruct the conserved variables component by component
+ *   (default); 1 = (1D Euler only) reconstruct in local characteristic
+ *   variables: the stencil's moments projected on the eigenvectors of the flux
+ *   Jacobian at the target cell's average, each field reconstructed by the
+ *   scalar procedure, the point values mapped back.  The paper does not say
+ *   which; its blast-wave example needs the characteristic form here. */
 typedef struct {
   int dim;
   int nx, ny;
@@ -100,6 +106,7 @@ typedef struct {
   double gamma_bar[4];
   int beta_of_q;
   double tvb_m;
+  int charwise;
 } hweno_grid;
 
 /* Boundary kinds of the four sides.  Periodic sides must come in pairs.

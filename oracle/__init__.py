@@ -44,11 +44,12 @@ class Cfg(ctypes.Structure):
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("eq", ctypes.c_int),
                 ("adv_a", ctypes.c_double), ("adv_b", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("indicator", ctypes.c_int), ("gbar", ctypes.c_double * 4), ("bc", ctypes.c_int * 4),
-                ("tvb_m", ctypes.c_double)]
+                ("tvb_m", ctypes.c_double), ("charwise", ctypes.c_int)]
 
 
 def make_cfg(dim, nx, ny=1, dx=1.0, dy=1.0, eq="euler", adv=(1.0, 0.0), gamma=1.4,
-             indicator="kxrcf", gbar=(1.0, 10.0, 100.0, 1000.0), bc=("periodic",) * 4, tvb_m=0.0) -> Cfg:
+             indicator="kxrcf", gbar=(1.0, 10.0, 100.0, 1000.0), bc=("periodic",) * 4, tvb_m=0.0,
+             charwise=False) -> Cfg:
     c = Cfg()
     c.dim, c.nx, c.ny = dim, nx, (ny if dim == 2 else 1)
     c.dx, c.dy = dx, (dy if dim == 2 else 1.0)
@@ -57,6 +58,7 @@ def make_cfg(dim, nx, ny=1, dx=1.0, dy=1.0, eq="euler", adv=(1.0, 0.0), gamma=1.
     c.gamma = gamma
     c.indicator = IND[indicator] if isinstance(indicator, str) else int(indicator)
     c.tvb_m = tvb_m
+    c.charwise = int(bool(charwise))
     for k in range(4):
         c.gbar[k] = gbar[k]
         b = bc[k]

@@ -55,6 +55,7 @@ typedef struct {
   double gbar[4];   /* positive linear-weight seeds, eq. (linear-weight) */
   int bc[4];        /* x-lo, x-hi, y-lo, y-hi: 0 periodic, 1 transmissive, 2 reflective (Euler) */
   double tvb_m;     /* TVB constant M of indicator 4 */
+  int charwise;     /* 1D Euler: reconstruct in local characteristic variables */
 } orc_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -614,12 +615,53 @@ static void gather_stencil(const orc_cfg *c, const double *m, int var, int i, in
     }
 }
 
+/* 1D Euler eigenvectors of the flux Jacobian at state (rho, rho u, E):
+ * right R (columns) and left L (rows), L R = I (Toro, Riemann Solvers, 3.1).
+ * Reading (charwise = 1): the paper reconstructs conserved variables without
+ * saying how; the usual alternative for systems is to project the
+ * stencil's moments on the characteristic fields of the target cell's average
+ * state, reconstruct each field with the scalar procedure (its own smoothness
+ * indicators and weights), and map the point values back.  Moments are linear
+ * functionals, so the projection applies to averages and first moments alike. */
+static void euler1d_eig(double gam, const double *u, double R[3][3], double Lm[3][3]) {
+  double rho = u[0], mu = u[1] / rho, p = (gam - 1.0) * (u[2] - 0.5 * rho * mu * mu);
+  double cs = sqrt(gam * p / rho), H = (u[2] + p) / rho;
+  double b1 = (gam - 1.0) / (cs * cs), b2 = 0.5 * b1 * mu * mu;
+  double Rt[3][3] = {{1.0, 1.0, 1.0}, {mu - cs, mu, mu + cs}, {H - mu * cs, 0.5 * mu * mu, H + mu * cs}};
+  double Lt[3][3] = {{0.5 * (b2 + mu / cs), -0.5 * (b1 * mu + 1.0 / cs), 0.5 * b1},
+                     {1.0 - b2, b1 * mu, -b1},
+                     {0.5 * (b2 - mu / cs), -0.5 * (b1 * mu - 1.0 / cs), 0.5 * b1}};
+  memcpy(R, Rt, sizeof Rt);
+  memcpy(Lm, Lt, sizeof Lt);
+}
+
 static void reconstruct_all(const orc_cfg *c, const double *m, double *G, const unsigned char *only) {
   int nv = nvars(c), ny = c->dim == 1 ? 1 : c->ny;
   for (int j = 0; j < ny; ++j)
     for (int i = 0; i < c->nx; ++i) {
       size_t cell = (size_t)j * c->nx + i;
       if (only && !only[cell]) continue;
+      if (c->charwise && c->dim == 1 && c->eq == 2) {
+        double R[3][3], Lm[3][3], u0[3];
+        for (int v = 0; v < 3; ++v) u0[v] = mom_at(c, m, v, 0, i, 0);
+        euler1d_eig(c->gamma, u0, R, Lm);
+        stencil_t sv[3];
+        for (int v = 0; v < 3; ++v) gather_stencil(c, m, v, i, j, &sv[v]);
+        double w[3][4];
+        for (int f = 0; f < 3; ++f) {
+          stencil_t st;
+          for (int o = 0; o < 3; ++o) {
+            st.ub[o] = Lm[f][0] * sv[0].ub[o] + Lm[f][1] * sv[1].ub[o] + Lm[f][2] * sv[2].ub[o];
+            st.vb[o] = Lm[f][0] * sv[0].vb[o] + Lm[f][1] * sv[1].vb[o] + Lm[f][2] * sv[2].vb[o];
+          }
+          recon_out ro;
+          recon_cell(c->dim, c->dx, c->dy, c->gbar, &st, &ro);
+          for (int q = 0; q < 4; ++q) w[f][q] = ro.vals[q];
+        }
+        for (int v = 0; v < 3; ++v)
+          for (int q = 0; q < 4; ++q) G[(cell * nv + v) * 16 + q] = R[v][0] * w[0][q] + R[v][1] * w[1][q] + R[v][2] * w[2][q];
+        continue;
+      }
       for (int v = 0; v < nv; ++v) {
         stencil_t st; recon_out ro;
         gather_stencil(c, m, v, i, j, &st);

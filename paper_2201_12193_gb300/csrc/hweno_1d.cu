@@ -59,6 +59,66 @@ __global__ void __launch_bounds__(RB) rec1d_kernel(Prob P, Weights<T> W, Beta1<T
   }
 }
 
+// Eigenvectors of the 1D Euler flux Jacobian at the state (rho, rho u, E):
+// right R (columns: u - c, u, u + c) and left L (rows), L R = I (Toro, Riemann
+// Solvers and Numerical Methods for Fluid Dynamics, Sec. 3.1).
+__device__ __forceinline__ void euler1d_eigvec(double gam, double r, double m, double E, double (&R)[3][3],
+                                               double (&L)[3][3]) {
+  const double mu = m / r, p = (gam - 1.0) * (E - 0.5 * r * mu * mu);
+  const double cs = sqrt(gam * p / r), H = (E + p) / r;
+  const double b1 = (gam - 1.0) / (cs * cs), b2 = 0.5 * b1 * mu * mu;
+  R[0][0] = 1.0; R[0][1] = 1.0; R[0][2] = 1.0;
+  R[1][0] = mu - cs; R[1][1] = mu; R[1][2] = mu + cs;
+  R[2][0] = H - mu * cs; R[2][1] = 0.5 * mu * mu; R[2][2] = H + mu * cs;
+  L[0][0] = 0.5 * (b2 + mu / cs); L[0][1] = -0.5 * (b1 * mu + 1.0 / cs); L[0][2] = 0.5 * b1;
+  L[1][0] = 1.0 - b2; L[1][1] = b1 * mu; L[1][2] = -b1;
+  L[2][0] = 0.5 * (b2 - mu / cs); L[2][1] = -0.5 * (b1 * mu - 1.0 / cs); L[2][2] = 0.5 * b1;
+}
+
+// Step 1 (and 2.3 when FLAGGED) in local characteristic variables (1D Euler,
+// Prob::charwise): the moments of the 3-cell stencil are projected on the
+// characteristic fields of the target cell's average state, each field is
+// reconstructed by the scalar procedure (its own smoothness indicators and
+// weights), and the point values are mapped back.  One thread per cell.
+template <typename T, bool FLAGGED>
+__global__ void __launch_bounds__(RB) rec1d_char_kernel(Prob P, Weights<T> W, Beta1<T> B,
+                                                       const double* __restrict__ U, const uint8_t* __restrict__ mask,
+                                                       const double* __restrict__ Mod, const int* __restrict__ list,
+                                                       const int* __restrict__ count, T* __restrict__ G,
+                                                       unsigned long long* __restrict__ rerec) {
+  const int n = FLAGGED ? *count : P.nx;
+  if (FLAGGED && rerec && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(rerec, (unsigned long long)n);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int i = FLAGGED ? list[t] : t;
+    const Img nb[3] = {image(P, i - 1, 0), image(P, i, 0), image(P, i + 1, 0)};
+    double Rd[3][3], Ld[3][3];
+    euler1d_eigvec(P.gamma, U[sidx(P, 0, 0, i, 0)], U[sidx(P, 1, 0, i, 0)], U[sidx(P, 2, 0, i, 0)], Rd, Ld);
+    T dv[3][6];
+#pragma unroll
+    for (int v = 0; v < 3; ++v)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        dv[v][c] = from_double<T>(load_mom1<FLAGGED>(P, U, mask, Mod, v, 0, nb[c]));
+        dv[v][3 + c] = from_double<T>(load_mom1<FLAGGED>(P, U, mask, Mod, v, 1, nb[c]));
+      }
+    T w[3][4];
+#pragma unroll 1
+    for (int f = 0; f < 3; ++f) {
+      const T l0 = from_double<T>(Ld[f][0]), l1 = from_double<T>(Ld[f][1]), l2 = from_double<T>(Ld[f][2]);
+      T d[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) d[q] = l0 * dv[0][q] + l1 * dv[1][q] + l2 * dv[2][q];
+      recon1d<T>(W, B, d, w[f]);
+    }
+#pragma unroll
+    for (int v = 0; v < 3; ++v) {
+      const T r0 = from_double<T>(Rd[v][0]), r1 = from_double<T>(Rd[v][1]), r2 = from_double<T>(Rd[v][2]);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) G[(long long)(v * 4 + p) * P.gplane + i] = r0 * w[0][p] + r1 * w[1][p] + r2 * w[2][p];
+    }
+  }
+}
+
 // KXRCF face velocity of a cell at its left (side 0) or right (side 1) face,
 // from its own point values: u at the face (scalars, f'(u)) or (rho u)/rho (Euler).
 template <typename T, int NV>
@@ -235,9 +295,15 @@ void stage_t(const Prob& P, const Weights<T>& W, const Beta1<T>& Bt, const Bufs&
   int* cnt = B.count + S.stage;
   cudaMemsetAsync(cnt, 0, sizeof(int), st);
   const int blocks = (P.nx + RB - 1) / RB, rblocks = (P.nx * NV + RB - 1) / RB;
+  bool charwise = false;
+  if constexpr (NV == 3) charwise = P.charwise != 0;
   if (B.prof) B.prof->begin(0, st);
-  rec1d_kernel<T, NV, false><<<rblocks, RB, 0, st>>>(P, W, Bt, S.Uin, nullptr, nullptr, nullptr, nullptr, (T*)B.G,
-                                                     nullptr);
+  if (charwise)
+    rec1d_char_kernel<T, false><<<blocks, RB, 0, st>>>(P, W, Bt, S.Uin, nullptr, nullptr, nullptr, nullptr, (T*)B.G,
+                                                       nullptr);
+  else
+    rec1d_kernel<T, NV, false><<<rblocks, RB, 0, st>>>(P, W, Bt, S.Uin, nullptr, nullptr, nullptr, nullptr, (T*)B.G,
+                                                       nullptr);
   if (B.prof) B.prof->end(st);
   if (B.prof) B.prof->begin(1, st);
   flag1d_kernel<T, NV><<<blocks, RB, 0, st>>>(P, W, S.Uin, (const T*)B.G, S.mask, S.Mod, B.list, cnt,
@@ -245,7 +311,10 @@ void stage_t(const Prob& P, const Weights<T>& W, const Beta1<T>& Bt, const Bufs&
   if (B.prof) B.prof->end(st);
   if (P.indicator != IND_NONE) {
     if (B.prof) B.prof->begin(2, st);
-    rec1d_kernel<T, NV, true><<<rblocks, RB, 0, st>>>(P, W, Bt, S.Uin, S.mask, S.Mod, B.list, cnt, (T*)B.G, B.rerec);
+    if (charwise)
+      rec1d_char_kernel<T, true><<<blocks, RB, 0, st>>>(P, W, Bt, S.Uin, S.mask, S.Mod, B.list, cnt, (T*)B.G, B.rerec);
+    else
+      rec1d_kernel<T, NV, true><<<rblocks, RB, 0, st>>>(P, W, Bt, S.Uin, S.mask, S.Mod, B.list, cnt, (T*)B.G, B.rerec);
     if (B.prof) B.prof->end(st);
   }
   Rk1 r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status, S.dtp};

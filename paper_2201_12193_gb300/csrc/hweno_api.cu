@@ -149,6 +149,9 @@ hweno_status validate(const hweno_grid* g, const hweno_bc* bc, double gamma, std
   }
   if (g->indicator < 0 || g->indicator > 4) { why = "indicator must be none, kxrcf, all, mlp or tvb"; return HWENO_EINVAL; }
   if (g->indicator == 4 && !(g->tvb_m >= 0.0 && isfinite(g->tvb_m))) { why = "tvb_m must be finite and >= 0"; return HWENO_EINVAL; }
+  if (g->charwise != 0 && (g->dim != 1 || g->eq != HWENO_EULER)) {
+    why = "characteristic reconstruction (charwise) is defined for 1D Euler"; return HWENO_EINVAL;
+  }
   if (g->indicator == 3 && (g->dim != 2 || g->eq != HWENO_EULER)) {
     why = "the learned indicator is defined for 2D Euler"; return HWENO_EINVAL;
   }
@@ -274,6 +277,7 @@ hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gam
   P.eq = h->g.eq;
   P.indicator = h->g.indicator;
   P.tvb_m = h->g.tvb_m;
+  P.charwise = h->g.charwise;
   P.bc[0] = bc->xlo; P.bc[1] = bc->xhi;
   P.bc[2] = h->g.dim == 2 ? bc->ylo : HWENO_BC_PERIODIC;
   P.bc[3] = h->g.dim == 2 ? bc->yhi : HWENO_BC_PERIODIC;

@@ -39,6 +39,7 @@ struct Prob {
   double adv_a, adv_b;    // linear advection speeds
   int nsm;                // multiprocessors of the device (grid sizing)
   double tvb_m;           // TVB constant M (indicator IND_TVB)
+  int charwise;           // 1D Euler: reconstruction in local characteristic variables
   int positivity;         // 1: rho <= 0 or p <= 0 averages are non-physical; 0: p is
                           //    clamped at 0 in the sound speed (only rho <= 0 / non-finite fail)
 };

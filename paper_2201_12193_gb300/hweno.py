@@ -34,7 +34,7 @@ class Grid(ctypes.Structure):
                 ("x0", ctypes.c_double), ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double),
                 ("eq", ctypes.c_int), ("adv_a", ctypes.c_double), ("adv_b", ctypes.c_double),
                 ("precision", ctypes.c_int), ("indicator", ctypes.c_int), ("gamma_bar", ctypes.c_double * 4),
-                ("beta_of_q", ctypes.c_int), ("tvb_m", ctypes.c_double)]
+                ("beta_of_q", ctypes.c_int), ("tvb_m", ctypes.c_double), ("charwise", ctypes.c_int)]
 
 
 class Bc(ctypes.Structure):
@@ -120,7 +120,7 @@ class Solver:
 
     def __init__(self, dim, nx, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, eq="euler", adv=(1.0, 0.0),
                  precision="fp64", indicator="kxrcf", gamma_bar=(1.0, 10.0, 100.0, 1000.0), beta_of_q=False,
-                 bc=("transmissive",) * 4, gamma=1.4, stream=None, tvb_m=0.0):
+                 bc=("transmissive",) * 4, gamma=1.4, stream=None, tvb_m=0.0, charwise=False):
         g = Grid()
         g.dim, g.nx, g.ny = dim, nx, (ny if dim == 2 else 1)
         g.x0, g.x1, g.y0, g.y1 = x0, x1, y0, y1
@@ -132,6 +132,7 @@ class Solver:
             g.gamma_bar[k] = gamma_bar[k]
         g.beta_of_q = int(bool(beta_of_q))
         g.tvb_m = float(tvb_m)
+        g.charwise = int(bool(charwise))
         b = Bc(*[BC[k] for k in bc])
         h = ctypes.c_void_p()
         st = lib().hweno_create(ctypes.byref(g), ctypes.byref(b), float(gamma), ctypes.byref(h))

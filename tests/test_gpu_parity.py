@@ -472,3 +472,88 @@ def test_full_size_learned_indicator_sampled(orc):
         # (a cell's L can nearly cancel between large fluxes)
         assert np.abs(g - want).sum() <= 12 * (1e-11 * np.abs(Lo).max() + 1e-9), (ci, cj, g, want)
     s.close()
+
+
+# ------------------------------------------------------------------ characteristic-wise reconstruction (1D Euler)
+
+EULER_1D = [(n, mk) for n, mk in PROBS_1D if n in ("shu_osher", "lax", "sod_ragged", "blast_wave_walls")]
+
+
+@pytest.mark.parametrize("name,make", EULER_1D, ids=[n for n, _ in EULER_1D])
+@pytest.mark.parametrize("indicator", ["kxrcf", "all"])
+@pytest.mark.parametrize("precision", ["fp64", "df64"])
+def test_charwise_rhs_parity(orc, name, make, indicator, precision):
+    """L, the modified moments and the masks with the reconstruction in local
+    characteristic variables, FP64 and double-float, against the oracle."""
+    p = make()
+    s = solver_of(p, indicator=indicator, charwise=True, precision=precision)
+    cfg = cfg_of(orc, p, indicator=indicator, charwise=True)
+    for seed in (0, 1):
+        U = p.m if seed == 0 else _perturbed(p, seed)
+        Um_g, L_g, mask_g, _ = gpu_rhs(s, U)
+        Um_o, L_o, mask_o, aleph_o, rc = orc.rhs(cfg, U)
+        assert rc == 0 and not (np.abs(aleph_o - 1.0) < 1e-10).any()
+        assert np.array_equal(mask_g, mask_o), (int(mask_g.sum()), int(mask_o.sum()))
+        assert rel_l1(Um_g, Um_o) <= TOL
+        assert np.abs(L_g - L_o).sum() <= 1e-11 * np.abs(L_o).sum() + 1e-9 * L_o.size, rel_l1(L_g, L_o)
+    s.close()
+
+
+def test_charwise_fp32_within_tolerance(orc):
+    p = W.shu_osher_1d(300)
+    s = solver_of(p, charwise=True, precision="fp32")
+    _, L_g, _, _ = gpu_rhs(s, p.m)
+    _, L_o, _, _, rc = orc.rhs(cfg_of(orc, p, charwise=True), p.m)
+    assert rc == 0 and rel_l1(L_g, L_o) <= 1e-5
+    s.close()
+
+
+@pytest.mark.parametrize("name,make,nsteps", [
+    ("shu_osher", lambda: W.shu_osher_1d(300), 10),
+    ("blast_wave_walls", lambda: W.blast_wave_1d(200), 10),
+], ids=["shu_osher", "blast_wave_walls"])
+def test_charwise_steps_parity(orc, name, make, nsteps):
+    p = make()
+    s = solver_of(p, charwise=True)
+    s.set_moments(torch.from_numpy(p.m).cuda())
+    cfg = cfg_of(orc, p, charwise=True)
+    m = p.m
+    for _ in range(nsteps):
+        dt = s.max_dt(0.6)
+        assert math.isclose(dt, orc.max_dt(cfg, m, 0.6), rel_tol=1e-13)
+        s.step(dt)
+        m, masks, rc = orc.step(cfg, m, dt)
+        assert rc == 0
+        assert np.array_equal(s.troubled_mask().reshape(3, -1), masks)
+    assert rel_l1(s.get_moments(), m) <= TOL
+    s.close()
+
+
+def test_charwise_blast_waves_full_run():
+    """Example 3.7 to t = 0.038 (N = 800) with the characteristic-wise
+    reconstruction and the positivity check on: the run completes, density and
+    pressure stay positive, mass and energy are conserved to rounding between
+    the walls, and the density peak is that of the problem's known solution
+    (about 6, near x = 0.78)."""
+    p = W.blast_wave_1d(800)
+    s = solver_of(p, charwise=True)
+    s.set_moments(p.m)
+    t0 = s.totals()
+    t, n = s.advance(p.t_end, 0.6)
+    assert t == pytest.approx(p.t_end, rel=1e-14) and n > 1500
+    t1 = s.totals()
+    for v in (0, 2):
+        assert abs(t1[v] - t0[v]) <= 1e-12 * abs(t0[v]), (v, t0[v], t1[v])
+    m = s.get_moments()
+    rho = m[0, 0, 0]
+    pr = (p.gamma - 1.0) * (m[2, 0, 0] - 0.5 * m[1, 0, 0] ** 2 / rho)
+    assert np.isfinite(m).all() and (rho > 0).all() and (pr > 0).all()
+    assert 5.5 < rho.max() < 6.5 and 0.74 < (np.argmax(rho) + 0.5) / 800 < 0.80
+    s.close()
+
+
+def test_charwise_rejected_outside_1d_euler():
+    with pytest.raises(Exception):
+        solver_of(W.four_quadrant_2d(16, seed=1), charwise=True)
+    with pytest.raises(Exception):
+        solver_of(W.burgers_1d(32), charwise=True)
