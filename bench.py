@@ -72,6 +72,8 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched form")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-indicator form")
     ap.add_argument("--no-1d", action="store_true", help="skip the 1D Shu-Osher full run")
+    ap.add_argument("--full-run", action="store_true",
+                    help="also run the 2048^2 four-quadrant problem to t = 0.25 in FP64 and FP32-bulk")
     ap.add_argument("--learned-n", type=int, default=4096, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu", action="store_true")
     return ap.parse_args()
@@ -366,36 +368,104 @@ def _peaks():
 
 
 def run_shu_osher(torch, hweno, world):
-    """The 1D Shu-Osher problem (N = 4000, transmissive, to t = 1.8, CFL 0.6, FP64):
-    a latency-bound run of ~5,600 small steps (192 KB of state).  Timed whole,
+    """The 1D Shu-Osher problem (N = 4000, transmissive, to t = 1.8, CFL 0.6): a
+    latency-bound run of ~5,800 small steps (192 KB of state).  FP64 timed whole,
     device-driven (hweno_advance: dt formed on the device, graph replays of 12
-    steps) against the host-driven loop (hweno_max_dt + hweno_step)."""
+    steps) against the host-driven loop (hweno_max_dt + hweno_step); the FP32-bulk
+    and double-float forms run device-driven to the same time, each with the
+    relative L1 difference of its final state to the FP64 run's (all moments, and
+    cell averages alone) and the troubled cells per stage.  For scale, the same
+    difference between the FP64 runs at N = 4000 and N = 8000 (cell averages of
+    the fine run summed in pairs): the scheme's own resolution error."""
     from paper_2201_12193_gb300 import workloads as W
     p = W.shu_osher_1d(4000)
     out = {}
     finals = {}
-    for mode in ("advance", "host_loop"):
-        s = hweno.Solver.from_problem(p)
+    for mode, prec, nx in (("advance", "fp64", 4000), ("host_loop", "fp64", 4000), ("advance_fp32", "fp32", 4000),
+                           ("advance_df64", "df64", 4000), ("advance_n8000", "fp64", 8000)):
+        q = p if nx == 4000 else W.shu_osher_1d(nx)
+        s = hweno.Solver.from_problem(q, precision=prec)
         s.set_stream(torch.cuda.current_stream())
-        s.set_moments(torch.from_numpy(p.m).cuda())
-        s.advance(0.01) if mode == "advance" else s.run(0.01)      # warm-up (graph capture)
-        s.set_moments(torch.from_numpy(p.m).cuda())
+        s.set_moments(torch.from_numpy(q.m).cuda())
+        s.run(0.01) if mode == "host_loop" else s.advance(0.01)      # warm-up (graph capture)
+        s.set_moments(torch.from_numpy(q.m).cuda())
         s.sync()
+        s.rerecon_count()
         barrier(world)
         t0 = time.perf_counter()
-        if mode == "advance":
-            t, n = s.advance(1.8, CFL)
-        else:
+        if mode == "host_loop":
             n = s.run(1.8, CFL)
+        else:
+            _, n = s.advance(1.8, CFL)
         secs = max_over_ranks(time.perf_counter() - t0, world)
         finals[mode] = s.get_moments()
-        out[mode] = {"value": aggregate(p.nx, 3, n, world, secs * 1e3), "steps": n, "seconds": secs,
-                     "us_per_step": secs * 1e6 / n}
+        out[mode] = {"value": aggregate(q.nx, 3, n, world, secs * 1e3), "steps": n, "seconds": secs,
+                     "us_per_step": secs * 1e6 / n, "troubled_per_stage": s.rerecon_count() / (3.0 * n)}
         s.close()
+    ref = finals["advance"]
+
+    def rel(a, b):
+        return float(np.abs(a - b).sum() / np.abs(b).sum())
+    for mode in ("advance_fp32", "advance_df64"):
+        out[mode]["rel_l1_to_fp64"] = rel(finals[mode], ref)
+        out[mode]["rel_l1_averages_to_fp64"] = rel(finals[mode][:, 0], ref[:, 0])
+    fine = finals["advance_n8000"][:, 0, 0]
+    coarse = 0.5 * (fine[:, 0::2] + fine[:, 1::2])
     same = bool(np.array_equal(finals["advance"], finals["host_loop"]))
     return {"shu_osher_1d_full_run": {"workload": "1d_euler_shu_osher_4000_to_t1.8", "dtype": "f64",
                                       "value": out["advance"]["value"], "unit": UNIT, "device_driven": out["advance"],
-                                      "host_driven": out["host_loop"], "identical_states": same}}
+                                      "host_driven": out["host_loop"], "identical_states": same,
+                                      "fp32bulk": out["advance_fp32"], "df64": out["advance_df64"],
+                                      "resolution_gap_averages_n4000_vs_n8000": rel(ref[:, 0, 0], coarse),
+                                      "n8000_troubled_per_stage": out["advance_n8000"]["troubled_per_stage"]}}
+
+
+def run_four_quadrant_full(torch, hweno, world, rank):
+    """The four-quadrant problem (2048^2, seeded quadrant states) run whole to
+    t = 0.25, device-driven, in FP64 and FP32-bulk: steps, time,
+    cell-updates/s and the relative L1 difference of each final state to the
+    FP64 run's.  A seed whose FP64 run leaves the physical set is redrawn and
+    listed.  Not part of the default run (about a quarter of an hour)."""
+    from paper_2201_12193_gb300 import workloads as W
+    rejected = []
+    seed = rank
+    out, finals = {}, {}
+
+    def run(p, prec):
+        s = hweno.Solver.from_problem(p, precision=prec)
+        try:
+            s.set_stream(torch.cuda.current_stream())
+            s.set_moments(torch.from_numpy(p.m).cuda())
+            s.sync()
+            t0 = time.perf_counter()
+            t, n = s.advance(0.25, CFL)
+            secs = time.perf_counter() - t0
+            finals[prec] = s.get_moments()
+            out[prec] = {"value": aggregate(p.nx * p.ny, 3, n, 1, secs * 1e3), "steps": n, "seconds": secs,
+                         "t": t, "troubled_fraction_last_stage": float(s.troubled_mask()[-1].mean())}
+        finally:
+            s.close()
+
+    while True:
+        p = W.four_quadrant_2d(N, seed=seed)
+        try:
+            run(p, "fp64")
+            break
+        except hweno.HwenoError as e:
+            if e.status != hweno.ENONPHYSICAL or len(rejected) >= 8:
+                raise
+            rejected.append(seed)
+            seed += 1000
+    for prec in ("fp32",):
+        try:
+            run(p, prec)
+        except hweno.HwenoError as e:
+            out[prec] = {"failed": str(e)}
+            continue
+        out[prec]["rel_l1_to_fp64"] = float(np.abs(finals[prec] - finals["fp64"]).sum()
+                                            / np.abs(finals["fp64"]).sum())
+    return {"four_quadrant_2048_to_t0.25": {"workload": "2d_euler_four_quadrant_2048x2048_to_t0.25", "seed": seed,
+                                            "rejected_seeds": rejected, "unit": UNIT, **out}}
 
 
 def run_learned(torch, hweno, args, world, rank):
@@ -586,6 +656,8 @@ def run_ours(args, world, rank, local):
 
     if not args.no_forms and not args.no_1d:
         forms.update(run_shu_osher(torch, hweno, world))
+    if args.full_run:
+        forms.update(run_four_quadrant_full(torch, hweno, world, rank))
 
     if not args.no_forms and not args.no_batch:
         forms.update(run_batched(torch, hweno, args, world, rank))

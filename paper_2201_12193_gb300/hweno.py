@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libhweno.so")
 _lib = None
 
+ENONPHYSICAL = -3
 STATUS = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "ENONPHYSICAL", -4: "ETIMEOUT", -5: "ESTATE", -6: "ENOMEM"}
 EQ = {"advection": 0, "burgers": 1, "euler": 2}
 IND = {"none": 0, "kxrcf": 1, "all": 2, "mlp": 3, "tvb": 4}
