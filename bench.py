@@ -353,7 +353,7 @@ def _rec_traffic_per_cell():
     if not (m1 and m2):
         return None
     h = hashlib.sha256()
-    for f in ("hweno_2d.cu", "hweno_device.cuh", "hweno_parity.h", "hweno_internal.h"):
+    for f in ("hweno_2d_kernels.cuh", "hweno_device.cuh", "hweno_parity.h", "hweno_internal.h"):
         with open(os.path.join(ROOT, "paper_2201_12193_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return float(m1.group(1)) if h.hexdigest() == m2.group(1) else None

@@ -26,7 +26,7 @@ _lib = None
 
 EQ = {"advection": 0, "burgers": 1, "euler": 2}
 IND = {"none": 0, "kxrcf": 1, "all": 2, "given": 3, "tvb": 4}
-BC = {"periodic": 0, "transmissive": 1, "reflective": 2}
+BC = {"periodic": 0, "transmissive": 1, "reflective": 2, "inflow": 3}
 
 
 def build(force: bool = False) -> str:
@@ -44,12 +44,19 @@ class Cfg(ctypes.Structure):
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("eq", ctypes.c_int),
                 ("adv_a", ctypes.c_double), ("adv_b", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("indicator", ctypes.c_int), ("gbar", ctypes.c_double * 4), ("bc", ctypes.c_int * 4),
-                ("tvb_m", ctypes.c_double), ("charwise", ctypes.c_int)]
+                ("tvb_m", ctypes.c_double), ("charwise", ctypes.c_int),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("t", ctypes.c_double),
+                ("seg_on", ctypes.c_int * 4), ("seg_c0", ctypes.c_double * 4), ("seg_speed", ctypes.c_double * 4),
+                ("fa", (ctypes.c_double * 4) * 4), ("fb", (ctypes.c_double * 4) * 4)]
 
 
 def make_cfg(dim, nx, ny=1, dx=1.0, dy=1.0, eq="euler", adv=(1.0, 0.0), gamma=1.4,
              indicator="kxrcf", gbar=(1.0, 10.0, 100.0, 1000.0), bc=("periodic",) * 4, tvb_m=0.0,
-             charwise=False) -> Cfg:
+             charwise=False, x0=0.0, y0=0.0, t=0.0, fixed=None) -> Cfg:
+    """fixed: per side (x-lo, x-hi, y-lo, y-hi) None or a dict with the
+    fixed ghost states: "a" inside the segment (centre coordinate along the
+    side below c0 + speed * t; no segment when "c0" is absent), "b" elsewhere
+    on an "inflow" side."""
     c = Cfg()
     c.dim, c.nx, c.ny = dim, nx, (ny if dim == 2 else 1)
     c.dx, c.dy = dx, (dy if dim == 2 else 1.0)
@@ -59,6 +66,17 @@ def make_cfg(dim, nx, ny=1, dx=1.0, dy=1.0, eq="euler", adv=(1.0, 0.0), gamma=1.
     c.indicator = IND[indicator] if isinstance(indicator, str) else int(indicator)
     c.tvb_m = tvb_m
     c.charwise = int(bool(charwise))
+    c.x0, c.y0, c.t = x0, y0, t
+    for k, f in enumerate(fixed or [None] * 4):
+        if not f:
+            continue
+        if f.get("c0") is not None:
+            c.seg_on[k] = 1
+            c.seg_c0[k] = f["c0"]
+            c.seg_speed[k] = f.get("speed", 0.0)
+        for v in range(4):
+            c.fa[k][v] = f.get("a", (0.0,) * 4)[v]
+            c.fb[k][v] = f.get("b", (0.0,) * 4)[v]
     for k in range(4):
         c.gbar[k] = gbar[k]
         b = bc[k]

@@ -56,6 +56,16 @@ typedef struct {
   int bc[4];        /* x-lo, x-hi, y-lo, y-hi: 0 periodic, 1 transmissive, 2 reflective (Euler) */
   double tvb_m;     /* TVB constant M of indicator 4 */
   int charwise;     /* 1D Euler: reconstruct in local characteristic variables */
+  /* Fixed-state (inflow) ghost cells, per side (x-lo, x-hi, y-lo, y-hi; 2D
+   * Euler).  A ghost cell whose centre coordinate along the side (y on the x
+   * sides, x on the y sides) is below seg_c0 + seg_speed * t holds state fa
+   * when seg_on; on a side of kind 3 (inflow) the other ghost cells hold fb;
+   * otherwise they follow the side's kind. */
+  double x0, y0;    /* lower-left corner of the domain (cell centres from it) */
+  double t;         /* time of the stage input (moving segments) */
+  int seg_on[4];
+  double seg_c0[4], seg_speed[4];
+  double fa[4][4], fb[4][4];
 } orc_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -459,20 +469,38 @@ static void recon_cell(int dim, double dx, double dy, const double gbar[4],
  * are reversed in that direction; reflective (a solid wall, Euler only) = the
  * transmissive mirror with the wall-normal momentum negated as well (all its
  * moments and point values).  Ghost flags and modified moments are those of
- * the image cell. */
-typedef struct { int i, j, sx, sy, rx, ry; } image_t;
+ * the image cell.  A fixed-state ghost (inflow, the post-shock boundaries of
+ * Sec. 3's double Mach reflection) holds a constant state: that average, zero
+ * first moments, the same value at every Gauss-Lobatto point, never troubled.
+ * Corners: the y rule applies to the cell that the x rule gives (ghost
+ * columns are filled first, then ghost rows over all columns), so a fixed y
+ * ghost overrides, and a y mirror of a fixed x ghost negates its y momentum
+ * when the y side is a wall. */
+typedef struct { int i, j, sx, sy, rx, ry; const double *fix; } image_t;
+
+/* state of a fixed ghost of side `side` at centre coordinate `pos` along
+ * the side, or NULL if the side's kind applies there */
+static const double *fixed_state(const orc_cfg *c, int side, double pos) {
+  if (c->seg_on[side] && pos < c->seg_c0[side] + c->seg_speed[side] * c->t) return c->fa[side];
+  if (c->bc[side] == 3) return c->fb[side];
+  return NULL;
+}
 
 static image_t cell_image(const orc_cfg *c, int i, int j) {
-  image_t r = {i, j, 1, 1, 0, 0};
-  if (i < 0 || i >= c->nx) {
-    int side = i < 0 ? 0 : 1;
-    if (c->bc[side] == 0) { r.i = ((i % c->nx) + c->nx) % c->nx; }
-    else { r.i = i < 0 ? -1 - i : 2 * c->nx - 1 - i; r.sx = -1; r.rx = c->bc[side] == 2; }
-  }
+  image_t r = {i, j, 1, 1, 0, 0, NULL};
   if (c->dim == 2 && (j < 0 || j >= c->ny)) {
     int side = j < 0 ? 2 : 3;
+    r.fix = fixed_state(c, side, c->x0 + (i + 0.5) * c->dx);
+    if (r.fix) return r;
     if (c->bc[side] == 0) { r.j = ((j % c->ny) + c->ny) % c->ny; }
     else { r.j = j < 0 ? -1 - j : 2 * c->ny - 1 - j; r.sy = -1; r.ry = c->bc[side] == 2; }
+  }
+  if (i < 0 || i >= c->nx) {
+    int side = i < 0 ? 0 : 1;
+    r.fix = fixed_state(c, side, c->dim == 2 ? c->y0 + (r.j + 0.5) * c->dy : 0.0);
+    if (r.fix) return r;
+    if (c->bc[side] == 0) { r.i = ((i % c->nx) + c->nx) % c->nx; }
+    else { r.i = i < 0 ? -1 - i : 2 * c->nx - 1 - i; r.sx = -1; r.rx = c->bc[side] == 2; }
   }
   return r;
 }
@@ -494,6 +522,7 @@ static double *MOM(const orc_cfg *c, double *m, int var, int mom, int i, int j) 
 /* moment of any (possibly ghost) cell */
 static double mom_at(const orc_cfg *c, const double *m, int var, int mom, int i, int j) {
   image_t im = cell_image(c, i, j);
+  if (im.fix) return mom == 0 ? wall_sign(&im, var) * im.fix[var] : 0.0;
   double v = *MOM(c, (double *)m, var, mom, im.i, im.j);
   if (mom == 1) v *= im.sx;
   if (mom == 2) v *= im.sy;
@@ -503,6 +532,7 @@ static double mom_at(const orc_cfg *c, const double *m, int var, int mom, int i,
 /* GL values array G[cell][var][16]; value of any (possibly ghost) cell at node (k,l) */
 static double gl_at(const orc_cfg *c, const double *G, int var, int i, int j, int k, int l) {
   image_t im = cell_image(c, i, j);
+  if (im.fix) return wall_sign(&im, var) * im.fix[var];
   if (im.sx < 0) k = 3 - k;
   if (im.sy < 0) l = 3 - l;
   size_t cell = (size_t)im.j * c->nx + im.i;
@@ -936,14 +966,19 @@ int orc_step(const orc_cfg *c, double *m, double dt, unsigned char *masks) {
   size_t nc = ncell(c), n = (size_t)nvars(c) * nmoms(c) * nc;
   double *Un = malloc(n * sizeof(double)), *U1 = malloc(n * sizeof(double));
   double *U2 = malloc(n * sizeof(double)), *Um = malloc(n * sizeof(double)), *L = malloc(n * sizeof(double));
-  int rc = orc_rhs(c, m, Un, L, masks ? masks : NULL, NULL);
+  /* stage times t, t + dt, t + dt/2 (the abscissae of the scheme) for
+   * time-dependent boundaries */
+  orc_cfg cs = *c;
+  int rc = orc_rhs(&cs, m, Un, L, masks ? masks : NULL, NULL);
   if (rc == ORC_OK) {
     for (size_t t = 0; t < n; ++t) U1[t] = Un[t] + dt * L[t];
-    rc = orc_rhs(c, U1, Um, L, masks ? masks + nc : NULL, NULL);
+    cs.t = c->t + dt;
+    rc = orc_rhs(&cs, U1, Um, L, masks ? masks + nc : NULL, NULL);
   }
   if (rc == ORC_OK) {
     for (size_t t = 0; t < n; ++t) U2[t] = 0.75 * Un[t] + 0.25 * Um[t] + 0.25 * dt * L[t];
-    rc = orc_rhs(c, U2, Um, L, masks ? masks + 2 * nc : NULL, NULL);
+    cs.t = c->t + 0.5 * dt;
+    rc = orc_rhs(&cs, U2, Um, L, masks ? masks + 2 * nc : NULL, NULL);
   }
   if (rc == ORC_OK) {
     for (size_t t = 0; t < n; ++t) U1[t] = Un[t] / 3.0 + 2.0 / 3.0 * Um[t] + 2.0 / 3.0 * dt * L[t];

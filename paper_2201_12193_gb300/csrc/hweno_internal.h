@@ -155,6 +155,9 @@ cudaError_t run_adam(float* th, const float* grad, float* m1, float* m2, int ste
 cudaError_t run_mlpre2d(const Prob& P, const float* th, float conf, const double* U, uint8_t* mask, double* Mod,
                         int* und, int* und_count, int* stats, float* prob, cudaStream_t st);
 void run_stage_2d(const Prob& P, const HostTabs& T, int prec, const Bufs& B, const StageCall& S, cudaStream_t st);
+void run_stage_2d_fp32(const Prob& P, const HostTabs& T, const Bufs& B, const StageCall& S, cudaStream_t st);
+void run_stage_2d_df64(const Prob& P, const HostTabs& T, const Bufs& B, const StageCall& S, cudaStream_t st);
+cudaError_t run_batch_stage_df64(const HostTabs& T, int tile_variant, const BatchStage& S, int nsm, cudaStream_t st);
 
 // Reductions over the cell averages (FP64): maximum wave speeds per direction
 // and totals sum(ubar) per variable.  partials needs reduce_partials_len(P)
