@@ -59,7 +59,9 @@ typedef enum {
 } hweno_status;
 
 typedef enum { HWENO_ADVECTION = 0, HWENO_BURGERS = 1, HWENO_EULER = 2 } hweno_eq;
-typedef enum { HWENO_BC_PERIODIC = 0, HWENO_BC_TRANSMISSIVE = 1, HWENO_BC_REFLECTIVE = 2 } hweno_bc_kind;
+typedef enum {
+  HWENO_BC_PERIODIC = 0, HWENO_BC_TRANSMISSIVE = 1, HWENO_BC_REFLECTIVE = 2, HWENO_BC_INFLOW = 3
+} hweno_bc_kind;
 typedef enum {
   HWENO_IND_NONE = 0, HWENO_IND_KXRCF = 1, HWENO_IND_ALL = 2, HWENO_IND_MLP = 3, HWENO_IND_TVB = 4
 } hweno_indicator;
@@ -112,7 +114,15 @@ typedef struct {
 /* Boundary kinds of the four sides.  Periodic sides must come in pairs.
  * Transmissive = the mirror image about the boundary face (the cell average
  * and the tangential first moment are copied, the normal first moment changes
- * sign); ghost cells are images of interior cells throughout a stage. */
+ * sign); ghost cells are images of interior cells throughout a stage.
+ * Reflective (Euler) = the transmissive image with the wall-normal momentum
+ * negated.  Inflow (2D Euler, FP64, not with the learned indicator) = ghost
+ * cells of fixed states set by hweno_set_fixed_state (the inflow and
+ * post-shock boundaries of Sec. 3's double Mach reflection and forward step):
+ * that cell average, zero first moments, the same value at every
+ * Gauss-Lobatto point, never troubled.  In a corner the y side's rule applies
+ * to the cell the x side's rule gives (a fixed y ghost wins; the y wall image
+ * of a fixed x ghost negates its y momentum). */
 typedef struct { int xlo, xhi, ylo, yhi; } hweno_bc;
 
 /* Create a solver.  gamma: ratio of specific heats (Euler; ignored otherwise).
@@ -126,8 +136,35 @@ void hweno_destroy(hweno_t h);
 /* Use cuda_stream (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream). */
 hweno_status hweno_set_stream(hweno_t h, void* cuda_stream);
 
-/* Copy moments in (on_device = 0: pageable or pinned host; 1: device pointer). */
+/* Copy moments in (on_device = 0: pageable or pinned host; 1: device pointer).
+ * Sets the solution time to 0. */
 hweno_status hweno_set_moments(hweno_t h, const double* m, size_t count, int on_device);
+
+/* Fixed-state ghost cells of one side (0 x-lo, 1 x-hi, 2 y-lo, 3 y-hi) of a
+ * single-problem 2D Euler FP64 handle.  With segment = 1, the ghost cells
+ * whose centre coordinate along the side (y on the x sides, x on the y sides;
+ * ghost cells one position beyond each end included) is below c0 + speed * t,
+ * t the time of the stage input, hold the conserved state a; the other ghost
+ * cells of an HWENO_BC_INFLOW side hold b, those of another kind follow that
+ * kind.  An inflow side needs this call before the first step (else step,
+ * advance and rhs return ESTATE); a segment may also sit on a transmissive or
+ * reflective side (the double Mach reflection's floor: post-shock before the
+ * wedge, wall after it).  States need rho > 0 and p > 0 (else EINVAL).  Stage
+ * times are t, t + dt and t + dt/2; positions and thresholds are rounded as
+ * written (no fused multiply-add). */
+typedef struct {
+  int segment;
+  double c0, speed;
+  double a[4];     /* (rho, rho u, rho v, E) inside the segment */
+  double b[4];     /* (rho, rho u, rho v, E) elsewhere on an inflow side */
+} hweno_fixed_state;
+hweno_status hweno_set_fixed_state(hweno_t h, int side, const hweno_fixed_state* f);
+
+/* Solution time of a single-problem handle (read by moving segments):
+ * hweno_step advances it by dt (restored when a step is rolled back),
+ * hweno_advance by the time it reached, hweno_set_moments resets it to 0. */
+hweno_status hweno_set_time(hweno_t h, double t);
+hweno_status hweno_get_time(hweno_t h, double* t);
 
 /* Copy the current moments out (synchronises when the destination is host memory). */
 hweno_status hweno_get_moments(hweno_t h, double* m, size_t count, int on_device);

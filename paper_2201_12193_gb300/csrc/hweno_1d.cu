@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(RB) flag1d_kernel(Prob P, Weights<T> W, const 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = i < P.nx;
   bool flag = false;
-  Img L{0, 0, 1, 1, 0}, R{0, 0, 1, 1, 0};
+  Img L{0, 0, 1, 1, 0, -1}, R{0, 0, 1, 1, 0, -1};
   if (valid) {
     L = image(P, i - 1, 0);
     R = image(P, i + 1, 0);
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(UB) update1d_kernel(Prob P, const T* __restric
       return;
     }
   }
-  const Img self{i, 0, 1, 1};
+  const Img self{i, 0, 1, 1, 0, -1};
   // fx[c] is the face left of cell i0 + c; one call site computes every face so
   // that faces shared by two blocks get bitwise the same flux.
   for (int c = t; c <= RB; c += UB) {     // UB > RB: at most one face per thread

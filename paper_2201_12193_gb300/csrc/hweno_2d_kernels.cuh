@@ -2,6 +2,7 @@
 // stage (shared by the per-precision translation units; internal linkage).
 #pragma once
 #include <algorithm>
+#include <type_traits>
 
 #include "hweno_internal.h"
 
@@ -18,14 +19,18 @@ struct Nbr {
   int xi[3], xs[3];     // image column and sign of the x first moment, for ox = -1, 0, 1
   int yj[3], ys[3];     // image row and sign of the y first moment, for oy = -1, 0, 1
   int neg[3][3];        // variables negated by reflective walls, [oy + 1][ox + 1]
+  int fs[3][3];         // fixed-state ghost entry (-1: none), set when FIX
 };
 
+template <bool FIX>
 __device__ __forceinline__ Nbr neighbours(const Prob& P, int i, int j) {
   Nbr n;
   int nx[3], ny[3];
 #pragma unroll
   for (int o = -1; o <= 1; ++o) {
-    const Img a = image(P, i + o, j), b = image(P, i, j + o);
+    // by the kinds alone: a fixed ghost in the separable x or y image does
+    // not make its row or column fixed for the diagonal cells
+    const Img a = image_kind(P, i + o, j), b = image_kind(P, i, j + o);
     n.xi[o + 1] = a.i; n.xs[o + 1] = a.sx; nx[o + 1] = a.neg;
     n.yj[o + 1] = b.j; n.ys[o + 1] = b.sy; ny[o + 1] = b.neg;
   }
@@ -33,6 +38,17 @@ __device__ __forceinline__ Nbr neighbours(const Prob& P, int i, int j) {
   for (int oy = 0; oy < 3; ++oy)
 #pragma unroll
     for (int ox = 0; ox < 3; ++ox) n.neg[oy][ox] = nx[ox] | ny[oy];
+  if constexpr (FIX) {
+    // fixed-state ghosts break the separable form: the full image of each cell
+#pragma unroll
+    for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+      for (int ox = 0; ox < 3; ++ox) {
+        const Img m = image(P, i + ox - 1, j + oy - 1);
+        n.fs[oy][ox] = m.fs;
+        if (m.fs >= 0) n.neg[oy][ox] = m.neg;
+      }
+  }
   return n;
 }
 
@@ -45,10 +61,14 @@ enum RecMode { REC_PLAIN = 0, REC_FLAGGED = 1, REC_MIXED = 2 };
 // Moment of kind 0 (average), 1 (x first moment) or 2 (y first moment) of
 // the stencil cell (ox, oy); when usemod, first moments of flagged stencil
 // cells come from the modified copy (eq. (vi) applied before Step 2.3).
-template <int MODE, bool SIGNBIT>
+template <int MODE, bool SIGNBIT, bool FIX>
 __device__ __forceinline__ double load_mom(const Prob& P, const double* __restrict__ U, const uint8_t* __restrict__ mask,
                                            const double* __restrict__ Mod, const Nbr& n, int var, int kind, int ox,
                                            int oy, bool usemod) {
+  if constexpr (FIX) {
+    const int fs = n.fs[oy + 1][ox + 1];
+    if (fs >= 0) return kind == 0 ? ((n.neg[oy + 1][ox + 1] >> var) & 1 ? -1.0 : 1.0) * P.fixtab[4 * fs + var] : 0.0;
+  }
   const int ci = n.xi[ox + 1], cj = n.yj[oy + 1];
   const long long so = (long long)cj * P.pitch + ci;
   if constexpr (SIGNBIT) {
@@ -84,14 +104,14 @@ __device__ __forceinline__ double load_mom(const Prob& P, const double* __restri
   }
 }
 
-template <typename T, int NV, int MODE>
+template <typename T, int NV, int MODE, bool FIX = false>
 __device__ __forceinline__ void rec2d_cell(const Prob& P, const Weights<T>& W, const Beta2<T>& B,
                                            const double* __restrict__ U, const uint8_t* __restrict__ mask,
                                            const double* __restrict__ Mod, int i, int j, T* __restrict__ G,
                                            T* __restrict__ aux) {
   constexpr bool FLAGGED = MODE == REC_FLAGGED;
   const bool usemod = MODE == REC_FLAGGED || (MODE == REC_MIXED && mask[(long long)j * P.nx + i] == 1);
-  const Nbr nb = neighbours(P, i, j);
+  const Nbr nb = neighbours<FIX>(P, i, j);
   const long long o = goff(P, i, j);
   T rinv[16];
   T pxl = T(0), pxr = T(0), pyb = T(0), pyt = T(0), nrm = T(0);
@@ -102,7 +122,7 @@ __device__ __forceinline__ void rec2d_cell(const Prob& P, const Weights<T>& W, c
     for (int c = 0; c < 23; ++c) {
       int kind, ox, oy;
       d4_slot(c, kind, ox, oy);
-      d[c] = from_double<T>(load_mom<MODE, !is_df64<T>::value>(P, U, mask, Mod, nb, v, kind, ox, oy, usemod));
+      d[c] = from_double<T>(load_mom<MODE, !is_df64<T>::value, FIX>(P, U, mask, Mod, nb, v, kind, ox, oy, usemod));
     }
     T out[16];
     recon2d<T>(W, B, d, out);
@@ -166,7 +186,7 @@ __device__ __forceinline__ void rec2d_cell(const Prob& P, const Weights<T>& W, c
 // reconstructed a second time.
 // Double-float: 4 resident blocks per SM (at most 128 registers, a few spills)
 // beat 3 (168 registers, none): 7.0 vs 8.3 ms per launch at 2048^2.
-template <typename T, int NV, int MODE>
+template <typename T, int NV, int MODE, bool FIX = false>
 __global__ void __launch_bounds__(RB, (is_df64<T>::value ? 4 : 1)) rec2d_kernel(Prob P, Weights<T> W, Beta2<T> B, const double* __restrict__ U,
                                                   const uint8_t* __restrict__ mask, const double* __restrict__ Mod,
                                                   const int* __restrict__ list, const int* __restrict__ count,
@@ -178,7 +198,7 @@ __global__ void __launch_bounds__(RB, (is_df64<T>::value ? 4 : 1)) rec2d_kernel(
   if (FLAGGED && rerec && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(rerec, (unsigned long long)n);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int cell = FLAGGED ? list[t] : (int)t;
-    rec2d_cell<T, NV, MODE>(P, W, B, U, mask, Mod, cell % P.nx, cell / P.nx, G, aux);
+    rec2d_cell<T, NV, MODE, FIX>(P, W, B, U, mask, Mod, cell % P.nx, cell / P.nx, G, aux);
   }
 }
 
@@ -202,13 +222,17 @@ __device__ __forceinline__ void modify2d_cell(const Prob& P, const double* __res
                                               int i, int j) {
   const Img L = image(P, i - 1, j), R = image(P, i + 1, j), Bo = image(P, i, j - 1), Tp = image(P, i, j + 1);
   const long long o = (long long)j * P.pitch + i;
+  // moment (kind 1: x, 2: y first moment) of an edge neighbour; a fixed-state
+  // ghost has its state as average and zero first moments
+  auto mom = [&](const Img& m, int v, int kind) -> double {
+    if (m.fs >= 0) return kind == 0 ? fixed_val(P, m, v) : 0.0;
+    const int g = vsign(m, v) * (kind == 1 ? m.sx : kind == 2 ? m.sy : 1);
+    return g * U[sidx(P, v, kind, m.i, m.j)];
+  };
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const int gL = vsign(L, v), gR = vsign(R, v), gB = vsign(Bo, v), gT = vsign(Tp, v);
-    const double uL = gL * U[sidx(P, v, 0, L.i, L.j)], uR = gR * U[sidx(P, v, 0, R.i, R.j)];
-    const double vL = gL * L.sx * U[sidx(P, v, 1, L.i, L.j)], vR = gR * R.sx * U[sidx(P, v, 1, R.i, R.j)];
-    const double uB = gB * U[sidx(P, v, 0, Bo.i, Bo.j)], uT = gT * U[sidx(P, v, 0, Tp.i, Tp.j)];
-    const double wB = gB * Bo.sy * U[sidx(P, v, 2, Bo.i, Bo.j)], wT = gT * Tp.sy * U[sidx(P, v, 2, Tp.i, Tp.j)];
+    const double uL = mom(L, v, 0), uR = mom(R, v, 0), vL = mom(L, v, 1), vR = mom(R, v, 1);
+    const double uB = mom(Bo, v, 0), uT = mom(Tp, v, 0), wB = mom(Bo, v, 2), wT = mom(Tp, v, 2);
     Mod[(long long)(v * 2 + 0) * P.plane + o] = MOD_WU * (uR - uL) + MOD_WV * (vL + vR);
     Mod[(long long)(v * 2 + 1) * P.plane + o] = MOD_WU * (uT - uB) + MOD_WV * (wB + wT);
   }
@@ -273,6 +297,11 @@ __global__ void __launch_bounds__(RB) fallback2d_kernel(Prob P, Weights<T> W, co
 
 template <typename T, int NV>
 __device__ __forceinline__ void gl_state(const Prob& P, const T* __restrict__ G, const Img& m, int k, int l, T (&u)[NV]) {
+  if (m.fs >= 0) {   // fixed-state ghost: its state at every point
+#pragma unroll
+    for (int v = 0; v < NV; ++v) u[v] = from_double<T>(fixed_val(P, m, v));
+    return;
+  }
   const long long o = goff(P, m.i, m.j);
   const int p = mpt(m, k, l);
 #pragma unroll
@@ -299,7 +328,7 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
   const int tx = tid % TXV, ty = tid / TXV;
   const int i = i0 + tx, j = j0 + ty;
   const bool live = i < P.nx && j < P.ny;
-  const Img self{i, j, 1, 1};
+  const Img self{i, j, 1, 1, 0, -1};
   // Every face flux of the tile at one Gauss-Lobatto point per iteration, by one
   // call site, so that a face shared by two tiles gets bitwise the same flux
   // from both (the flux differences then telescope exactly in FP64).
@@ -434,6 +463,21 @@ __global__ void __launch_bounds__(TX * TY) update2d_kernel(Prob P, const T* __re
   update2d_tile<T, NV, TX, TY>(P, G, S, blockIdx.x * TX, blockIdx.y * TY, threadIdx.y * TX + threadIdx.x, xf, yf);
 }
 
+// Fixed-state ghosts are supported for 2D Euler in FP64 (the library rejects
+// other combinations), so only that instantiation carries the FIX variant.
+template <typename T, int NV, int MODE>
+void launch_rec2d(int blocks, cudaStream_t st, const Prob& P, const Weights<T>& W, const Beta2<T>& Bt,
+                  const double* U, const uint8_t* mask, const double* Mod, const int* list, const int* count, T* G,
+                  T* aux, unsigned long long* rerec) {
+  if constexpr (NV == 4 && std::is_same<T, double>::value) {
+    if (P.fixtab) {
+      rec2d_kernel<T, NV, MODE, true><<<blocks, RB, 0, st>>>(P, W, Bt, U, mask, Mod, list, count, G, aux, rerec);
+      return;
+    }
+  }
+  rec2d_kernel<T, NV, MODE><<<blocks, RB, 0, st>>>(P, W, Bt, U, mask, Mod, list, count, G, aux, rerec);
+}
+
 template <typename T, int NV>
 void stage_t(const Prob& P, const HostTabs& HT, const Weights<T>& W, const Beta2<T>& Bt, const Bufs& B,
              const StageCall& S, cudaStream_t st) {
@@ -463,8 +507,8 @@ void stage_t(const Prob& P, const HostTabs& HT, const Weights<T>& W, const Beta2
     if (B.prof) B.prof->end(st);
   } else {
     if (B.prof) B.prof->begin(0, st);
-    rec2d_kernel<T, NV, REC_PLAIN><<<rblocks, RB, 0, st>>>(P, W, Bt, S.Uin, nullptr, nullptr, nullptr, nullptr,
-                                                           (T*)B.G, (T*)B.aux, nullptr);
+    launch_rec2d<T, NV, REC_PLAIN>(rblocks, st, P, W, Bt, S.Uin, nullptr, nullptr, nullptr, nullptr, (T*)B.G,
+                                   (T*)B.aux, nullptr);
     if (B.prof) B.prof->end(st);
     if (B.prof) B.prof->begin(1, st);
     flag2d_kernel<T, NV><<<grd, blk, 0, st>>>(P, W, S.Uin, (const T*)B.G, (const T*)B.aux, S.mask, S.Mod, B.list,
@@ -473,8 +517,8 @@ void stage_t(const Prob& P, const HostTabs& HT, const Weights<T>& W, const Beta2
   }
   if (P.indicator != IND_NONE) {
     if (B.prof) B.prof->begin(2, st);
-    rec2d_kernel<T, NV, REC_FLAGGED><<<fblocks, RB, 0, st>>>(P, W, Bt, S.Uin, S.mask, S.Mod, B.list, cnt, (T*)B.G,
-                                                             nullptr, B.rerec);
+    launch_rec2d<T, NV, REC_FLAGGED>(fblocks, st, P, W, Bt, S.Uin, S.mask, S.Mod, B.list, cnt, (T*)B.G, nullptr,
+                                     B.rerec);
     if (B.prof) B.prof->end(st);
   }
   Rk r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status, S.dtp};

@@ -33,7 +33,11 @@ struct hweno_s {
   double* red_out = nullptr;     // reduction results (device)
   double* host_buf = nullptr;    // pinned: reduction results + status
   hw::Prof prof;                 // per-kernel event timing (hweno_profile)
-  double* adv = nullptr;         // hweno_advance: device {T, cfl, max_steps, t, dt, steps}
+  double* adv = nullptr;         // hweno_advance: device {T, cfl, max_steps, t, dt, steps, t at the step's start}
+  double time = 0.0, time_prev = 0.0;   // solution time (moving fixed-state segments); before the last step
+  hw::FixSpec fix{};             // fixed-state (inflow) ghost cells
+  bool fix_set[4] = {false, false, false, false};
+  double* fixtab = nullptr;      // their per-stage table (device), Prob::fixtab
   cudaGraphExec_t agraphs[3] = {nullptr, nullptr, nullptr};   // hweno_advance, one per state rotation
   bool adv_graph = true;         // capture works here (else direct launches)
   float* mlp = nullptr;          // learned indicator parameters (device)
@@ -159,10 +163,14 @@ hweno_status validate(const hweno_grid* g, const hweno_bc* bc, double gamma, std
     if (!(g->gamma_bar[l] > 0.0) || !isfinite(g->gamma_bar[l])) { why = "gamma_bar must be positive"; return HWENO_EINVAL; }
   const int k[4] = {bc->xlo, bc->xhi, bc->ylo, bc->yhi};
   for (int s = 0; s < (g->dim == 2 ? 4 : 2); ++s)
-    if (k[s] != HWENO_BC_PERIODIC && k[s] != HWENO_BC_TRANSMISSIVE && k[s] != HWENO_BC_REFLECTIVE) {
+    if (k[s] != HWENO_BC_PERIODIC && k[s] != HWENO_BC_TRANSMISSIVE && k[s] != HWENO_BC_REFLECTIVE &&
+        k[s] != HWENO_BC_INFLOW) {
       why = "unknown boundary kind"; return HWENO_EINVAL;
     } else if (k[s] == HWENO_BC_REFLECTIVE && g->eq != HWENO_EULER) {
       why = "reflective walls need the Euler equations"; return HWENO_EINVAL;
+    } else if (k[s] == HWENO_BC_INFLOW && (g->dim != 2 || g->eq != HWENO_EULER || g->precision != 0 ||
+                                           g->indicator == 3)) {
+      why = "inflow sides need 2D Euler in FP64 without the learned indicator"; return HWENO_EINVAL;
     }
   if ((bc->xlo == HWENO_BC_PERIODIC) != (bc->xhi == HWENO_BC_PERIODIC) ||
       (g->dim == 2 && (bc->ylo == HWENO_BC_PERIODIC) != (bc->yhi == HWENO_BC_PERIODIC))) {
@@ -192,6 +200,7 @@ void free_all(hweno_s* h) {
   cudaFree(h->B.und_count);
   cudaFree(h->B.rerec);
   cudaFree(h->adv);
+  cudaFree(h->fixtab);
   cudaFree(h->dprobs);
   cudaFree(h->blist);
   cudaFree(h->speeds);
@@ -232,15 +241,23 @@ hweno_status check_status(hweno_t h) {
   if (!h->positivity) st &= ~hw::ST_NONPOSITIVE;
   if (st != 0) {
     CK(h, cudaMemsetAsync(h->B.status, 0, sizeof(unsigned), h->stream));
-    if (h->stepped) h->cur = h->prev;
+    if (h->stepped) { h->cur = h->prev; h->time = h->time_prev; }
     h->stepped = false;
     char buf[200];
-    snprintf(buf, sizeof buf, "last step produced a non-physical state or timed out (status 0x%x: %s%s%s); rolled back",
+    snprintf(buf, sizeof buf, "last step produced a non-physical state or timed out (status 0x%x: %s%s%s%s); rolled back",
              st, (st & hw::ST_NONFINITE) ? "non-finite " : "", (st & hw::ST_NONPOSITIVE) ? "rho<=0 or p<=0 " : "",
-             (st & hw::ST_TIMEOUT) ? "grid barrier wait limit" : "");
+             (st & hw::ST_NODT) ? "no CFL step length " : "", (st & hw::ST_TIMEOUT) ? "grid barrier wait limit" : "");
     return fail(h, (st & hw::ST_TIMEOUT) ? HWENO_ETIMEOUT : HWENO_ENONPHYSICAL, buf);
   }
   return HWENO_OK;
+}
+
+// every inflow side has its fixed states
+bool fix_ready(const hweno_s* h) {
+  const int k[4] = {h->bc.xlo, h->bc.xhi, h->bc.ylo, h->bc.yhi};
+  for (int s = 0; s < 4; ++s)
+    if (h->g.dim == 2 && k[s] == HWENO_BC_INFLOW && !h->fix_set[s]) return false;
+  return true;
 }
 
 }  // namespace
@@ -361,6 +378,7 @@ hweno_status hweno_set_moments(hweno_t h, const double* m, size_t count, int on_
   CK(h, cudaMemsetAsync(h->B.status, 0, sizeof(unsigned), h->stream));
   h->have_state = true;
   h->stepped = false;
+  h->time = 0.0;
   if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
   return HWENO_OK;
 }
@@ -386,9 +404,13 @@ hweno_status hweno_step(hweno_t h, double dt) {
   if (!h->have_state) return fail(h, HWENO_ESTATE, "step: no moments set");
   if (h->g.indicator == 3 && !h->have_mlp) return fail(h, HWENO_ESTATE, "step: learned indicator not set (hweno_set_mlp)");
   if (!(dt >= 0.0) || !isfinite(dt)) return fail(h, HWENO_EINVAL, "step: dt must be finite and >= 0");
+  if (!fix_ready(h)) return fail(h, HWENO_ESTATE, "step: an inflow side has no fixed states (hweno_set_fixed_state)");
   const int a = h->cur, b = (h->cur + 1) % 3, c = (h->cur + 2) % 3;
   const size_t nc = ncell(h);
+  // stage times t, t + dt, t + dt/2 (the scheme's abscissae) for moving segments
+  const double tst[3] = {h->time, h->time + dt, h->time + 0.5 * dt};
   auto run = [&](const hw::StageCall& S) {
+    if (h->P.fixtab) hw::run_fixfill(h->fix, h->fixtab, tst[S.stage], nullptr, nullptr, 0.0, h->stream);
     if (h->g.dim == 1) hw::run_stage_1d(h->P, h->T, h->fp32, h->B, S, h->stream);
     else hw::run_stage_2d(h->P, h->T, h->fp32, h->B, S, h->stream);
   };
@@ -409,6 +431,8 @@ hweno_status hweno_step(hweno_t h, double dt) {
   h->prev = a;
   h->cur = b;
   h->stepped = true;
+  h->time_prev = h->time;
+  h->time += dt;
   return HWENO_OK;
 }
 
@@ -431,6 +455,10 @@ cudaError_t advance_steps(hweno_t h, int a, cudaStream_t st) {
     hw::run_wavespeed(h->P, h->U[a], h->red_part, h->red_out, st);
     hw::run_advance_dt(h->P, h->red_out, par, stt, h->B.status, st);
     auto run = [&](const hw::StageCall& S) {
+      if (h->P.fixtab) {   // stage time from the device: t_n + c dt, c = 0, 1, 1/2
+        const double cst[3] = {0.0, 1.0, 0.5};
+        hw::run_fixfill(h->fix, h->fixtab, 0.0, stt + 3, stt + 1, cst[S.stage], st);
+      }
       if (h->g.dim == 1) hw::run_stage_1d(h->P, h->T, h->fp32, h->B, S, st);
       else hw::run_stage_2d(h->P, h->T, h->fp32, h->B, S, st);
     };
@@ -478,11 +506,14 @@ hweno_status hweno_advance(hweno_t h, double t_end, double cfl, long long max_st
   if (h->g.indicator == 3 && !h->have_mlp) return fail(h, HWENO_ESTATE, "advance: learned indicator not set");
   if (!(t_end >= 0.0) || !isfinite(t_end) || !(cfl > 0.0) || !isfinite(cfl) || max_steps < 0)
     return fail(h, HWENO_EINVAL, "advance: need t_end >= 0, cfl > 0 and max_steps >= 0");
+  if (!fix_ready(h)) return fail(h, HWENO_ESTATE, "advance: an inflow side has no fixed states");
   hweno_status s0 = check_status(h);
   if (s0 != HWENO_OK) return s0;
-  if (!h->adv) CK(h, cudaMalloc(&h->adv, 6 * sizeof(double)));
+  if (!h->adv) CK(h, cudaMalloc(&h->adv, 8 * sizeof(double)));
   double* hb = h->host_buf + 8;
-  hb[0] = t_end; hb[1] = cfl; hb[2] = (double)max_steps; hb[3] = 0.0; hb[4] = 0.0; hb[5] = 0.0;
+  // the device clock runs on the solution time: from h->time to h->time + t_end
+  const double t0 = h->time;
+  hb[0] = t0 + t_end; hb[1] = cfl; hb[2] = (double)max_steps; hb[3] = t0; hb[4] = 0.0; hb[5] = 0.0;
   CK(h, cudaMemcpyAsync(h->adv, hb, 6 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   h->stepped = false;     // several steps per replay: no single-step roll-back
   double t = 0.0, steps = 0.0;
@@ -500,7 +531,8 @@ hweno_status hweno_advance(hweno_t h, double t_end, double cfl, long long max_st
     const hweno_status s = check_status(h);
     if (s != HWENO_OK) return s;
     const double before = steps;
-    t = hb[3];
+    t = hb[3] - t0;
+    h->time = hb[3];
     steps = hb[5];
     if (steps == before) break;           // nothing advanced (dt could not be formed)
   }
@@ -558,6 +590,8 @@ hweno_status hweno_rhs(hweno_t h, const double* U, double* Umod, double* L, unsi
   Prob P = h->P;           // caller arrays are unpadded
   P.pitch = P.nx;
   P.plane = (long long)P.ny * P.nx;
+  if (!fix_ready(h)) return fail(h, HWENO_ESTATE, "rhs: an inflow side has no fixed states");
+  if (h->P.fixtab) hw::run_fixfill(h->fix, h->fixtab, h->time, nullptr, nullptr, 0.0, h->stream);
   hw::StageCall S{};
   S.stage = 3; S.Uin = U; S.Un = U; S.Uout = nullptr; S.dt = 0.0; S.cA = 0.0; S.cB = 1.0;
   S.mask = mask; S.Mod = h->ModK; S.maskN = nullptr; S.ModN = nullptr;
@@ -609,6 +643,58 @@ hweno_status hweno_mlp_fallbacks(hweno_t h, long long* cells) {
   CK(h, cudaStreamSynchronize(h->stream));
   CK(h, cudaMemsetAsync(h->mlp_stats, 0, sizeof(int), h->stream));
   *cells = v;
+  return HWENO_OK;
+}
+
+hweno_status hweno_set_fixed_state(hweno_t h, int side, const hweno_fixed_state* f) {
+  if (!h || !f) return HWENO_EINVAL;
+  if (h->batch || h->g.dim != 2 || h->g.eq != HWENO_EULER || h->fp32 != hw::PREC_FP64 || h->g.indicator == 3)
+    return fail(h, HWENO_EINVAL, "set_fixed_state: single-problem 2D Euler FP64 handles without the learned indicator");
+  if (side < 0 || side > 3) return fail(h, HWENO_EINVAL, "set_fixed_state: side must be 0..3");
+  const int kinds[4] = {h->bc.xlo, h->bc.xhi, h->bc.ylo, h->bc.yhi};
+  const bool inflow = kinds[side] == HWENO_BC_INFLOW;
+  if (kinds[side] == HWENO_BC_PERIODIC) return fail(h, HWENO_EINVAL, "set_fixed_state: the side is periodic");
+  if (!inflow && !f->segment) return fail(h, HWENO_EINVAL, "set_fixed_state: only inflow sides take states without a segment");
+  auto physical = [&](const double* u) {
+    for (int v = 0; v < 4; ++v) if (!isfinite(u[v])) return false;
+    const double p = (h->gamma - 1.0) * (u[3] - 0.5 * (u[1] * u[1] + u[2] * u[2]) / u[0]);
+    return u[0] > 0.0 && p > 0.0;
+  };
+  if (f->segment && (!physical(f->a) || !isfinite(f->c0) || !isfinite(f->speed)))
+    return fail(h, HWENO_EINVAL, "set_fixed_state: segment state must have rho > 0 and p > 0, c0 and speed finite");
+  if (inflow && !physical(f->b)) return fail(h, HWENO_EINVAL, "set_fixed_state: inflow state must have rho > 0 and p > 0");
+  hw::FixSpec& F = h->fix;
+  if (!h->fixtab) {
+    F.fixlen = std::max(h->P.nx, h->P.ny) + 2;
+    F.n[0] = F.n[1] = h->P.ny;
+    F.n[2] = F.n[3] = h->P.nx;
+    F.x0 = h->g.x0; F.y0 = h->g.y0; F.dx = h->P.dx; F.dy = h->P.dy;
+    for (int s = 0; s < 4; ++s) F.inflow[s] = kinds[s] == HWENO_BC_INFLOW;
+    CK(h, cudaMalloc(&h->fixtab, 16 * (size_t)F.fixlen * sizeof(double)));
+    CK(h, cudaMemsetAsync(h->fixtab, 0, 16 * (size_t)F.fixlen * sizeof(double), h->stream));
+    h->P.fixtab = h->fixtab;
+    h->P.fixlen = F.fixlen;
+  }
+  F.seg[side] = f->segment ? 1 : 0;
+  F.c0[side] = f->c0;
+  F.speed[side] = f->speed;
+  for (int v = 0; v < 4; ++v) { F.a[side][v] = f->a[v]; F.b[side][v] = f->b[v]; }
+  h->fix_set[side] = true;
+  drop_graphs(h);
+  return HWENO_OK;
+}
+
+hweno_status hweno_set_time(hweno_t h, double t) {
+  if (!h || !isfinite(t)) return HWENO_EINVAL;
+  if (h->batch) return fail(h, HWENO_ESTATE, "set_time: single-problem handles only");
+  h->time = t;
+  h->stepped = false;
+  return HWENO_OK;
+}
+
+hweno_status hweno_get_time(hweno_t h, double* t) {
+  if (!h || !t) return HWENO_EINVAL;
+  *t = h->time;
   return HWENO_OK;
 }
 
@@ -729,6 +815,11 @@ hweno_status hweno_create_batch(const hweno_grid* grids, const hweno_bc* bcs, in
       return HWENO_EINVAL;
     }
     const hweno_grid& g = grids[k];
+    if (bcs[k].xlo == HWENO_BC_INFLOW || bcs[k].xhi == HWENO_BC_INFLOW || bcs[k].ylo == HWENO_BC_INFLOW ||
+        bcs[k].yhi == HWENO_BC_INFLOW) {
+      fprintf(stderr, "hweno_create_batch: problem %d: inflow sides run on single-problem handles\n", k);
+      return HWENO_EINVAL;
+    }
     if (g.dim != 2 || g.eq != HWENO_EULER || g.precision != grids[0].precision ||
         g.indicator != grids[0].indicator || g.beta_of_q != grids[0].beta_of_q ||
         memcmp(g.gamma_bar, grids[0].gamma_bar, sizeof g.gamma_bar) != 0) {

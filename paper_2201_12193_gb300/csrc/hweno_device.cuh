@@ -23,6 +23,7 @@ constexpr int IND_NONE = 0, IND_KXRCF = 1, IND_ALL = 2, IND_MLP = 3, IND_TVB = 4
 // device status word bits
 constexpr unsigned ST_NONFINITE = 1u;     // a non-finite value in the new state
 constexpr unsigned ST_NONPOSITIVE = 2u;   // rho <= 0 or p <= 0 in a new cell average (Euler)
+constexpr unsigned ST_NODT = 8u;          // no CFL step length (rho <= 0 or a non-finite wave speed)
 
 // Problem description passed by value to every kernel.
 struct Prob {
@@ -42,6 +43,10 @@ struct Prob {
   int charwise;           // 1D Euler: reconstruction in local characteristic variables
   int positivity;         // 1: rho <= 0 or p <= 0 averages are non-physical; 0: p is
                           //    clamped at 0 in the sound speed (only rho <= 0 / non-finite fail)
+  const double* fixtab;   // fixed-state ghost cells (inflow; 2D Euler): [side][pos + 1][4] conserved
+                          //    states for ghost positions pos in [-1, n] along each side, rho = 0
+                          //    where the side's kind applies instead; null: no fixed-state side
+  int fixlen;             // entries per side of fixtab
 };
 
 // Sound speed of a cell average for the CFL rule; +inf marks a non-physical
@@ -87,12 +92,46 @@ template <typename T> __device__ __forceinline__ T tmax(T a, T b) { return a > b
 // with the wall-normal momentum negated as well (all its moments and point
 // values): neg has bit v set for each variable v the image negates
 // (variable 1 = x momentum, 2 = y momentum in 2D).
-struct Img { int i, j, sx, sy, neg; };
+// A fixed-state ghost (inflow, the post-shock boundaries of the double Mach
+// reflection) holds a constant state, entry fs of Prob::fixtab: that average,
+// zero first moments, the same value at every Gauss-Lobatto point, never
+// troubled.  Corners take the y rule on the cell the x rule gives (ghost
+// columns first, then ghost rows over all columns): a fixed y ghost wins, and
+// the y mirror of a fixed x ghost negates its y momentum at a wall.
+struct Img { int i, j, sx, sy, neg, fs; };
 
 __device__ __forceinline__ int wrap(int i, int n) { i %= n; return i < 0 ? i + n : i; }
 
 __device__ __forceinline__ Img image(const Prob& P, int i, int j) {
-  Img r{i, j, 1, 1, 0};
+  Img r{i, j, 1, 1, 0, -1};
+  if (j < 0 || j >= P.ny) {
+    const int side = j < 0 ? 2 : 3;
+    if (P.fixtab) {
+      const int e = side * P.fixlen + i + 1;
+      if (P.fixtab[4 * e] > 0.0) { r.fs = e; return r; }
+    }
+    const int k = P.bc[side];
+    if (k == BC_PERIODIC) r.j = wrap(j, P.ny);
+    else { r.j = j < 0 ? -1 - j : 2 * P.ny - 1 - j; r.sy = -1; if (k == BC_REFLECTIVE) r.neg |= 4; }
+  }
+  if (i < 0 || i >= P.nx) {
+    const int side = i < 0 ? 0 : 1;
+    if (P.fixtab) {
+      const int e = side * P.fixlen + r.j + 1;
+      if (P.fixtab[4 * e] > 0.0) { r.fs = e; return r; }
+    }
+    const int k = P.bc[side];
+    if (k == BC_PERIODIC) r.i = wrap(i, P.nx);
+    else { r.i = i < 0 ? -1 - i : 2 * P.nx - 1 - i; r.sx = -1; if (k == BC_REFLECTIVE) r.neg |= 2; }
+  }
+  return r;
+}
+
+// The image by the sides' kinds alone (fixed states ignored; an inflow side
+// maps like a transmissive one).  Separable in x and y; equal to image() for
+// every cell image() does not make a fixed-state ghost.
+__device__ __forceinline__ Img image_kind(const Prob& P, int i, int j) {
+  Img r{i, j, 1, 1, 0, -1};
   if (i < 0 || i >= P.nx) {
     const int k = P.bc[i < 0 ? 0 : 1];
     if (k == BC_PERIODIC) r.i = wrap(i, P.nx);
@@ -106,11 +145,22 @@ __device__ __forceinline__ Img image(const Prob& P, int i, int j) {
   return r;
 }
 
+// Variable v of a fixed-state ghost (its average and every point value)
+__device__ __forceinline__ double fixed_val(const Prob& P, const Img& m, int v) {
+  return ((m.neg >> v) & 1 ? -1.0 : 1.0) * P.fixtab[4 * m.fs + v];
+}
+
 // Sign of variable v of an image cell (reflective walls)
 __device__ __forceinline__ int vsign(const Img& m, int v) { return (m.neg >> v) & 1 ? -1 : 1; }
 
 __device__ __forceinline__ long long sidx(const Prob& P, int var, int mom, int i, int j) {
   return (long long)(var * P.nmom + mom) * P.plane + (long long)j * P.pitch + i;
+}
+
+// Cell average of variable v of an image cell, fixed-state ghosts included.
+__device__ __forceinline__ double avg_img(const Prob& P, const double* __restrict__ U, const Img& m, int v) {
+  if (m.fs >= 0) return fixed_val(P, m, v);
+  return vsign(m, v) * U[sidx(P, v, 0, m.i, m.j)];
 }
 
 // ---------------------------------------------------------------- physics
@@ -447,33 +497,40 @@ __device__ __forceinline__ T kxrcf2d(const Prob& P, const Weights<T>& W, const T
   const long long o = goff(P, i, j);
   const Img L = image(P, i - 1, j), R = image(P, i + 1, j), Bo = image(P, i, j - 1), Tp = image(P, i, j + 1);
   const long long oL = goff(P, L.i, L.j), oR = goff(P, R.i, R.j), oB = goff(P, Bo.i, Bo.j), oT = goff(P, Tp.i, Tp.j);
-  // the neighbours' face velocities (the x ones negated through an x wall, the y ones through a y wall)
-  const T axl = aux[(L.sx < 0 ? 0 : 1) * P.gplane + oL], axr = aux[(R.sx < 0 ? 1 : 0) * P.gplane + oR];
-  const T ayb = aux[(Bo.sy < 0 ? 2 : 3) * P.gplane + oB], ayt = aux[(Tp.sy < 0 ? 3 : 2) * P.gplane + oT];
+  // the neighbours' face velocities (the x ones negated through an x wall, the y
+  // ones through a y wall); a fixed-state ghost's is its own state's velocity
+  const T axl = L.fs >= 0 ? from_double<T>(P.fixtab[4 * L.fs + 1] / P.fixtab[4 * L.fs]) : aux[(L.sx < 0 ? 0 : 1) * P.gplane + oL];
+  const T axr = R.fs >= 0 ? from_double<T>(P.fixtab[4 * R.fs + 1] / P.fixtab[4 * R.fs]) : aux[(R.sx < 0 ? 1 : 0) * P.gplane + oR];
+  const T ayb = Bo.fs >= 0 ? from_double<T>(P.fixtab[4 * Bo.fs + 2] / P.fixtab[4 * Bo.fs]) : aux[(Bo.sy < 0 ? 2 : 3) * P.gplane + oB];
+  const T ayt = Tp.fs >= 0 ? from_double<T>(P.fixtab[4 * Tp.fs + 2] / P.fixtab[4 * Tp.fs]) : aux[(Tp.sy < 0 ? 3 : 2) * P.gplane + oT];
   const T vxl = T(0.5) * ((L.neg & 2 ? -axl : axl) + aux[0 * P.gplane + o]);
   const T vxr = T(0.5) * (aux[1 * P.gplane + o] + (R.neg & 2 ? -axr : axr));
   const T vyb = T(0.5) * ((Bo.neg & 4 ? -ayb : ayb) + aux[2 * P.gplane + o]);
   const T vyt = T(0.5) * (aux[3 * P.gplane + o] + (Tp.neg & 4 ? -ayt : ayt));
+  // the indicator variable (density) of a neighbour at its point (k, l)
+  auto rho_at = [&](const Img& m, long long om, int k, int l) -> T {
+    return m.fs >= 0 ? from_double<T>(P.fixtab[4 * m.fs]) : G[(long long)mpt(m, k, l) * P.gplane + om];
+  };
   const T dx = T(P.dx), dy = T(P.dy);
   T s = T(0), len = T(0);
   if (vxl > T(KX_VDEAD)) {
 #pragma unroll
-    for (int l = 0; l < 4; ++l) s += dy * gl_w<T>(l) * (G[(long long)(l)*P.gplane + o] - G[(long long)mpt(L, 3, l) * P.gplane + oL]);
+    for (int l = 0; l < 4; ++l) s += dy * gl_w<T>(l) * (G[(long long)(l)*P.gplane + o] - rho_at(L, oL, 3, l));
     len += dy;
   }
   if (-vxr > T(KX_VDEAD)) {
 #pragma unroll
-    for (int l = 0; l < 4; ++l) s += dy * gl_w<T>(l) * (G[(long long)(12 + l) * P.gplane + o] - G[(long long)mpt(R, 0, l) * P.gplane + oR]);
+    for (int l = 0; l < 4; ++l) s += dy * gl_w<T>(l) * (G[(long long)(12 + l) * P.gplane + o] - rho_at(R, oR, 0, l));
     len += dy;
   }
   if (vyb > T(KX_VDEAD)) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) s += dx * gl_w<T>(k) * (G[(long long)(k * 4) * P.gplane + o] - G[(long long)mpt(Bo, k, 3) * P.gplane + oB]);
+    for (int k = 0; k < 4; ++k) s += dx * gl_w<T>(k) * (G[(long long)(k * 4) * P.gplane + o] - rho_at(Bo, oB, k, 3));
     len += dx;
   }
   if (-vyt > T(KX_VDEAD)) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) s += dx * gl_w<T>(k) * (G[(long long)(k * 4 + 3) * P.gplane + o] - G[(long long)mpt(Tp, k, 0) * P.gplane + oT]);
+    for (int k = 0; k < 4; ++k) s += dx * gl_w<T>(k) * (G[(long long)(k * 4 + 3) * P.gplane + o] - rho_at(Tp, oT, k, 0));
     len += dx;
   }
   const T nrm = aux[4 * P.gplane + o];
@@ -502,11 +559,11 @@ __device__ __forceinline__ bool tvb_cell(const Prob& P, const double* __restrict
   const double u0 = U[sidx(P, 0, 0, i, j)];
   const Img L = image(P, i - 1, j), R = image(P, i + 1, j);
   const double ax = 6.0 * U[sidx(P, 0, 1, i, j)];
-  if (tvb_changes(ax, U[sidx(P, 0, 0, R.i, R.j)] - u0, u0 - U[sidx(P, 0, 0, L.i, L.j)], bound)) return true;
+  if (tvb_changes(ax, avg_img(P, U, R, 0) - u0, u0 - avg_img(P, U, L, 0), bound)) return true;
   if (P.nmom == 2) return false;
   const Img Bo = image(P, i, j - 1), Tp = image(P, i, j + 1);
   const double ay = 6.0 * U[sidx(P, 0, 2, i, j)];
-  return tvb_changes(ay, U[sidx(P, 0, 0, Tp.i, Tp.j)] - u0, u0 - U[sidx(P, 0, 0, Bo.i, Bo.j)], bound);
+  return tvb_changes(ay, avg_img(P, U, Tp, 0) - u0, u0 - avg_img(P, U, Bo, 0), bound);
 }
 
 }  // namespace hw

@@ -168,4 +168,21 @@ void run_advance_dt(const Prob& P, const double* speeds, const double* par, doub
                     cudaStream_t s);
 void run_totals(const Prob& P, const double* U, double* partials, double* out, cudaStream_t st);
 
+// Fixed-state (inflow) ghost cells of a 2D Euler handle: per side, a segment
+// of ghost positions whose centre coordinate along the side is below
+// c0 + speed * t holds state a; the rest of an inflow side holds b.
+struct FixSpec {
+  int seg[4];             // segment set on the side
+  int inflow[4];          // the side's kind is HWENO_BC_INFLOW
+  int n[4];               // cells along the side (ny on x sides, nx on y sides)
+  double c0[4], speed[4];
+  double a[4][4], b[4][4];
+  double x0, y0, dx, dy;
+  int fixlen;             // table entries per side (positions -1 .. max(nx, ny))
+};
+// Fill the table Prob::fixtab for the stage at time t, or at *tn + c * *dtp
+// read on the device when dtp is set (hweno_advance).
+void run_fixfill(const FixSpec& F, double* tab, double t, const double* tn, const double* dtp, double c,
+                 cudaStream_t st);
+
 }  // namespace hw

@@ -109,8 +109,9 @@ int first_pass_blocks(const Prob& P) {
 // The step length of hweno_advance on the device, from the wave-speed maxima in
 // sp[0..1]: the CFL rule of the host's hweno_max_dt (same expressions), clipped
 // to the remaining time; st[0] = t, st[1] = dt, st[2] = steps taken,
-// par = {T, cfl, max_steps}.  dt = -1 marks a step to skip (done, step budget
-// spent, or a non-physical average, which also sets ST_NONPOSITIVE).
+// st[3] = the time at the start of the step, par = {T, cfl, max_steps}.  dt = -1 marks a step to skip (done, step budget
+// spent, or a non-physical average, which also sets ST_NONPOSITIVE and
+// ST_NODT; the latter fails the call whatever the positivity switch).
 __global__ void advance_dt_kernel(Prob P, const double* __restrict__ sp, const double* __restrict__ par,
                                   double* __restrict__ st, unsigned* __restrict__ status) {
   const double ax = sp[0], ay = sp[1];
@@ -122,9 +123,10 @@ __global__ void advance_dt_kernel(Prob P, const double* __restrict__ sp, const d
     dtc = r > 0.0 ? cfl / r : INFINITY;
   }
   const double t = st[0], rem = T - t;
+  st[3] = t;
   double dt = -1.0;
   if (!(dtc > 0.0) || isnan(dtc)) {
-    atomicOr(status, ST_NONPOSITIVE);
+    atomicOr(status, ST_NONPOSITIVE | ST_NODT);
   } else if (st[2] < maxs && rem > 1e-14 * fmax(1.0, fabs(T))) {
     dt = fmin(dtc, rem);
     st[0] = dtc >= rem ? T : t + dt;
@@ -133,7 +135,38 @@ __global__ void advance_dt_kernel(Prob P, const double* __restrict__ sp, const d
   st[1] = dt;
 }
 
+// Fixed-state ghost table for the stage at time t (or, with dtp set, at
+// *tn + c * *dtp read on the device; a skipped step, *dtp < 0, leaves it).
+// Products and sums are rounded separately (no fused multiply-add), as the
+// host computes the same positions and times.
+__global__ void fixfill_kernel(FixSpec F, double* __restrict__ tab, double t, const double* __restrict__ tn,
+                               const double* __restrict__ dtp, double c) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= 4 * F.fixlen) return;
+  if (dtp) {
+    const double dt = *dtp;
+    if (dt < 0.0) return;
+    t = __dadd_rn(*tn, __dmul_rn(c, dt));
+  }
+  const int side = q / F.fixlen, pos = q % F.fixlen - 1;
+  const double at = __dmul_rn((double)pos + 0.5, side < 2 ? F.dy : F.dx);
+  const double pc = __dadd_rn(side < 2 ? F.y0 : F.x0, at);
+  const double* src = nullptr;
+  if (pos <= F.n[side]) {
+    if (F.seg[side] && pc < __dadd_rn(F.c0[side], __dmul_rn(F.speed[side], t))) src = F.a[side];
+    else if (F.inflow[side]) src = F.b[side];
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) tab[4 * (long long)q + v] = src ? src[v] : 0.0;
+}
+
 }  // namespace
+
+void run_fixfill(const FixSpec& F, double* tab, double t, const double* tn, const double* dtp, double c,
+                 cudaStream_t st) {
+  const int n = 4 * F.fixlen;
+  fixfill_kernel<<<(n + 127) / 128, 128, 0, st>>>(F, tab, t, tn, dtp, c);
+}
 
 void run_advance_dt(const Prob& P, const double* speeds, const double* par, double* st, unsigned* status,
                     cudaStream_t s) {

@@ -20,7 +20,7 @@ ENONPHYSICAL = -3
 STATUS = {0: "OK", -1: "EINVAL", -2: "ECUDA", -3: "ENONPHYSICAL", -4: "ETIMEOUT", -5: "ESTATE", -6: "ENOMEM"}
 EQ = {"advection": 0, "burgers": 1, "euler": 2}
 IND = {"none": 0, "kxrcf": 1, "all": 2, "mlp": 3, "tvb": 4}
-BC = {"periodic": 0, "transmissive": 1, "reflective": 2}
+BC = {"periodic": 0, "transmissive": 1, "reflective": 2, "inflow": 3}
 PREC = {"fp64": 0, "fp32": 1, "df64": 2}
 
 
@@ -36,6 +36,11 @@ class Grid(ctypes.Structure):
                 ("eq", ctypes.c_int), ("adv_a", ctypes.c_double), ("adv_b", ctypes.c_double),
                 ("precision", ctypes.c_int), ("indicator", ctypes.c_int), ("gamma_bar", ctypes.c_double * 4),
                 ("beta_of_q", ctypes.c_int), ("tvb_m", ctypes.c_double), ("charwise", ctypes.c_int)]
+
+
+class FixedState(ctypes.Structure):
+    _fields_ = [("segment", ctypes.c_int), ("c0", ctypes.c_double), ("speed", ctypes.c_double),
+                ("a", ctypes.c_double * 4), ("b", ctypes.c_double * 4)]
 
 
 class Bc(ctypes.Structure):
@@ -89,6 +94,9 @@ def lib():
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
         L.hweno_rerecon_count.argtypes = [H, ctypes.POINTER(ctypes.c_longlong)]
         L.hweno_set_positivity_check.argtypes = [H, ctypes.c_int]
+        L.hweno_set_fixed_state.argtypes = [H, ctypes.c_int, ctypes.POINTER(FixedState)]
+        L.hweno_set_time.argtypes = [H, ctypes.c_double]
+        L.hweno_get_time.argtypes = [H, D]
         L.hweno_last_error.argtypes = [H]
         L.hweno_last_error.restype = ctypes.c_char_p
         L.hweno_version.restype = ctypes.c_int
@@ -151,7 +159,32 @@ class Solver:
 
     @classmethod
     def from_problem(cls, p, **kw):
-        return cls(p.dim, p.nx, p.ny, p.x0, p.x1, p.y0, p.y1, eq=p.eq, adv=p.adv, bc=p.bc, gamma=p.gamma, **kw)
+        s = cls(p.dim, p.nx, p.ny, p.x0, p.x1, p.y0, p.y1, eq=p.eq, adv=p.adv, bc=p.bc, gamma=p.gamma, **kw)
+        for side, f in enumerate(p.fixed or ()):
+            if f:
+                s.set_fixed_state(side, **f)
+        return s
+
+    def set_fixed_state(self, side, a=None, b=None, c0=None, speed=0.0):
+        """Fixed ghost states of one side (0 x-lo, 1 x-hi, 2 y-lo, 3 y-hi): a inside
+        the segment (centre coordinate along the side below c0 + speed * t; no
+        segment when c0 is None), b elsewhere on an "inflow" side."""
+        f = FixedState()
+        f.segment = int(c0 is not None)
+        f.c0 = float(c0 if c0 is not None else 0.0)
+        f.speed = float(speed)
+        for v in range(4):
+            f.a[v] = float(a[v]) if a is not None else 0.0
+            f.b[v] = float(b[v]) if b is not None else 0.0
+        self._check(lib().hweno_set_fixed_state(self._h, int(side), ctypes.byref(f)))
+
+    def set_time(self, t):
+        self._check(lib().hweno_set_time(self._h, float(t)))
+
+    def time(self):
+        v = ctypes.c_double()
+        self._check(lib().hweno_get_time(self._h, ctypes.byref(v)))
+        return v.value
 
     def _check(self, st):
         if st != 0:

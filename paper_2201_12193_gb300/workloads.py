@@ -43,6 +43,7 @@ class Problem:
     t_end: float = 0.0
     seed: int | None = None
     meta: dict = dataclasses.field(default_factory=dict)
+    fixed: tuple | None = None   # per side: None or dict(a=, b=, c0=, speed=) of fixed ghost states
 
     @property
     def dx(self):
@@ -286,6 +287,34 @@ def blast_2d(n=4096, seed=0, ncircles=8):
     return Problem("blast_2d", 2, n, n, 0.0, 1.0, 0.0, 1.0, "euler", ("transmissive",) * 4, m,
                    seed=seed, meta={"cx": cx.tolist(), "cy": cy.tolist(), "r": rad.tolist(),
                                     "p_in": pin.tolist()})
+
+
+def double_mach_2d(ny=400):
+    """Example 3.9, double Mach reflection: [0,4] x [0,1] (4 ny x ny square
+    cells), a Mach 10 shock at 60 degrees to the x-axis through (1/6, 0).
+    Post-shock (rho, u, v, p) = (8, 8.25 cos 30, -8.25 sin 30, 116.5), pre-shock
+    (1.4, 0, 0, 1).  Boundaries: inflow of the post-shock state on the left,
+    outflow (transmissive) on the right; on the floor the post-shock state
+    before x = 1/6 and a reflective wall after it; on the top the exact shock
+    trace: ghost cells (centre height 1 + dy/2) hold the post-shock state left
+    of x = 1/6 + (1 + dy/2 + 20 t)/sqrt(3), the pre-shock state right of it.
+    Cell moments of the initial discontinuity by 8 x 8 Gauss-Legendre points.
+    To t = 0.2."""
+    nx = 4 * ny
+    s3 = math.sqrt(3.0)
+    post = prim_to_cons_2d(8.0, 8.25 * s3 / 2.0, -8.25 * 0.5, 116.5)
+    pre = prim_to_cons_2d(1.4, 0.0, 0.0, 1.0)
+
+    def f(X, Y):
+        left = X < 1.0 / 6.0 + Y / s3
+        return np.stack([np.where(left, post[v], pre[v]) for v in range(4)])
+    m = moments_2d(f, 0.0, 4.0, 0.0, 1.0, nx, ny)
+    dy = 1.0 / ny
+    post_t, pre_t = tuple(float(x) for x in post), tuple(float(x) for x in pre)
+    fixed = ({"b": post_t}, None, {"a": post_t, "c0": 1.0 / 6.0},
+             {"a": post_t, "b": pre_t, "c0": 1.0 / 6.0 + (1.0 + 0.5 * dy) / s3, "speed": 20.0 / s3})
+    return Problem("double_mach_2d", 2, nx, ny, 0.0, 4.0, 0.0, 1.0, "euler",
+                   ("inflow", "transmissive", "reflective", "inflow"), m, t_end=0.2, fixed=fixed)
 
 
 def batch_sizes(seed=0, count=256, choices=(64, 128, 256, 512)):

@@ -36,7 +36,8 @@ def rel_l1(a, b):
 
 
 def cfg_of(orc, p, **kw):
-    return orc.make_cfg(p.dim, p.nx, p.ny, dx=p.dx, dy=p.dy, eq=p.eq, adv=p.adv, gamma=p.gamma, bc=p.bc, **kw)
+    return orc.make_cfg(p.dim, p.nx, p.ny, dx=p.dx, dy=p.dy, eq=p.eq, adv=p.adv, gamma=p.gamma, bc=p.bc,
+                        x0=p.x0, y0=p.y0, fixed=p.fixed, **kw)
 
 
 def solver_of(p, **kw):
@@ -305,6 +306,22 @@ def test_nonphysical_step_rolls_back():
     s.close()
 
 
+def test_advance_without_a_step_length_fails_with_the_check_off():
+    """A cell with rho <= 0 leaves no CFL step length: hweno_advance reports it
+    (ENONPHYSICAL) whatever the positivity switch, instead of returning short."""
+    p = W.sod_1d(64)
+    m = p.m.copy()
+    m[0, 0, 0, 30] = -0.5
+    for check in (True, False):
+        s = solver_of(p)
+        s.set_positivity_check(check)
+        s.set_moments(m)
+        with pytest.raises(hweno.HwenoError) as e:
+            s.advance(0.1, 0.6)
+        assert e.value.status == -3
+        s.close()
+
+
 # ------------------------------------------------------------------ double-float precision
 
 @pytest.mark.parametrize("name,make", [
@@ -557,3 +574,123 @@ def test_charwise_rejected_outside_1d_euler():
         solver_of(W.four_quadrant_2d(16, seed=1), charwise=True)
     with pytest.raises(Exception):
         solver_of(W.burgers_1d(32), charwise=True)
+
+
+# ------------------------------------------------------------------ fixed-state (inflow) boundaries
+
+def _mirror_inflow():
+    """Left inflow with a segment (its y momentum reversed below y = 0),
+    transmissive elsewhere, on [0, 10/12] x [-1, 1]: the corner and segment
+    paths of the ghost-cell rules."""
+    nx, ny = 10, 12
+    h = 1.0 / 6
+    rng = np.random.default_rng(7)
+    X, Y = np.meshgrid((np.arange(nx) + 0.5) * h, -1.0 + (np.arange(ny) + 0.5) * h)
+    m = np.zeros((4, 3, ny, nx))
+    m[:, 0] = W.prim_to_cons_2d(1.0 + 0.2 * np.sin(2 * X + Y), 0.6 + 0.1 * np.cos(X - Y), 0.2 + 0.1 * np.sin(3 * Y),
+                                1.0 + 0.2 * np.cos(2 * Y))
+    m[:, 1:] = 0.01 * rng.standard_normal((4, 2, ny, nx))
+    s = tuple(float(x) for x in W.prim_to_cons_2d(1.4, 0.8, 0.3, 1.1))
+    return W.Problem("mirror_inflow", 2, nx, ny, 0.0, nx * h, -1.0, 1.0, "euler",
+                     ("inflow", "transmissive", "transmissive", "transmissive"), m,
+                     fixed=({"a": (s[0], s[1], -s[2], s[3]), "b": s, "c0": 0.0}, None, None, None))
+
+
+INFLOW = [("double_mach", lambda: W.double_mach_2d(12)), ("mirror_inflow", _mirror_inflow)]
+
+
+@pytest.mark.parametrize("name,make", INFLOW, ids=[n for n, _ in INFLOW])
+@pytest.mark.parametrize("indicator", ["kxrcf", "none", "all", "tvb"])
+@pytest.mark.parametrize("t", [0.0, 0.013])
+def test_inflow_rhs_parity(orc, name, make, indicator, t):
+    p = make()
+    kw = {"tvb_m": 1.0} if indicator == "tvb" else {}
+    s = solver_of(p, indicator=indicator, **kw)
+    s.set_moments(p.m)
+    s.set_time(t)
+    Um_g, L_g, mask_g, aleph_g = gpu_rhs(s, p.m)
+    Um_o, L_o, mask_o, aleph_o, rc = orc.rhs(cfg_of(orc, p, indicator=indicator, t=t, **kw), p.m)
+    assert rc == 0 and not (np.abs(aleph_o - 1.0) < 1e-10).any()
+    assert np.array_equal(mask_g, mask_o), (int(mask_g.sum()), int(mask_o.sum()))
+    assert rel_l1(Um_g, Um_o) <= TOL
+    assert np.abs(L_g - L_o).sum() <= 1e-11 * np.abs(L_o).sum() + 1e-9 * L_o.size, rel_l1(L_g, L_o)
+    if indicator == "kxrcf":
+        np.testing.assert_allclose(aleph_g, aleph_o, rtol=1e-9, atol=1e-9)
+    s.close()
+
+
+def test_inflow_steps_parity(orc):
+    """Ten steps of the double Mach reflection (the top boundary's shock trace
+    moves with the stage times t, t + dt, t + dt/2)."""
+    p = W.double_mach_2d(16)
+    s = solver_of(p)
+    s.set_moments(p.m)
+    cfg = cfg_of(orc, p)
+    m, t = p.m, 0.0
+    for _ in range(10):
+        dt = s.max_dt(0.6)
+        assert math.isclose(dt, orc.max_dt(cfg, m, 0.6), rel_tol=1e-13)
+        s.step(dt)
+        cfg.t = t
+        m, masks, rc = orc.step(cfg, m, dt)
+        assert rc == 0
+        assert np.array_equal(s.troubled_mask().reshape(3, -1), masks)
+        t += dt
+    assert s.time() == t
+    assert rel_l1(s.get_moments(), m) <= TOL
+    s.close()
+
+
+def test_inflow_advance_equals_host_driven_run():
+    """Device-formed stage times (graph replays) against the host loop, bitwise."""
+    p = W.double_mach_2d(16)
+    a = solver_of(p)
+    a.set_moments(p.m)
+    t, n = a.advance(0.03, 0.6)
+    b = solver_of(p)
+    b.set_moments(p.m)
+    nb = b.run(0.03, 0.6)
+    assert n == nb and n > 12
+    assert np.array_equal(a.get_moments(), b.get_moments())
+    assert a.time() == pytest.approx(0.03, rel=1e-14)
+    a.close()
+    b.close()
+
+
+def test_double_mach_run():
+    """Example 3.9 at 400 x 100 with the KXRCF modification, to t = 0.08: the run
+    stays physical, troubled cells lie along the shocks, and on the top row the
+    incident shock sits where the exact trace puts it.  (Further on, at
+    t ~ 0.107, a cell average next to the start of the wall reaches p < 0 with
+    the component-wise reconstruction; the paper shows 1600 x 400 to 0.2.)"""
+    p = W.double_mach_2d(100)
+    s = solver_of(p)
+    s.set_moments(p.m)
+    t_end = 0.08
+    t, n = s.advance(t_end, 0.6)
+    assert t == pytest.approx(t_end, rel=1e-14) and n > 100
+    m = s.get_moments()
+    rho = m[0, 0]
+    pr = 0.4 * (m[3, 0] - 0.5 * (m[1, 0] ** 2 + m[2, 0] ** 2) / rho)
+    assert np.isfinite(m).all() and (rho > 0).all() and (pr > 0).all()
+    mask = s.troubled_mask()[-1].reshape(p.ny, p.nx)
+    assert 0 < mask.mean() < 0.2
+    # top row: post-shock density left of the shock trace, pre-shock right of it
+    xs = 1.0 / 6.0 + (1.0 + 20.0 * t_end) / math.sqrt(3.0)
+    xc = (np.arange(p.nx) + 0.5) * p.dx
+    top = rho[-1]
+    assert np.all(np.abs(top[xc > xs + 0.1] - 1.4) < 1e-6)
+    assert np.all(top[(xc < xs - 0.1) & (xc > xs - 0.5)] > 5.0)
+    s.close()
+
+
+def test_inflow_rejected_where_unsupported():
+    p = W.double_mach_2d(8)
+    for kw in ({"precision": "fp32"}, {"precision": "df64"}, {"indicator": "mlp"}):
+        with pytest.raises(Exception):
+            solver_of(p, **kw)
+    s = hweno.Solver.from_problem(W.Problem(p.name, 2, p.nx, p.ny, p.x0, p.x1, p.y0, p.y1, "euler", p.bc, p.m))
+    s.set_moments(p.m)
+    with pytest.raises(hweno.HwenoError):
+        s.step(1e-4)                                   # inflow sides without states
+    s.close()
