@@ -105,6 +105,7 @@ def lib():
             _lib.orc_phys_flux.argtypes = [C, D, ctypes.c_int, D]
             _lib.orc_totals.argtypes = [C, D, D]
             _lib.orc_set_beta_source.argtypes = [ctypes.c_int]
+            _lib.orc_euler1d_eig.argtypes = [ctypes.c_double, D, D, D]
         return _lib
 
 
@@ -147,6 +148,16 @@ def step(cfg: Cfg, m: np.ndarray, dt: float):
     masks = np.zeros((3, ncell), np.uint8)
     rc = lib().orc_step(ctypes.byref(cfg), _dp(m), float(dt), _u8(masks))
     return m, masks, rc
+
+
+def euler1d_eig(gamma: float, u) -> tuple[np.ndarray, np.ndarray]:
+    """Right (columns) and left (rows) eigenvectors of the 1D Euler flux
+    Jacobian at the conserved state u, as the characteristic option uses them."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    R = np.empty((3, 3))
+    L = np.empty((3, 3))
+    lib().orc_euler1d_eig(float(gamma), _dp(u), _dp(R), _dp(L))
+    return R, L
 
 
 def max_dt(cfg: Cfg, m: np.ndarray, cfl: float = 0.6) -> float:

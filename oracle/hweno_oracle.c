@@ -1113,6 +1113,15 @@ void orc_num_flux(const orc_cfg *c, const double *uL, const double *uR, int dir,
 
 void orc_phys_flux(const orc_cfg *c, const double *u, int dir, double *f) { phys_flux(c, u, dir, f); }
 
+/* 1D Euler eigenvectors used by the characteristic-wise option (R row-major,
+ * columns = right eigenvectors; L row-major, rows = left eigenvectors). */
+void orc_euler1d_eig(double gam, const double *u, double *R, double *L) {
+  double Rm[3][3], Lm[3][3];
+  euler1d_eig(gam, u, Rm, Lm);
+  memcpy(R, Rm, sizeof Rm);
+  memcpy(L, Lm, sizeof Lm);
+}
+
 /* Conservation totals: sum over cells of ubar * dx * dy, per variable. */
 void orc_totals(const orc_cfg *c, const double *m, double *sums) {
   int nv = nvars(c), ny = c->dim == 1 ? 1 : c->ny;

@@ -63,3 +63,25 @@ def test_blast_waves_run_through_with_characteristic_reconstruction(orc):
     rho = m[0, 0, 0]
     assert 5.5 < rho.max() < 6.5 and 0.74 < (np.argmax(rho) + 0.5) / n < 0.80
     assert abs(m[0, 0].sum() - mass0) <= 1e-12 * mass0          # walls: no mass leaves
+
+
+def test_eigenvectors_diagonalise_the_flux_jacobian(orc):
+    """L R = I, and R diag(u - c, u, u + c) L equals the Jacobian of the oracle's
+    own 1D Euler flux by central differences (states at rest, subsonic and
+    supersonic, either direction)."""
+    cfg = orc.make_cfg(1, 8, eq="euler")
+    g = 1.4
+    for rho, mu, p in ((1.0, 0.0, 1.0), (0.3, 0.7, 2.0), (5.0, -3.1, 0.4), (1.2, 4.0, 0.1)):
+        u = np.array(W.prim_to_cons_1d(np.array(rho), np.array(mu), np.array(p)), dtype=np.float64)
+        R, L = orc.euler1d_eig(g, u)
+        np.testing.assert_allclose(L @ R, np.eye(3), atol=1e-13)
+        c = np.sqrt(g * p / rho)
+        A = R @ np.diag([mu - c, mu, mu + c]) @ L
+        J = np.empty((3, 3))
+        for k in range(3):
+            h = 1e-6 * max(1.0, abs(u[k]))
+            up, um = u.copy(), u.copy()
+            up[k] += h
+            um[k] -= h
+            J[:, k] = (orc.phys_flux(cfg, up) - orc.phys_flux(cfg, um)) / (2 * h)
+        np.testing.assert_allclose(A, J, rtol=1e-7, atol=1e-7 * np.abs(J).max())
