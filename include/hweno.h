@@ -247,7 +247,10 @@ hweno_status hweno_mlp_adam(float* params, const float* grad, float* m1, float* 
 
 /* Advance by t_end (>= 0) with the CFL step length (cfl > 0, the rule of
  * hweno_max_dt) computed on the device each step, the last step clipped so that
- * the run ends at t_end exactly, at most max_steps steps.  Steps run in groups
+ * the run ends at t_end exactly, at most max_steps steps.  The solution time
+ * (hweno_get_time) advances with it; moving fixed-state segments read their
+ * stage times on the device.  No CFL step length (rho <= 0 or a non-finite wave
+ * speed) fails the call with ENONPHYSICAL whatever the positivity switch.  Steps run in groups
  * of 12 replayed from a CUDA graph (no host round trip per step); steps left
  * over in the last group once t_end or max_steps is reached are skipped (the
  * state passes through unchanged).  Writes the time reached and the steps taken
