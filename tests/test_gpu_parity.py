@@ -684,6 +684,30 @@ def test_double_mach_run():
     s.close()
 
 
+def test_double_mach_without_modification_runs_through():
+    """Example 3.9 at 400 x 100 to t = 0.2 without the modification (HWENO6):
+    physical throughout; the incident shock on the top row within three cells of
+    the exact trace, the Mach stem on the floor near x = 2.8, the pre-shock gas
+    ahead of the shock untouched."""
+    p = W.double_mach_2d(100)
+    s = solver_of(p, indicator="none")
+    s.set_moments(p.m)
+    t, n = s.advance(p.t_end, 0.6)
+    assert t == pytest.approx(0.2, rel=1e-14) and n > 300
+    m = s.get_moments()
+    rho = m[0, 0]
+    pr = 0.4 * (m[3, 0] - 0.5 * (m[1, 0] ** 2 + m[2, 0] ** 2) / rho)
+    assert np.isfinite(m).all() and (rho > 0).all() and (pr > 0).all()
+    xc = (np.arange(p.nx) + 0.5) * p.dx
+    xs = 1.0 / 6.0 + (1.0 + 20.0 * 0.2) / math.sqrt(3.0)
+    drop = xc[np.argmax(rho[-1] < 0.5 * (8.0 + 1.4))]
+    assert abs(drop - xs) < 3 * p.dx
+    stem = xc[np.nonzero(rho[0] > 3.0)[0].max()]
+    assert 2.6 < stem < 3.0
+    assert np.abs(rho[:, xc > xs + 0.15] - 1.4).max() < 1e-6
+    s.close()
+
+
 def test_inflow_rejected_where_unsupported():
     p = W.double_mach_2d(8)
     for kw in ({"precision": "fp32"}, {"precision": "df64"}, {"indicator": "mlp"}):
