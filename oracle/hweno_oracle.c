@@ -66,6 +66,9 @@ typedef struct {
   int seg_on[4];
   double seg_c0[4], seg_speed[4];
   double fa[4][4], fb[4][4];
+  int mod_in_L_only; /* 1: the modified first moments serve L only; the Runge-Kutta
+                        combination takes the unmodified stage states (reading B
+                        of the modification's persistence) */
 } orc_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -969,16 +972,21 @@ int orc_step(const orc_cfg *c, double *m, double dt, unsigned char *masks) {
   /* stage times t, t + dt, t + dt/2 (the abscissae of the scheme) for
    * time-dependent boundaries */
   orc_cfg cs = *c;
+  /* Un / Um: the stage states the combination takes: modified (default) or,
+   * with mod_in_L_only, as they entered the stage */
   int rc = orc_rhs(&cs, m, Un, L, masks ? masks : NULL, NULL);
+  if (c->mod_in_L_only) memcpy(Un, m, n * sizeof(double));
   if (rc == ORC_OK) {
     for (size_t t = 0; t < n; ++t) U1[t] = Un[t] + dt * L[t];
     cs.t = c->t + dt;
     rc = orc_rhs(&cs, U1, Um, L, masks ? masks + nc : NULL, NULL);
+    if (c->mod_in_L_only) memcpy(Um, U1, n * sizeof(double));
   }
   if (rc == ORC_OK) {
     for (size_t t = 0; t < n; ++t) U2[t] = 0.75 * Un[t] + 0.25 * Um[t] + 0.25 * dt * L[t];
     cs.t = c->t + 0.5 * dt;
     rc = orc_rhs(&cs, U2, Um, L, masks ? masks + 2 * nc : NULL, NULL);
+    if (c->mod_in_L_only) memcpy(Um, U2, n * sizeof(double));
   }
   if (rc == ORC_OK) {
     for (size_t t = 0; t < n; ++t) U1[t] = Un[t] / 3.0 + 2.0 / 3.0 * Um[t] + 2.0 / 3.0 * dt * L[t];

@@ -156,3 +156,29 @@ def test_double_mach_first_steps(orc):
         t += dt
     assert np.isfinite(m).all() and (m[0, 0] > 0).all()
     assert m[0, 0].sum() > mass0          # post-shock gas flows in from the left and the floor
+
+
+def test_modification_in_L_only_variant(orc):
+    """The oracle's mod_in_L_only switch (the modified first moments serve L
+    only; the Runge-Kutta combination takes the stage states as they entered):
+    a step equals three right-hand sides combined with the unmodified states;
+    it equals the default step when no cell is troubled and differs when some
+    are."""
+    p = W.four_quadrant_2d(24, seed=2, ny=20)
+    kw = dict(dx=p.dx, dy=p.dy, bc=p.bc)
+    dt = 0.2 * orc.max_dt(orc.make_cfg(2, p.nx, p.ny, **kw), p.m, 0.6)
+    cB = orc.make_cfg(2, p.nx, p.ny, mod_in_L_only=True, **kw)
+    got, masks, rc = orc.step(cB, p.m, dt)
+    assert rc == 0 and masks.sum() > 0
+    _, L0, _, _, _ = orc.rhs(cB, p.m)
+    U1 = p.m + dt * L0
+    _, L1, _, _, _ = orc.rhs(cB, U1)
+    U2 = 0.75 * p.m + 0.25 * U1 + 0.25 * dt * L1
+    _, L2, _, _, _ = orc.rhs(cB, U2)
+    want = p.m / 3.0 + 2.0 / 3.0 * U2 + 2.0 / 3.0 * dt * L2
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-13 * np.abs(want).max())
+    default, _, _ = orc.step(orc.make_cfg(2, p.nx, p.ny, **kw), p.m, dt)
+    assert np.abs(default - got).max() > 1e-8
+    a, _, _ = orc.step(orc.make_cfg(2, p.nx, p.ny, indicator="none", mod_in_L_only=True, **kw), p.m, dt)
+    b, _, _ = orc.step(orc.make_cfg(2, p.nx, p.ny, indicator="none", **kw), p.m, dt)
+    np.testing.assert_array_equal(a, b)
