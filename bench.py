@@ -7,11 +7,14 @@ One bench step = one whole pass of the hot path: the CFL wave-speed reduction
 (hweno_max_dt) and one SSP-RK3 step (hweno_step: three stages of reconstruct,
 indicator + modification, troubled re-reconstruction, fluxes + quadrature +
 update).  value = cells * 3 stages * steps / device time, FP64 (the scheme as
-specified).  Under "forms": the FP32-bulk form (relative L1 difference to FP64),
-the batched form (256 problems of uneven size, one persistent launch per stage,
-CUDA graph), and the learned-indicator form on 4096^2 blast data against the
-plain scheme on the same data (throughputs, network roofline, recall / miss /
-false-alarm rates against KXRCF, L1 drift).
+specified).  Under "forms": the FP32-bulk and double-float forms (relative L1
+difference to FP64), the 1D Shu-Osher problem run whole (device-driven against
+the host loop; FP32-bulk and double-float beside FP64 with the N = 4000 vs 8000
+resolution gap), the batched form (256 problems of uneven size, one persistent
+launch per stage, CUDA graph), and the learned-indicator form on 4096^2 blast
+data against the plain scheme on the same data (throughputs, network roofline,
+recall / miss / false-alarm rates against KXRCF, L1 drift).  --full-run adds the
+2048^2 problem run whole to t = 0.25 in FP64 and FP32-bulk.
 
 Multi-GPU (torchrun): each rank advances its own independently seeded problem
 (weak scaling, no data-path collective); the timing barrier and the max over
