@@ -182,3 +182,25 @@ def test_modification_in_L_only_variant(orc):
     a, _, _ = orc.step(orc.make_cfg(2, p.nx, p.ny, indicator="none", mod_in_L_only=True, **kw), p.m, dt)
     b, _, _ = orc.step(orc.make_cfg(2, p.nx, p.ny, indicator="none", **kw), p.m, dt)
     np.testing.assert_array_equal(a, b)
+
+
+def test_double_mach_initial_data():
+    """The Example 3.9 input: total mass against the exact area left of the
+    shock line x = 1/6 + y/sqrt(3) (area 1/6 + 1/(2 sqrt 3) of [0,4] x [0,1]),
+    the two states far from the line, the post-shock state's Mach 10 shock
+    relation (mass flux continuity across a shock moving at speed 10 normal to
+    itself), and the top segment's trace at the ghost centre height."""
+    ny = 50
+    p = W.double_mach_2d(ny)
+    s3 = math.sqrt(3.0)
+    area_left = 1.0 / 6.0 + 1.0 / (2.0 * s3)
+    mass = p.m[0, 0].sum() * p.dx * p.dy
+    exact = 8.0 * area_left + 1.4 * (4.0 - area_left)
+    assert abs(mass - exact) < 1e-3 * exact
+    assert abs(p.m[0, 0, 10, 0] - 8.0) < 1e-12 and abs(p.m[0, 0, 10, -1] - 1.4) < 1e-12
+    post = p.fixed[0]["b"]
+    rho, un = post[0], (post[1] * s3 / 2.0 - post[2] * 0.5) / post[0]      # velocity normal to the shock
+    assert abs(rho * (10.0 - un) - 1.4 * 10.0) < 1e-9 * 14.0             # mass flux in the shock frame
+    top = p.fixed[3]
+    assert top["c0"] == pytest.approx(1.0 / 6.0 + (1.0 + 0.5 / ny) / s3, rel=1e-15)
+    assert top["speed"] == pytest.approx(20.0 / s3, rel=1e-15)
