@@ -672,6 +672,7 @@ hweno_status hweno_set_fixed_state(hweno_t h, int side, const hweno_fixed_state*
     for (int s = 0; s < 4; ++s) F.inflow[s] = kinds[s] == HWENO_BC_INFLOW;
     CK(h, cudaMalloc(&h->fixtab, 16 * (size_t)F.fixlen * sizeof(double)));
     CK(h, cudaMemsetAsync(h->fixtab, 0, 16 * (size_t)F.fixlen * sizeof(double), h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));   // done before any later stream fills the table
     h->P.fixtab = h->fixtab;
     h->P.fixlen = F.fixlen;
   }
