@@ -26,7 +26,14 @@
  *   - HLLC flux eqs. (f_HLLC), (COEF), (uLR_); Gauss-Lobatto quadrature
  *     eqs. (F), (integral1)-(integral3); semi-discrete forms eqs.
  *     (1D-equ-int-approximation), (2D-equ-int-approximation);
- *   - SSP Runge-Kutta eq. (Runge-Kutta).
+ *   - SSP Runge-Kutta eq. (Runge-Kutta), stages at t, t + dt, t + dt/2.
+ *
+ * Options beyond the paper's defaults, each pinned by the tests: the TVB
+ * indicator of Remark 2 (indicator 4), given decisions (indicator 3, the
+ * learned indicator's order), reflective walls and fixed-state ghost cells
+ * with moving segments (Examples 3.7, 3.9), characteristic-wise
+ * reconstruction for 1D Euler, and the modified first moments used in L
+ * only (mod_in_L_only).
  *
  * Readings of points the paper leaves open (each one also used by the GPU
  * path) are marked "Reading:" where they are applied.
