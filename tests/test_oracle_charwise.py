@@ -108,3 +108,24 @@ def test_charwise_shock_tubes_converge_to_exact_riemann(orc, name):
         errs[cw] = e
     assert errs[True][1] < 0.85 * errs[True][0], errs
     assert errs[True][1] < 1.25 * errs[False][1], errs
+
+
+def test_modification_in_L_only_runs_the_blast_waves_through(orc):
+    """Component-wise, Example 3.7 stops at the collision (t ~ 0.028) when the
+    modified first moments persist in the state (the default reading), and runs
+    to t = 0.038 with them used inside L only (mod_in_L_only)."""
+    p = W.blast_wave_1d(400)
+    reached = {}
+    for b in (False, True):
+        cfg = orc.make_cfg(1, 400, dx=p.dx, eq="euler", bc=p.bc, mod_in_L_only=b)
+        m, t = p.m.copy(), 0.0
+        while t < p.t_end - 1e-14:
+            dt = min(orc.max_dt(cfg, m, 0.6), p.t_end - t)
+            if not (np.isfinite(dt) and dt > 0):
+                break
+            m, _, rc = orc.step(cfg, m, dt)
+            if rc != 0:
+                break
+            t += dt
+        reached[b] = t
+    assert reached[False] < 0.03 and reached[True] == pytest.approx(p.t_end, rel=1e-12), reached
