@@ -125,7 +125,14 @@ def _f64(x):
 
 
 class Solver:
-    """One problem on the GPU; method names follow the C ABI (hweno_*)."""
+    """One problem on the GPU; method names follow the C ABI (hweno_*).
+
+    precision: "fp64" (the scheme as specified), "fp32" (FP32 bulk, FP64 state and
+    Runge-Kutta accumulation) or "df64" (double-float pairs); indicator: "kxrcf",
+    "none", "all", "tvb" (with tvb_m) or "mlp" (with set_mlp); bc per side:
+    "periodic", "transmissive", "reflective" (Euler) or "inflow" (2D Euler FP64,
+    states by set_fixed_state); charwise: characteristic-wise reconstruction
+    (1D Euler)."""
 
     def __init__(self, dim, nx, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, eq="euler", adv=(1.0, 0.0),
                  precision="fp64", indicator="kxrcf", gamma_bar=(1.0, 10.0, 100.0, 1000.0), beta_of_q=False,
