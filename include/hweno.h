@@ -170,8 +170,9 @@ hweno_status hweno_get_time(hweno_t h, double* t);
 hweno_status hweno_get_moments(hweno_t h, double* m, size_t count, int on_device);
 
 /* One SSP-RK3 step of size dt (three stages, eq. (Runge-Kutta)); asynchronous.
- * Reading: the first moments modified in troubled cells replace the stage
- * input and enter the Runge-Kutta combination. */
+ * Reading (default, hweno_set_persistence): the first moments modified in
+ * troubled cells replace the stage input and enter the Runge-Kutta
+ * combination. */
 hweno_status hweno_step(hweno_t h, double dt);
 
 /* dt for the next step from the cell averages (CFL rule of Sec. 3, formula not
@@ -270,6 +271,16 @@ hweno_status hweno_advance(hweno_t h, double t_end, double cfl, long long max_st
  * does).  Applies to single and batch handles. */
 hweno_status hweno_set_positivity_check(hweno_t h, int on);
 
+/* How the first moments modified by eq. (vi) in troubled cells (Step 2.2) are
+ * used; the paper does not say.  persist = 1 (default): they replace the
+ * stage input, so the Runge-Kutta combination of eq. (Runge-Kutta) takes them
+ * (stage 1 also modifies U^n); this reproduces Table 1's HWENO6-M5-NI errors
+ * (Sec. 3, Example 3.1).  persist = 0: they serve the evaluation of L only and
+ * the combination takes the stage states as they entered the stage.
+ * hweno_rhs is unaffected (its Umod output holds the modified moments either
+ * way).  EINVAL for other values.  Single and batch handles. */
+hweno_status hweno_set_persistence(hweno_t h, int persist);
+
 /* Troubled re-reconstruction work (Step 2.3): the number of cells reconstructed
  * a second time, from modified moments, since the last call (then reset to 0).
  * Single-problem handles; synchronises the handle's stream.  No counterpart in
@@ -304,6 +315,15 @@ hweno_status hweno_step_batch(hweno_t h, const double* dt_device, double cfl);
 hweno_status hweno_batch_dt(hweno_t h, double* dt, int n);
 hweno_status hweno_batch_troubled_mask(hweno_t h, int k, unsigned char* mask, size_t count);
 hweno_status hweno_batch_set_tile(hweno_t h, int variant);
+/* Bound of the grid barrier's waits (no counterpart in the paper): a wait
+ * gives up after spin_limit polls (64 ns sleeps each; default 2^26, seconds),
+ * sets HWENO_ETIMEOUT for the next synchronising call (which rolls the step
+ * back) and lets the block continue, so no wait can hang the GPU.
+ * extra_arrivals (0 normally, at most 1024) makes every barrier wait for that
+ * many arrivals beyond the launched blocks, so every wait runs out: the way to
+ * exercise the timeout path without faulting anything.  Takes effect from the
+ * next hweno_step_batch. */
+hweno_status hweno_batch_set_barrier(hweno_t h, long long spin_limit, int extra_arrivals);
 /* 1 if the last batched step was replayed from a captured CUDA graph, 0 if its
  * launches were issued directly (capture unavailable), -1 for a non-batch handle. */
 int hweno_batch_uses_graph(hweno_t h);

@@ -258,8 +258,9 @@ __global__ void __launch_bounds__(UB) update1d_kernel(Prob P, const T* __restric
   }
   const double idx = 1.0 / P.dx;
   const T tidx = T(idx);
-  const bool fk = S.mask[i] != 0;
-  const bool fn = S.maskN && S.maskN[i] != 0;
+  // modified first moments in the combination (persist), and always in the Umod output of Lout
+  const bool fk = S.mask[i] != 0 && (P.persist || S.Lout);
+  const bool fn = P.persist && S.maskN && S.maskN[i] != 0;
   double newavg[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {

@@ -412,8 +412,9 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
   const T tidx = T(idx), tidy = T(idy);
   const long long so = (long long)j * P.pitch + i;
   const long long cell = (long long)j * P.nx + i;
-  const bool fk = S.mask[cell] != 0;
-  const bool fn = S.maskN && S.maskN[cell] != 0;
+  // modified first moments in the combination (persist), and always in the Umod output of Lout
+  const bool fk = S.mask[cell] != 0 && (P.persist || S.Lout);
+  const bool fn = P.persist && S.maskN && S.maskN[cell] != 0;
   double newavg[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
@@ -536,9 +537,9 @@ void stage_t(const Prob& P, const HostTabs& HT, const Weights<T>& W, const Beta2
 // past the limit the block records ST_TIMEOUT and continues (the host reports
 // HWENO_ETIMEOUT), so no wait can hang the GPU.
 
-constexpr unsigned long long BARRIER_SPIN_LIMIT = 1ull << 26;   // x >= 64 ns sleeps: seconds
-
-__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status) {
+// nblocks: arrivals that release the barrier; limit: polls before the wait gives up.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, unsigned* status,
+                                             unsigned long long limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* vgen = bar + 1;
@@ -552,7 +553,7 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned nblocks, un
     } else {
       unsigned long long spins = 0;
       while (*vgen == gen) {
-        if (++spins > BARRIER_SPIN_LIMIT) {
+        if (++spins > limit) {
           atomicOr(status, ST_TIMEOUT);
           break;
         }
@@ -610,7 +611,7 @@ __global__ void __launch_bounds__(TXV * TYV) batch_stage_kernel(BatchStage A, We
         atomicMax(A.speeds + 2 * p + 1, (unsigned long long)__double_as_longlong(sy));
       }
     }
-    grid_barrier(A.bar, nb, A.status);
+    grid_barrier(A.bar, nb + A.bar_extra, A.status, A.spin_limit);
   }
   // Step 1: every cell
   for (int it = blockIdx.x; it < A.n_rec; it += nb) {
@@ -621,7 +622,7 @@ __global__ void __launch_bounds__(TXV * TYV) batch_stage_kernel(BatchStage A, We
       rec2d_cell<T, 4, REC_PLAIN>(Q.P, W, B, A.Uin + Q.uoff, nullptr, nullptr, cell % Q.P.nx, cell / Q.P.nx, G + Q.goff,
                               aux + Q.aoff);
   }
-  grid_barrier(A.bar, nb, A.status);
+  grid_barrier(A.bar, nb + A.bar_extra, A.status, A.spin_limit);
   // Steps 2.1-2.2
   for (int it = blockIdx.x; it < A.n_rec; it += nb) {
     const int p = owner<0>(A.probs, A.nprob, it);
@@ -636,19 +637,21 @@ __global__ void __launch_bounds__(TXV * TYV) batch_stage_kernel(BatchStage A, We
       if (flag) modify2d_cell<4>(Q.P, A.Uin + Q.uoff, A.Mod + Q.moff, i, j);
     }
   }
-  grid_barrier(A.bar, nb, A.status);
+  grid_barrier(A.bar, nb + A.bar_extra, A.status, A.spin_limit);
   // Step 2.3: troubled cells
   {
     const int n = *(volatile int*)A.count;
     for (int t = blockIdx.x * RB + tid; t < n; t += nb * RB) {
       const unsigned long long e = A.list[t];
       const int p = (int)(e >> 32), cell = (int)(e & 0xffffffffu);
+      // after a barrier wait that gave up, an entry may not be written yet
+      if (p < 0 || p >= A.nprob || cell < 0 || cell >= A.probs[p].P.nx * A.probs[p].P.ny) continue;
       const BProb& Q = A.probs[p];
       rec2d_cell<T, 4, REC_FLAGGED>(Q.P, W, B, A.Uin + Q.uoff, A.mask + Q.coff, A.Mod + Q.moff, cell % Q.P.nx,
                              cell / Q.P.nx, G + Q.goff, nullptr);
     }
   }
-  grid_barrier(A.bar, nb, A.status);
+  grid_barrier(A.bar, nb + A.bar_extra, A.status, A.spin_limit);
   // Step 3: fluxes, quadrature, L, Runge-Kutta
   for (int it = blockIdx.x; it < A.n_upd; it += nb) {
     const int p = owner<1>(A.probs, A.nprob, it);

@@ -64,6 +64,8 @@ struct hweno_s {
   double graph_cfl = -1.0;
   int graph_variant = -1;
   bool use_graph = true;
+  unsigned long long spin_limit = hw::BARRIER_SPIN_DEFAULT;   // grid-barrier wait bound
+  unsigned bar_extra = 0;        // extra arrivals the barrier waits for (timeout-path tests)
 };
 
 namespace {
@@ -305,6 +307,7 @@ hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gam
   P.adv_b = h->g.adv_b;
   P.nsm = 152;
   P.positivity = 1;
+  P.persist = 1;
   cudaDeviceGetAttribute(&P.nsm, cudaDevAttrMultiProcessorCount, h->dev);
   h->fp32 = h->g.precision;
   build_tables(h);
@@ -713,6 +716,20 @@ hweno_status hweno_set_positivity_check(hweno_t h, int on) {
   return HWENO_OK;
 }
 
+hweno_status hweno_set_persistence(hweno_t h, int persist) {
+  if (!h) return HWENO_EINVAL;
+  if (persist != 0 && persist != 1) return fail(h, HWENO_EINVAL, "set_persistence: persist must be 0 or 1");
+  h->P.persist = persist;
+  drop_graphs(h);
+  if (h->batch) {
+    for (auto& q : h->probs) q.P.persist = persist;
+    CK(h, cudaMemcpyAsync(h->dprobs, h->probs.data(), h->probs.size() * sizeof(hw::BProb), cudaMemcpyHostToDevice,
+                          h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+  }
+  return HWENO_OK;
+}
+
 hweno_status hweno_rerecon_count(hweno_t h, long long* cells) {
   if (!h || !cells) return HWENO_EINVAL;
   if (h->batch) return fail(h, HWENO_ESTATE, "rerecon_count: single-problem handles only");
@@ -854,7 +871,7 @@ hweno_status hweno_create_batch(const hweno_grid* grids, const hweno_bc* bcs, in
     P.nvar = 4; P.nmom = 3; P.eq = HWENO_EULER; P.indicator = g.indicator; P.tvb_m = g.tvb_m;
     P.bc[0] = bcs[k].xlo; P.bc[1] = bcs[k].xhi; P.bc[2] = bcs[k].ylo; P.bc[3] = bcs[k].yhi;
     P.dx = (g.x1 - g.x0) / P.nx; P.dy = (g.y1 - g.y0) / P.ny;
-    P.gamma = gamma; P.adv_a = 0.0; P.adv_b = 0.0; P.nsm = nsm; P.positivity = 1;
+    P.gamma = gamma; P.adv_a = 0.0; P.adv_b = 0.0; P.nsm = nsm; P.positivity = 1; P.persist = 1;
     q.uoff = tu; q.goff = tg; q.aoff = ta; q.moff = tm; q.coff = tc;
     tu += 12 * P.plane; tg += 64 * P.gplane; ta += 5 * P.gplane; tm += 8 * P.plane; tc += (long long)P.nx * P.ny;
     h->probs.push_back(q);
@@ -891,6 +908,7 @@ hweno_status hweno_create_batch(const hweno_grid* grids, const hweno_bc* bcs, in
   cudaMemset(h->B.status, 0, sizeof(unsigned));
   cudaMemset(h->mask3, 0, 3 * tc);
   cudaMemset(h->bar, 0, 2 * sizeof(unsigned));
+  cudaMemset(h->blist, 0, tc * sizeof(unsigned long long));
   cudaMemset(h->pstatus, 0, n * sizeof(unsigned));
   cudaMemset(h->dt_out, 0, n * sizeof(double));
   for (int k = 0; k < 3; ++k) cudaMemset(h->U[k], 0, tu * sizeof(double));
@@ -969,6 +987,16 @@ hweno_status hweno_batch_dt(hweno_t h, double* dt, int n) {
   return HWENO_OK;
 }
 
+hweno_status hweno_batch_set_barrier(hweno_t h, long long spin_limit, int extra_arrivals) {
+  if (!h || !h->batch) return HWENO_EINVAL;
+  if (spin_limit < 1 || extra_arrivals < 0 || extra_arrivals > 1024)
+    return fail(h, HWENO_EINVAL, "batch_set_barrier: need spin_limit >= 1 and 0 <= extra_arrivals <= 1024");
+  h->spin_limit = (unsigned long long)spin_limit;
+  h->bar_extra = (unsigned)extra_arrivals;
+  drop_graphs(h);
+  return HWENO_OK;
+}
+
 hweno_status hweno_step_batch(hweno_t h, const double* dt_device, double cfl) {
   if (!h || !h->batch) return HWENO_EINVAL;
   if (!h->have_state) return fail(h, HWENO_ESTATE, "step_batch: no moments set");
@@ -1000,6 +1028,7 @@ hweno_status hweno_step_batch(hweno_t h, const double* dt_device, double cfl) {
       S.G = h->B.G; S.aux = h->B.aux; S.list = h->blist; S.count = h->B.count + st;
       S.speeds = h->speeds; S.dt_in = dt_device; S.dt_out = h->dt_out; S.cfl = cfl;
       S.status = h->B.status; S.pstatus = h->pstatus; S.bar = h->bar; S.stage = st;
+      S.spin_limit = h->spin_limit; S.bar_extra = h->bar_extra;
       S.Un = h->U[a];
       if (st == 0) { S.Uin = h->U[a]; S.Uout = h->U[b]; S.cA = 0.0; S.cB = 1.0; S.Mod = h->ModN; S.ModN = nullptr;
                      S.mask = h->mask3; S.maskN = nullptr; }
@@ -1038,7 +1067,8 @@ hweno_status batch_graph(hweno_t h, int a, const double* dt_in, double cfl, cuda
       S.probs = h->dprobs; S.nprob = h->nprob; S.n_rec = h->n_rec; S.n_upd = h->n_upd;
       S.G = h->B.G; S.aux = h->B.aux; S.list = h->blist; S.count = h->B.count + st;
       S.speeds = h->speeds; S.dt_in = dt_in; S.dt_out = h->dt_out; S.cfl = cfl;
-      S.status = h->B.status; S.pstatus = h->pstatus; S.bar = h->bar; S.stage = st; S.Un = h->U[a];
+      S.status = h->B.status; S.pstatus = h->pstatus; S.bar = h->bar; S.stage = st;
+      S.spin_limit = h->spin_limit; S.bar_extra = h->bar_extra; S.Un = h->U[a];
       if (st == 0) { S.Uin = h->U[a]; S.Uout = h->U[b]; S.cA = 0.0; S.cB = 1.0; S.Mod = h->ModN; S.ModN = nullptr;
                      S.mask = h->mask3; S.maskN = nullptr; }
       if (st == 1) { S.Uin = h->U[b]; S.Uout = h->U[c]; S.cA = 0.75; S.cB = 0.25; S.Mod = h->ModK; S.ModN = h->ModN;

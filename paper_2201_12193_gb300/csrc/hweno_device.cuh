@@ -47,6 +47,9 @@ struct Prob {
                           //    states for ghost positions pos in [-1, n] along each side, rho = 0
                           //    where the side's kind applies instead; null: no fixed-state side
   int fixlen;             // entries per side of fixtab
+  int persist;            // 1: the first moments modified in troubled cells (eq. (vi)) replace the
+                          //    stage input and enter the Runge-Kutta combination; 0: they serve
+                          //    L only and the combination takes the stage states as they entered
 };
 
 // Sound speed of a cell average for the CFL rule; +inf marks a non-physical

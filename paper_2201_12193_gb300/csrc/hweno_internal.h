@@ -137,7 +137,13 @@ struct BatchStage {
   unsigned* status;       // ST_TIMEOUT of the grid barrier
   unsigned* pstatus;      // per problem: ST_NONFINITE / ST_NONPOSITIVE of its new state
   unsigned* bar;          // grid barrier {arrived, generation}
+  unsigned long long spin_limit;   // polls (64 ns sleeps each) before a barrier wait gives up
+  unsigned bar_extra;     // arrivals a barrier waits for beyond the launched blocks (0; > 0 only to
+                          //    exercise the timeout path)
 };
+
+// Default bound of a grid-barrier wait: 2^26 polls with 64 ns sleeps, seconds.
+constexpr unsigned long long BARRIER_SPIN_DEFAULT = 1ull << 26;
 
 // Launch one batched stage as a single persistent cooperative kernel (grid =
 // resident blocks); returns the CUDA error of the launch.

@@ -80,6 +80,7 @@ def lib():
         L.hweno_batch_dt.argtypes = [H, D, ctypes.c_int]
         L.hweno_batch_troubled_mask.argtypes = [H, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]
         L.hweno_batch_set_tile.argtypes = [H, ctypes.c_int]
+        L.hweno_batch_set_barrier.argtypes = [H, ctypes.c_longlong, ctypes.c_int]
         L.hweno_batch_uses_graph.argtypes = [H]
         L.hweno_batch_status.argtypes = [H, ctypes.POINTER(ctypes.c_uint), ctypes.c_int]
         L.hweno_mlp_nparam.restype = ctypes.c_int
@@ -94,6 +95,7 @@ def lib():
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]
         L.hweno_rerecon_count.argtypes = [H, ctypes.POINTER(ctypes.c_longlong)]
         L.hweno_set_positivity_check.argtypes = [H, ctypes.c_int]
+        L.hweno_set_persistence.argtypes = [H, ctypes.c_int]
         L.hweno_set_fixed_state.argtypes = [H, ctypes.c_int, ctypes.POINTER(FixedState)]
         L.hweno_set_time.argtypes = [H, ctypes.c_double]
         L.hweno_get_time.argtypes = [H, D]
@@ -119,7 +121,7 @@ def _f64(x):
     if isinstance(x, np.ndarray):
         if x.dtype != np.float64:
             raise TypeError("moments must be float64")
-    elif x.dtype.is_floating_point and x.element_size() != 8:
+    elif str(x.dtype) != "torch.float64":
         raise TypeError("moments must be float64")
     return x
 
@@ -285,6 +287,12 @@ class Solver:
         """Off: only non-finite values fail a step (rho <= 0 / p <= 0 averages carry on)."""
         self._check(lib().hweno_set_positivity_check(self._h, int(bool(on))))
 
+    def set_persistence(self, persist=True):
+        """True (default): the first moments modified in troubled cells (eq. (vi))
+        replace the stage input and enter the Runge-Kutta combination; False:
+        they serve L only."""
+        self._check(lib().hweno_set_persistence(self._h, int(bool(persist))))
+
     def rerecon_count(self):
         """Cells reconstructed a second time (troubled cells, Step 2.3) since the last call."""
         v = ctypes.c_longlong()
@@ -336,12 +344,26 @@ def version():
 
 
 def max_dt_noalloc(grid, gamma, m, cfl, out, stream=None):
-    """hweno_max_dt_noalloc: m and out are CUDA float64 tensors (state; 3 doubles
-    receiving max a_x, max a_y, dt); nothing is allocated by the library."""
+    """hweno_max_dt_noalloc: m and out are CUDA float64 tensors on the current
+    device (m the state of the grid, nvar*nmom*ny*nx values; out 3 doubles
+    receiving max a_x, max a_y, dt); nothing is allocated by the library.
+    stream: a torch.cuda.Stream or raw cudaStream_t; None = torch's current
+    stream, so the call is ordered after the work that wrote m."""
+    import torch
+
     a, dev, n = _ptr(_f64(m))
     o, odev, on = _ptr(_f64(out))
     if not (dev and odev) or on < 3:
         raise ValueError("m and out must be CUDA float64 tensors (out with 3 elements)")
+    cur = torch.cuda.current_device()
+    if m.device.index != cur or out.device.index != cur:
+        raise ValueError("m and out must live on the current CUDA device")
+    nvar = 1 if grid.eq != EQ["euler"] else (3 if grid.dim == 1 else 4)
+    need = nvar * (2 if grid.dim == 1 else 3) * grid.nx * (grid.ny if grid.dim == 2 else 1)
+    if n < need:
+        raise ValueError(f"m holds {n} values; the grid needs {need}")
+    if stream is None:
+        stream = torch.cuda.current_stream()
     s = getattr(stream, "cuda_stream", stream) or 0
     st = lib().hweno_max_dt_noalloc(ctypes.byref(grid), float(gamma), ctypes.c_void_p(a), float(cfl),
                                     ctypes.c_void_p(o), ctypes.c_void_p(s))
@@ -428,6 +450,9 @@ class BatchSolver:
     def set_positivity_check(self, on=True):
         self._check(lib().hweno_set_positivity_check(self._h, int(bool(on))))
 
+    def set_persistence(self, persist=True):
+        self._check(lib().hweno_set_persistence(self._h, int(bool(persist))))
+
     def close(self):
         if getattr(self, "_h", None):
             lib().hweno_destroy(self._h)
@@ -473,6 +498,11 @@ class BatchSolver:
 
     def set_tile(self, variant):
         self._check(lib().hweno_batch_set_tile(self._h, int(variant)))
+
+    def set_barrier(self, spin_limit=1 << 26, extra_arrivals=0):
+        """Bound of the grid barrier's waits; extra_arrivals > 0 makes every wait
+        run out (the timeout path: the next synchronising call raises ETIMEOUT)."""
+        self._check(lib().hweno_batch_set_barrier(self._h, int(spin_limit), int(extra_arrivals)))
 
     def uses_graph(self):
         return lib().hweno_batch_uses_graph(self._h) == 1

@@ -120,3 +120,60 @@ def test_batch_df64_meets_the_fp64_bar(orc):
             m, _, rc = orc.step(cfg, m, dts[st][k])
             assert rc == 0
         assert rel_l1(got[k], m) <= 1e-12
+
+
+def test_barrier_timeout_is_reported_and_the_handle_recovers():
+    """The grid barrier's bounded wait: with one arrival more than the launched
+    blocks every wait runs out after a short limit; the next synchronising call
+    reports ETIMEOUT and rolls the step back, and once the barrier is set back
+    the handle steps exactly as a fresh one."""
+    probs = small_batch()[:3]
+    want, _, _ = run_batch(probs, 1)
+    s = hweno.BatchSolver(probs)
+    for k, p in enumerate(probs):
+        s.set_moments(k, torch.from_numpy(p.m).cuda())
+    s.set_barrier(spin_limit=2000, extra_arrivals=1)
+    s.step(cfl=0.6)
+    with pytest.raises(hweno.HwenoError) as e:
+        s.sync()
+    assert e.value.status == -4
+    for k, p in enumerate(probs):          # rolled back to the state before the step
+        np.testing.assert_array_equal(s.get_moments(k), p.m)
+    s.set_barrier()
+    s.step(cfl=0.6)
+    s.sync()
+    for k in range(len(probs)):
+        np.testing.assert_array_equal(s.get_moments(k), want[k])
+    s.close()
+
+
+def test_batch_reading_of_the_modification_matches_the_oracle(orc):
+    """set_persistence(False): the modified first moments serve L only (the
+    oracle's mod_in_L_only); bitwise the single-problem path with the same
+    switch and within 1e-12 of the oracle."""
+    probs = small_batch()[:3]
+    s = hweno.BatchSolver(probs)
+    s.set_persistence(False)
+    for k, p in enumerate(probs):
+        s.set_moments(k, torch.from_numpy(p.m).cuda())
+    dts = []
+    for _ in range(2):
+        s.step(cfl=0.6)
+        dts.append(s.dts())
+    s.sync()
+    got = [s.get_moments(k) for k in range(len(probs))]
+    s.close()
+    for k, p in enumerate(probs):
+        one = hweno.Solver.from_problem(p)
+        one.set_persistence(False)
+        one.set_moments(p.m)
+        for st in range(2):
+            one.step(dts[st][k])
+        np.testing.assert_array_equal(one.get_moments(), got[k])
+        one.close()
+        cfg = orc.make_cfg(2, p.nx, p.ny, dx=p.dx, dy=p.dy, eq="euler", bc=p.bc, mod_in_L_only=True)
+        m = p.m
+        for st in range(2):
+            m, _, rc = orc.step(cfg, m, dts[st][k])
+            assert rc == 0
+        assert rel_l1(got[k], m) <= 1e-12
