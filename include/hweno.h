@@ -175,6 +175,30 @@ hweno_status hweno_get_moments(hweno_t h, double* m, size_t count, int on_device
  * combination. */
 hweno_status hweno_step(hweno_t h, double dt);
 
+/* Row-slab decomposition of one 2D grid (no counterpart in the paper: the
+ * update of a cell in one stage depends on the stage input of the cells up to
+ * 4 rows and columns away (moments -> point values -> troubled flags ->
+ * re-reconstruction -> fluxes), so a slab that holds 4 halo rows on each
+ * internal side, refilled from its neighbours before every stage, advances its
+ * own rows exactly as the whole grid would).
+ * hweno_set_owned_rows: the rows [jlo, jhi) this handle owns; only they enter
+ *   the status checks, the CFL wave speeds and hweno_totals (default: all).
+ * hweno_stage: stage k (0, 1, 2, in this order, the same dt) of one SSP-RK3
+ *   step; the three stages equal hweno_step bit for bit.  Asynchronous.
+ * hweno_copy_rows: rows [j0, j0 + nrows) of every (variable, moment) plane of
+ *   the state the next stage reads (U^n before stage 0, U^(1), U^(2) between
+ *   stages) to (to_state = 0) or from (1) the device buffer buf, laid out
+ *   [nvar * nmom][nrows][nx].  Asynchronous on the handle's stream.
+ * hweno_wave_speeds: max a_x, max a_y over the owned rows (the quantities of
+ *   hweno_max_dt's rule, +inf for a non-physical average), host array of 2.
+ *   Synchronises.
+ * Single 2D handles (else ESTATE); EINVAL for rows out of range or a stage out
+ * of order. */
+hweno_status hweno_set_owned_rows(hweno_t h, int jlo, int jhi);
+hweno_status hweno_stage(hweno_t h, int k, double dt);
+hweno_status hweno_copy_rows(hweno_t h, int j0, int nrows, double* buf, int to_state);
+hweno_status hweno_wave_speeds(hweno_t h, double* ax_ay);
+
 /* dt for the next step from the cell averages (CFL rule of Sec. 3, formula not
  * printed there; reading): 1D dt = cfl dx / max(|f'|) or max(|mu| + c);
  * 2D dt = cfl / (max(a_x)/dx + max(a_y)/dy).  Synchronises. */
@@ -271,6 +295,18 @@ hweno_status hweno_advance(hweno_t h, double t_end, double cfl, long long max_st
  * does).  Applies to single and batch handles. */
 hweno_status hweno_set_positivity_check(hweno_t h, int on);
 
+/* One fused kernel per Runge-Kutta stage (on = 1) instead of the pipeline of
+ * four launches (on = 0, default): Steps 1-3 of Sec. 2.2 (reconstruction,
+ * eq. (KXRCF_), eq. (vi), the troubled re-reconstruction, HLLC fluxes,
+ * eqs. (integral1)-(integral3), L and eq. (Runge-Kutta)) for a strip of cells
+ * in one block, the point values kept in shared memory.  Single 2D Euler
+ * handles with the KXRCF, none or all indicator (else ESTATE); sides with
+ * fixed states (hweno_set_fixed_state) keep the pipeline.  Boundary images
+ * enter as ordinary cells, so cells next to a non-periodic side may differ from
+ * the pipeline by rounding; elsewhere the two agree to rounding of the
+ * quadrature sums.  Applies to hweno_step, hweno_advance and hweno_rhs. */
+hweno_status hweno_set_fused(hweno_t h, int on);
+
 /* How the first moments modified by eq. (vi) in troubled cells (Step 2.2) are
  * used; the paper does not say.  persist = 1 (default): they replace the
  * stage input, so the Runge-Kutta combination of eq. (Runge-Kutta) takes them
@@ -337,7 +373,7 @@ hweno_status hweno_batch_status(hweno_t h, unsigned* bits, int n);
  * first nkinds (>= 4) kernel kinds {0 reconstruct, 1 indicator + modification
  * (KXRCF, or its fallback pass after the learned indicator), 2 reconstruct
  * troubled cells, 3 fluxes + quadrature + Runge-Kutta update, 4 learned
- * indicator network pass}, the summed device milliseconds and launch counts
+ * indicator network pass, 5 fused stage}, the summed device milliseconds and launch counts
  * since the last read (kinds past nkinds are dropped; slots past the last kind
  * are zeroed). */
 hweno_status hweno_profile(hweno_t h, int enable);

@@ -99,6 +99,7 @@ def lib():
             _lib.orc_step.argtypes = [C, D, ctypes.c_double, U8]
             _lib.orc_max_dt.argtypes = [C, D, ctypes.c_double]
             _lib.orc_max_dt.restype = ctypes.c_double
+            _lib.orc_wave_speeds.argtypes = [C, D, ctypes.c_int, ctypes.c_int, D]
             _lib.orc_modification_weights.argtypes = [D]
             _lib.orc_recon_cell.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, D, D, D, D, D]
             _lib.orc_poly.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, D, D, D]
@@ -165,6 +166,14 @@ def euler1d_eig(gamma: float, u) -> tuple[np.ndarray, np.ndarray]:
 def max_dt(cfg: Cfg, m: np.ndarray, cfl: float = 0.6) -> float:
     m = np.ascontiguousarray(m, dtype=np.float64)
     return lib().orc_max_dt(ctypes.byref(cfg), _dp(m), float(cfl))
+
+
+def wave_speeds(cfg: Cfg, m: np.ndarray, jlo: int, jhi: int):
+    """(max a_x, max a_y) of the CFL rule over rows [jlo, jhi)."""
+    m = np.ascontiguousarray(m, dtype=np.float64)
+    out = np.zeros(2)
+    lib().orc_wave_speeds(ctypes.byref(cfg), _dp(m), int(jlo), int(jhi), _dp(out))
+    return float(out[0]), float(out[1])
 
 
 def totals(cfg: Cfg, m: np.ndarray) -> np.ndarray:

@@ -1007,10 +1007,12 @@ int orc_step(const orc_cfg *c, double *m, double dt, unsigned char *masks) {
 /* Reading of the CFL rule (CFL 0.6 in Sec. 3, formula not printed):
  *   1D dt = cfl dx / max(|f'(ubar)|) or max(|mu|+c) from cell averages;
  *   2D dt = cfl / (max(a_x)/dx + max(a_y)/dy). */
-double orc_max_dt(const orc_cfg *c, const double *m, double cfl) {
-  int nv = nvars(c), ny = c->dim == 1 ? 1 : c->ny;
+/* The largest wave speeds max(a_x), max(a_y) over rows [jlo, jhi) (the
+ * quantities of the CFL rule below); out[2]. */
+void orc_wave_speeds(const orc_cfg *c, const double *m, int jlo, int jhi, double *out) {
+  int nv = nvars(c);
   double ax = 0.0, ay = 0.0;
-  for (int j = 0; j < ny; ++j)
+  for (int j = jlo; j < jhi; ++j)
     for (int i = 0; i < c->nx; ++i) {
       double u[4];
       for (int v = 0; v < nv; ++v) u[v] = *MOM(c, (double *)m, v, 0, i, j);
@@ -1029,8 +1031,15 @@ double orc_max_dt(const orc_cfg *c, const double *m, double cfl) {
       if (sx > ax) ax = sx;
       if (sy > ay) ay = sy;
     }
-  if (c->dim == 1) return cfl * c->dx / ax;
-  return cfl / (ax / c->dx + ay / c->dy);
+  out[0] = ax;
+  out[1] = ay;
+}
+
+double orc_max_dt(const orc_cfg *c, const double *m, double cfl) {
+  double a[2];
+  orc_wave_speeds(c, m, 0, c->dim == 1 ? 1 : c->ny, a);
+  if (c->dim == 1) return cfl * c->dx / a[0];
+  return cfl / (a[0] / c->dx + a[1] / c->dy);
 }
 
 /* ------------------------------------------------------------------ */

@@ -435,10 +435,10 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
       const double r = S.cA * un + S.cB * (uin + S.dt * L[m]);
       S.Uout[si] = r;
       if (m == 0) newavg[v] = r;
-      if (!isfinite(r)) atomicOr(S.status, ST_NONFINITE);
+      if (!isfinite(r) && j >= P.jlo && j < P.jhi) atomicOr(S.status, ST_NONFINITE);
     }
   }
-  if (!S.Lout && P.eq == EQ_EULER && NV == 4) {
+  if (!S.Lout && P.eq == EQ_EULER && NV == 4 && j >= P.jlo && j < P.jhi) {
     const double rho = newavg[0];
     const double p = (P.gamma - 1.0) * (newavg[NV - 1] - 0.5 * (newavg[1] * newavg[1] + newavg[2] * newavg[2]) / rho);
     if (!(rho > 0.0) || !(p > 0.0)) atomicOr(S.status, ST_NONPOSITIVE);
@@ -464,6 +464,14 @@ __global__ void __launch_bounds__(TX * TY) update2d_kernel(Prob P, const T* __re
   update2d_tile<T, NV, TX, TY>(P, G, S, blockIdx.x * TX, blockIdx.y * TY, threadIdx.y * TX + threadIdx.x, xf, yf);
 }
 
+}  // namespace
+}  // namespace hw
+
+#include "hweno_fused.cuh"
+
+namespace hw {
+namespace {
+
 // Fixed-state ghosts are supported for 2D Euler in FP64 (the library rejects
 // other combinations), so only that instantiation carries the FIX variant.
 template <typename T, int NV, int MODE>
@@ -482,6 +490,16 @@ void launch_rec2d(int blocks, cudaStream_t st, const Prob& P, const Weights<T>& 
 template <typename T, int NV>
 void stage_t(const Prob& P, const HostTabs& HT, const Weights<T>& W, const Beta2<T>& Bt, const Bufs& B,
              const StageCall& S, cudaStream_t st) {
+  if constexpr (NV == 4) {
+    if (fused_applies(P, NV)) {   // the whole stage in one launch
+      Rk r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status, S.dtp};
+      FzOut o{S.mask, S.Mod, S.aleph, B.rerec};
+      if (B.prof) B.prof->begin(5, st);
+      launch_fused2d<T>(P, W, Bt, r, o, st);
+      if (B.prof) B.prof->end(st);
+      return;
+    }
+  }
   const long long ncell = (long long)P.nx * P.ny;
   int* cnt = B.count + S.stage;
   cudaMemsetAsync(cnt, 0, sizeof(int), st);

@@ -64,6 +64,9 @@ struct hweno_s {
   double graph_cfl = -1.0;
   int graph_variant = -1;
   bool use_graph = true;
+  int next_stage = 0;            // hweno_stage: the stage to run next (0: no step in progress)
+  int stage_a = 0;               // hweno_stage: rotation of the step in progress
+  double stage_dt = 0.0;         // hweno_stage: its dt
   unsigned long long spin_limit = hw::BARRIER_SPIN_DEFAULT;   // grid-barrier wait bound
   unsigned bar_extra = 0;        // extra arrivals the barrier waits for (timeout-path tests)
 };
@@ -245,6 +248,7 @@ hweno_status check_status(hweno_t h) {
     CK(h, cudaMemsetAsync(h->B.status, 0, sizeof(unsigned), h->stream));
     if (h->stepped) { h->cur = h->prev; h->time = h->time_prev; }
     h->stepped = false;
+    h->next_stage = 0;      // a step begun with hweno_stage is abandoned; U^n is intact
     char buf[200];
     snprintf(buf, sizeof buf, "last step produced a non-physical state or timed out (status 0x%x: %s%s%s%s); rolled back",
              st, (st & hw::ST_NONFINITE) ? "non-finite " : "", (st & hw::ST_NONPOSITIVE) ? "rho<=0 or p<=0 " : "",
@@ -308,6 +312,8 @@ hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gam
   P.nsm = 152;
   P.positivity = 1;
   P.persist = 1;
+  P.jlo = 0;
+  P.jhi = P.ny;
   cudaDeviceGetAttribute(&P.nsm, cudaDevAttrMultiProcessorCount, h->dev);
   h->fp32 = h->g.precision;
   build_tables(h);
@@ -381,6 +387,7 @@ hweno_status hweno_set_moments(hweno_t h, const double* m, size_t count, int on_
   CK(h, cudaMemsetAsync(h->B.status, 0, sizeof(unsigned), h->stream));
   h->have_state = true;
   h->stepped = false;
+  h->next_stage = 0;
   h->time = 0.0;
   if (!on_device) CK(h, cudaStreamSynchronize(h->stream));
   return HWENO_OK;
@@ -402,40 +409,132 @@ hweno_status hweno_get_moments(hweno_t h, double* m, size_t count, int on_device
   return HWENO_OK;
 }
 
-hweno_status hweno_step(hweno_t h, double dt) {
-  if (!h) return HWENO_EINVAL;
-  if (!h->have_state) return fail(h, HWENO_ESTATE, "step: no moments set");
-  if (h->g.indicator == 3 && !h->have_mlp) return fail(h, HWENO_ESTATE, "step: learned indicator not set (hweno_set_mlp)");
-  if (!(dt >= 0.0) || !isfinite(dt)) return fail(h, HWENO_EINVAL, "step: dt must be finite and >= 0");
-  if (!fix_ready(h)) return fail(h, HWENO_ESTATE, "step: an inflow side has no fixed states (hweno_set_fixed_state)");
-  const int a = h->cur, b = (h->cur + 1) % 3, c = (h->cur + 2) % 3;
+namespace {
+
+// Stage k (0, 1, 2) of the SSP-RK3 step from rotation a (eq. (Runge-Kutta)):
+//   U^(1) = U^n' + dt L(U^n');  U^(2) = 3/4 U^n' + 1/4 (U^(1)' + dt L(U^(1)'));
+//   U^{n+1} = 1/3 U^n' + 2/3 (U^(2)' + dt L(U^(2)'))
+// (' marks the modified first moments where the handle's reading uses them).
+void launch_stage(hweno_t h, int k, int a, double dt, double t) {
+  const int b = (a + 1) % 3, c = (a + 2) % 3;
   const size_t nc = ncell(h);
-  // stage times t, t + dt, t + dt/2 (the scheme's abscissae) for moving segments
-  const double tst[3] = {h->time, h->time + dt, h->time + 0.5 * dt};
-  auto run = [&](const hw::StageCall& S) {
-    if (h->P.fixtab) hw::run_fixfill(h->fix, h->fixtab, tst[S.stage], nullptr, nullptr, 0.0, h->stream);
-    if (h->g.dim == 1) hw::run_stage_1d(h->P, h->T, h->fp32, h->B, S, h->stream);
-    else hw::run_stage_2d(h->P, h->T, h->fp32, h->B, S, h->stream);
-  };
   hw::StageCall S{};
-  // U^(1) = U^n' + dt L(U^n')
-  S.stage = 0; S.Uin = h->U[a]; S.Un = h->U[a]; S.Uout = h->U[b]; S.dt = dt; S.cA = 0.0; S.cB = 1.0;
-  S.mask = h->mask3; S.Mod = h->ModN; S.maskN = nullptr; S.ModN = nullptr;
-  run(S);
-  // U^(2) = 3/4 U^n' + 1/4 (U^(1)' + dt L(U^(1)'))
-  S.stage = 1; S.Uin = h->U[b]; S.Un = h->U[a]; S.Uout = h->U[c]; S.cA = 0.75; S.cB = 0.25;
-  S.mask = h->mask3 + nc; S.Mod = h->ModK; S.maskN = h->mask3; S.ModN = h->ModN;
-  run(S);
-  // U^{n+1} = 1/3 U^n' + 2/3 (U^(2)' + dt L(U^(2)'))
-  S.stage = 2; S.Uin = h->U[c]; S.Un = h->U[a]; S.Uout = h->U[b]; S.cA = 1.0 / 3.0; S.cB = 2.0 / 3.0;
-  S.mask = h->mask3 + 2 * nc; S.Mod = h->ModK;
-  run(S);
-  CK(h, cudaGetLastError());
+  S.stage = k; S.Un = h->U[a]; S.dt = dt;
+  if (k == 0) {
+    S.Uin = h->U[a]; S.Uout = h->U[b]; S.cA = 0.0; S.cB = 1.0;
+    S.mask = h->mask3; S.Mod = h->ModN; S.maskN = nullptr; S.ModN = nullptr;
+  } else if (k == 1) {
+    S.Uin = h->U[b]; S.Uout = h->U[c]; S.cA = 0.75; S.cB = 0.25;
+    S.mask = h->mask3 + nc; S.Mod = h->ModK; S.maskN = h->mask3; S.ModN = h->ModN;
+  } else {
+    S.Uin = h->U[c]; S.Uout = h->U[b]; S.cA = 1.0 / 3.0; S.cB = 2.0 / 3.0;
+    S.mask = h->mask3 + 2 * nc; S.Mod = h->ModK; S.maskN = h->mask3; S.ModN = h->ModN;
+  }
+  if (h->P.fixtab) hw::run_fixfill(h->fix, h->fixtab, t, nullptr, nullptr, 0.0, h->stream);
+  if (h->g.dim == 1) hw::run_stage_1d(h->P, h->T, h->fp32, h->B, S, h->stream);
+  else hw::run_stage_2d(h->P, h->T, h->fp32, h->B, S, h->stream);
+}
+
+hweno_status step_checks(hweno_t h, double dt, const char* who) {
+  if (!h->have_state) return fail(h, HWENO_ESTATE, std::string(who) + ": no moments set");
+  if (h->g.indicator == 3 && !h->have_mlp)
+    return fail(h, HWENO_ESTATE, std::string(who) + ": learned indicator not set (hweno_set_mlp)");
+  if (!(dt >= 0.0) || !isfinite(dt)) return fail(h, HWENO_EINVAL, std::string(who) + ": dt must be finite and >= 0");
+  if (!fix_ready(h))
+    return fail(h, HWENO_ESTATE, std::string(who) + ": an inflow side has no fixed states (hweno_set_fixed_state)");
+  return HWENO_OK;
+}
+
+// the step's bookkeeping once its last stage is enqueued
+void finish_step(hweno_t h, int a, double dt) {
   h->prev = a;
-  h->cur = b;
+  h->cur = (a + 1) % 3;
   h->stepped = true;
   h->time_prev = h->time;
   h->time += dt;
+}
+
+}  // namespace
+
+hweno_status hweno_step(hweno_t h, double dt) {
+  if (!h) return HWENO_EINVAL;
+  if (h->next_stage != 0) return fail(h, HWENO_ESTATE, "step: a step begun with hweno_stage is not finished");
+  const hweno_status s = step_checks(h, dt, "step");
+  if (s != HWENO_OK) return s;
+  const int a = h->cur;
+  // stage times t, t + dt, t + dt/2 (the scheme's abscissae) for moving segments
+  const double tst[3] = {h->time, h->time + dt, h->time + 0.5 * dt};
+  for (int k = 0; k < 3; ++k) launch_stage(h, k, a, dt, tst[k]);
+  CK(h, cudaGetLastError());
+  finish_step(h, a, dt);
+  return HWENO_OK;
+}
+
+hweno_status hweno_stage(hweno_t h, int k, double dt) {
+  if (!h) return HWENO_EINVAL;
+  if (h->batch) return fail(h, HWENO_ESTATE, "stage: single-problem handles only");
+  if (k != h->next_stage) return fail(h, HWENO_ESTATE, "stage: stages run in the order 0, 1, 2");
+  if (k == 0) {
+    const hweno_status s = step_checks(h, dt, "stage");
+    if (s != HWENO_OK) return s;
+    h->stage_a = h->cur;
+    h->stage_dt = dt;
+  } else if (dt != h->stage_dt) {
+    return fail(h, HWENO_EINVAL, "stage: the three stages of a step take the same dt");
+  }
+  const double c[3] = {0.0, 1.0, 0.5};
+  launch_stage(h, k, h->stage_a, dt, h->time + c[k] * dt);
+  CK(h, cudaGetLastError());
+  if (k == 2) {
+    finish_step(h, h->stage_a, dt);
+    h->next_stage = 0;
+  } else {
+    h->next_stage = k + 1;
+  }
+  return HWENO_OK;
+}
+
+hweno_status hweno_set_owned_rows(hweno_t h, int jlo, int jhi) {
+  if (!h) return HWENO_EINVAL;
+  if (h->batch || h->g.dim != 2) return fail(h, HWENO_ESTATE, "set_owned_rows: single 2D handles only");
+  if (jlo < 0 || jhi > h->P.ny || jhi <= jlo) return fail(h, HWENO_EINVAL, "set_owned_rows: need 0 <= jlo < jhi <= ny");
+  h->P.jlo = jlo;
+  h->P.jhi = jhi;
+  drop_graphs(h);
+  return HWENO_OK;
+}
+
+hweno_status hweno_copy_rows(hweno_t h, int j0, int nrows, double* buf, int to_state) {
+  if (!h) return HWENO_EINVAL;
+  if (h->batch || h->g.dim != 2) return fail(h, HWENO_ESTATE, "copy_rows: single 2D handles only");
+  if (!buf || nrows < 1 || j0 < 0 || j0 + nrows > h->P.ny) return fail(h, HWENO_EINVAL, "copy_rows: rows out of range");
+  if (!h->have_state) return fail(h, HWENO_ESTATE, "copy_rows: no moments set");
+  // the state the next stage reads: U^n before a step, U^(1) or U^(2) between stages
+  const int a = h->next_stage == 0 ? h->cur : h->stage_a;
+  double* U = h->U[(a + h->next_stage) % 3];
+  const size_t w = h->P.nx * sizeof(double);
+  for (int q = 0; q < h->P.nvar * h->P.nmom; ++q) {
+    double* st = U + (size_t)q * h->P.plane + (size_t)j0 * h->P.pitch;
+    double* bb = buf + (size_t)q * nrows * h->P.nx;
+    if (to_state)
+      CK(h, cudaMemcpy2DAsync(st, h->P.pitch * sizeof(double), bb, w, w, nrows, cudaMemcpyDeviceToDevice, h->stream));
+    else
+      CK(h, cudaMemcpy2DAsync(bb, w, st, h->P.pitch * sizeof(double), w, nrows, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return HWENO_OK;
+}
+
+hweno_status hweno_wave_speeds(hweno_t h, double* ax_ay) {
+  if (!h || !ax_ay) return HWENO_EINVAL;
+  if (h->batch) return fail(h, HWENO_ESTATE, "wave_speeds: single-problem handles only");
+  if (!h->have_state) return fail(h, HWENO_ESTATE, "wave_speeds: no moments set");
+  hweno_status s = check_status(h);
+  if (s != HWENO_OK) return s;
+  hw::run_wavespeed(h->P, h->U[h->cur], h->red_part, h->red_out, h->stream);
+  CK(h, cudaMemcpyAsync(h->host_buf, h->red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  ax_ay[0] = h->host_buf[0];
+  ax_ay[1] = h->host_buf[1];
   return HWENO_OK;
 }
 
@@ -716,6 +815,19 @@ hweno_status hweno_set_positivity_check(hweno_t h, int on) {
   return HWENO_OK;
 }
 
+hweno_status hweno_set_fused(hweno_t h, int on) {
+  if (!h) return HWENO_EINVAL;
+  if (on != 0 && on != 1) return fail(h, HWENO_EINVAL, "set_fused: on must be 0 or 1");
+  if (on && (h->batch || h->g.dim != 2 || h->g.eq != HWENO_EULER ||
+             (h->g.indicator != HWENO_IND_NONE && h->g.indicator != HWENO_IND_KXRCF &&
+              h->g.indicator != HWENO_IND_ALL)))
+    return fail(h, HWENO_ESTATE, "set_fused: the fused stage is for single 2D Euler handles with the KXRCF, "
+                                 "none or all indicator");
+  h->P.fused = on;
+  drop_graphs(h);
+  return HWENO_OK;
+}
+
 hweno_status hweno_set_persistence(hweno_t h, int persist) {
   if (!h) return HWENO_EINVAL;
   if (persist != 0 && persist != 1) return fail(h, HWENO_EINVAL, "set_persistence: persist must be 0 or 1");
@@ -872,6 +984,7 @@ hweno_status hweno_create_batch(const hweno_grid* grids, const hweno_bc* bcs, in
     P.bc[0] = bcs[k].xlo; P.bc[1] = bcs[k].xhi; P.bc[2] = bcs[k].ylo; P.bc[3] = bcs[k].yhi;
     P.dx = (g.x1 - g.x0) / P.nx; P.dy = (g.y1 - g.y0) / P.ny;
     P.gamma = gamma; P.adv_a = 0.0; P.adv_b = 0.0; P.nsm = nsm; P.positivity = 1; P.persist = 1;
+    P.jlo = 0; P.jhi = P.ny;
     q.uoff = tu; q.goff = tg; q.aoff = ta; q.moff = tm; q.coff = tc;
     tu += 12 * P.plane; tg += 64 * P.gplane; ta += 5 * P.gplane; tm += 8 * P.plane; tc += (long long)P.nx * P.ny;
     h->probs.push_back(q);

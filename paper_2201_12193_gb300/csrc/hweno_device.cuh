@@ -50,6 +50,10 @@ struct Prob {
   int persist;            // 1: the first moments modified in troubled cells (eq. (vi)) replace the
                           //    stage input and enter the Runge-Kutta combination; 0: they serve
                           //    L only and the combination takes the stage states as they entered
+  int fused;              // 2D Euler: one fused kernel per stage where it applies (else the pipeline)
+  int jlo, jhi;           // owned rows [jlo, jhi): the rows a row-slab of a decomposed grid owns (the
+                          //    others are halo rows refilled from the neighbours before each stage);
+                          //    only they enter the status checks, the CFL reduction and the totals
 };
 
 // Sound speed of a cell average for the CFL rule; +inf marks a non-physical

@@ -30,8 +30,8 @@ enum { PREC_FP64 = 0, PREC_FP32 = 1, PREC_DF64 = 2 };
 // launching stream, read back (and summed per kernel kind) after a sync.
 struct Prof {
   // 0 reconstruct, 1 indicator + modify, 2 reconstruct troubled, 3 flux + update,
-  // 4 learned-indicator network pass
-  static constexpr int KINDS = 5;
+  // 4 learned-indicator network pass, 5 fused stage (all of 0-3 in one launch)
+  static constexpr int KINDS = 6;
   std::vector<cudaEvent_t> pool;
   std::vector<int> kinds;           // kind of each begin/end pair
   size_t used = 0;                  // events handed out

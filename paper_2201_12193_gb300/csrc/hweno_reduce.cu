@@ -47,9 +47,9 @@ __device__ __forceinline__ void block_reduce(double (&v)[K], bool is_max, double
 __global__ void __launch_bounds__(RT) wavespeed_kernel(Prob P, const double* __restrict__ U, double* __restrict__ part) {
   __shared__ double sm[2][RT / 32];
   double v[2] = {0.0, 0.0};
-  const long long n = (long long)P.nx * P.ny;
+  const long long n = (long long)P.nx * (P.jhi - P.jlo);   // owned rows
   for (long long t = (long long)blockIdx.x * RT + threadIdx.x; t < n; t += (long long)gridDim.x * RT) {
-    const int i = (int)(t % P.nx), j = (int)(t / P.nx);
+    const int i = (int)(t % P.nx), j = P.jlo + (int)(t / P.nx);
     double sx, sy;
     if (P.eq == EQ_ADV) { sx = fabs(P.adv_a); sy = fabs(P.adv_b); }
     else if (P.eq == EQ_BURGERS) { sx = sy = fabs(U[sidx(P, 0, 0, i, j)]); }
@@ -71,9 +71,9 @@ __global__ void __launch_bounds__(RT) wavespeed_kernel(Prob P, const double* __r
 __global__ void __launch_bounds__(RT) totals_kernel(Prob P, const double* __restrict__ U, double* __restrict__ part) {
   __shared__ double sm[4][RT / 32];
   double v[4] = {0.0, 0.0, 0.0, 0.0};
-  const long long n = (long long)P.nx * P.ny;
+  const long long n = (long long)P.nx * (P.jhi - P.jlo);   // owned rows
   for (long long t = (long long)blockIdx.x * RT + threadIdx.x; t < n; t += (long long)gridDim.x * RT) {
-    const int i = (int)(t % P.nx), j = (int)(t / P.nx);
+    const int i = (int)(t % P.nx), j = P.jlo + (int)(t / P.nx);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       if (k < P.nvar) v[k] += U[sidx(P, k, 0, i, j)];
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(RT) finish_kernel(const double* __restrict__ p
 }
 
 int first_pass_blocks(const Prob& P) {
-  const long long n = (long long)P.nx * P.ny;
+  const long long n = (long long)P.nx * (P.jhi - P.jlo);
   return (int)std::min<long long>(MAXB, (n + RT - 1) / RT);
 }
 

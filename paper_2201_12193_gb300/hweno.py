@@ -96,6 +96,11 @@ def lib():
         L.hweno_rerecon_count.argtypes = [H, ctypes.POINTER(ctypes.c_longlong)]
         L.hweno_set_positivity_check.argtypes = [H, ctypes.c_int]
         L.hweno_set_persistence.argtypes = [H, ctypes.c_int]
+        L.hweno_set_fused.argtypes = [H, ctypes.c_int]
+        L.hweno_set_owned_rows.argtypes = [H, ctypes.c_int, ctypes.c_int]
+        L.hweno_stage.argtypes = [H, ctypes.c_int, ctypes.c_double]
+        L.hweno_copy_rows.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
+        L.hweno_wave_speeds.argtypes = [H, D]
         L.hweno_set_fixed_state.argtypes = [H, ctypes.c_int, ctypes.POINTER(FixedState)]
         L.hweno_set_time.argtypes = [H, ctypes.c_double]
         L.hweno_get_time.argtypes = [H, D]
@@ -287,6 +292,33 @@ class Solver:
         """Off: only non-finite values fail a step (rho <= 0 / p <= 0 averages carry on)."""
         self._check(lib().hweno_set_positivity_check(self._h, int(bool(on))))
 
+    def set_owned_rows(self, jlo, jhi):
+        """Rows [jlo, jhi) this handle owns (row-slab decomposition)."""
+        self._check(lib().hweno_set_owned_rows(self._h, int(jlo), int(jhi)))
+
+    def stage(self, k, dt):
+        """Stage k (0, 1, 2) of one SSP-RK3 step."""
+        self._check(lib().hweno_stage(self._h, int(k), float(dt)))
+
+    def copy_rows(self, j0, nrows, buf, to_state):
+        """Rows [j0, j0 + nrows) of the state the next stage reads, to or from
+        buf (CUDA float64 tensor of nvar*nmom*nrows*nx values)."""
+        a, dev, n = _ptr(_f64(buf))
+        if not dev or n != self.nvar * self.nmom * nrows * self.nx:
+            raise ValueError("buf must be a CUDA float64 tensor of nvar*nmom*nrows*nx values")
+        self._check(lib().hweno_copy_rows(self._h, int(j0), int(nrows), ctypes.c_void_p(a), int(bool(to_state))))
+
+    def wave_speeds(self):
+        """(max a_x, max a_y) over the owned rows."""
+        out = (ctypes.c_double * 2)()
+        self._check(lib().hweno_wave_speeds(self._h, out))
+        return out[0], out[1]
+
+    def set_fused(self, on=True):
+        """One fused kernel per Runge-Kutta stage (2D Euler; KXRCF, none or all
+        indicator) instead of the four-launch pipeline."""
+        self._check(lib().hweno_set_fused(self._h, int(bool(on))))
+
     def set_persistence(self, persist=True):
         """True (default): the first moments modified in troubled cells (eq. (vi))
         replace the stage input and enter the Runge-Kutta combination; False:
@@ -304,7 +336,7 @@ class Solver:
         self._check(lib().hweno_features(self._h, ctypes.c_void_p(_ptr(U)[0]), ctypes.c_void_p(_ptr(cells)[0]),
                                          int(cells.numel()), ctypes.c_void_p(_ptr(X)[0])))
 
-    KERNEL_KINDS = ("reconstruct", "indicator", "reconstruct_troubled", "update", "learned_indicator")
+    KERNEL_KINDS = ("reconstruct", "indicator", "reconstruct_troubled", "update", "learned_indicator", "fused_stage")
 
     def profile(self, enable=True):
         self._check(lib().hweno_profile(self._h, int(bool(enable))))
