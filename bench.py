@@ -16,9 +16,10 @@ data against the plain scheme on the same data (throughputs, network roofline,
 recall / miss / false-alarm rates against KXRCF, L1 drift).  --full-run adds the
 2048^2 problem run whole to t = 0.25 in FP64 and FP32-bulk.
 
-Multi-GPU (torchrun): each rank advances its own independently seeded problem
-(weak scaling, no data-path collective); the timing barrier and the max over
-ranks use torch.distributed.
+Multi-GPU (torchrun): the 2048^2 grid is split into one row slab per rank; the
+4-row halos travel between neighbouring ranks (NCCL point to point) before
+every Runge-Kutta stage and the CFL wave speeds are max-reduced (strong
+scaling); the timing barrier and the max over ranks use torch.distributed.
 
 --impl reference times the CPU FP64 oracle (the reference arm of this build)
 on a bounded window of the same workload.
@@ -58,7 +59,6 @@ def _rec_flop_per_cell(nvar=4):
     return nvar * (sbv + 112) + 44
 # algorithmic HBM bytes per cell-stage: read U^(k) (12 doubles), read U^n for stages 2-3, write U^(k+1)
 ALGO_BYTES_PER_CELL_STAGE = 12 * 8 * (1 + 2.0 / 3.0 + 1)
-FP64_PEAK_NOMINAL = 1.25e12   # GB300 FP64 FLOP/s (nominal)
 
 
 def parse():
@@ -75,6 +75,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched form")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-indicator form")
     ap.add_argument("--no-1d", action="store_true", help="skip the 1D Shu-Osher full run")
+    ap.add_argument("--no-fused", action="store_true", help="skip the fused-stage forms")
+    ap.add_argument("--dmr", action="store_true",
+                    help="also run Example 3.9 (double Mach reflection) at 1600 x 400 to t = 0.2")
     ap.add_argument("--full-run", action="store_true",
                     help="also run the 2048^2 four-quadrant problem to t = 0.25 in FP64 and FP32-bulk")
     ap.add_argument("--learned-n", type=int, default=4096, help=argparse.SUPPRESS)
@@ -233,8 +236,10 @@ def time_oracle_all_cores(n, half):
 
 # ------------------------------------------------------------------ our arm
 
-def run_solver(torch, hweno, p, precision, steps, warmup, world, profile=False, clocks=None):
+def run_solver(torch, hweno, p, precision, steps, warmup, world, profile=False, clocks=None, fused=False):
     s = hweno.Solver.from_problem(p, precision=precision)
+    if fused:
+        s.set_fused(True)
     s.set_stream(torch.cuda.current_stream())
     s.set_moments(torch.from_numpy(p.m).cuda())
     for _ in range(warmup):
@@ -341,25 +346,32 @@ def run_batched(torch, hweno, args, world, rank):
 MLP_FLOP_PER_CELL = 2 * (108 * 64 + 64 * 64 + 64)    # 11,072 multiply-adds per cell
 
 
-def _rec_traffic_per_cell():
-    """DRAM bytes per cell of one rec2d launch from the committed ncu summary, or
-    None when the kernel sources changed since that capture."""
+KERNEL_SOURCES = ("hweno_2d_kernels.cuh", "hweno_device.cuh", "hweno_parity.h", "hweno_internal.h", "hweno_fused.cuh")
+
+
+def source_hash():
+    """SHA-256 of the 2D kernel sources (a committed ncu figure holds only for them)."""
     import hashlib
-    import re
-    try:
-        with open(os.path.join(ROOT, "profiles", "rec2d_fp64_four_quadrant_traffic.md")) as f:
-            txt = f.read()
-    except OSError:
-        return None
-    m1 = re.search(r"^bytes_per_cell: ([0-9.]+)$", txt, re.M)
-    m2 = re.search(r"^source_sha256: ([0-9a-f]{64})$", txt, re.M)
-    if not (m1 and m2):
-        return None
     h = hashlib.sha256()
-    for f in ("hweno_2d_kernels.cuh", "hweno_device.cuh", "hweno_parity.h", "hweno_internal.h"):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2201_12193_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    return float(m1.group(1)) if h.hexdigest() == m2.group(1) else None
+    return h.hexdigest()
+
+
+def traffic_per_cell(kernel):
+    """DRAM bytes per cell of one launch of `kernel` from the committed ncu
+    figures (profiles/dram_traffic.json), or None when the kernel sources
+    changed since that capture."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    k = d.get("kernels", {}).get(kernel)
+    if not k or d.get("source_sha256") != source_hash():
+        return None
+    return float(k["bytes_per_cell"])
 
 
 def _peaks():
@@ -368,6 +380,28 @@ def _peaks():
             return json.load(f)
     except (OSError, ValueError):
         return {}
+
+
+HBM_FALLBACK_GBPS = 6800.0
+
+
+def hbm_peak():
+    """(GB/s, source): the measured copy bandwidth, else the recipe's fallback."""
+    v = _peaks().get("hbm_gbs")
+    return (float(v), "MEASURED_PEAKS.json hbm_gbs (of measured)") if v else \
+        (HBM_FALLBACK_GBPS, "recipe fallback 6.8 TB/s (of fallback)")
+
+
+def alu_peaks(hweno):
+    """FP64 and FP32 FMA throughput measured on this device now (hweno_alu_probe,
+    best of 3 launches), and the nominal FP64 figure derived from the unit
+    counts: 2 FP64 FMA per clock per SM x 152 SMs x 2070 MHz x 2 flop."""
+    f64 = max(hweno.alu_probe("fp64") for _ in range(3))
+    f32 = max(hweno.alu_probe("fp32") for _ in range(3))
+    return {"fp64_tflops": f64 / 1e12, "fp32_tflops": f32 / 1e12,
+            "fp64_nominal_tflops": 2 * 2 * 152 * 2.07e9 / 1e12,
+            "how": "hweno_alu_probe: 8 independent FMA chains per thread, 4 x 256 threads per SM, "
+                   "CUDA events, best of 3 (of measured)"}
 
 
 def run_shu_osher(torch, hweno, world):
@@ -587,6 +621,148 @@ def run_learned(torch, hweno, args, world, rank):
         "roofline_network": roof, "input_generation_s": gen_s}}
 
 
+def run_fused_forms(torch, hweno, args, p, world, out64, peaks, hbm_gbps, hbm_src):
+    """The fused stage kernel (one launch per Runge-Kutta stage, point values in
+    shared memory) on the headline workload in FP32 bulk, double-float and
+    FP64: throughput, the HBM roofline of its algorithmic bytes, the ALU rate
+    of the reconstruction it performs once per cell (the recomputed halo not
+    counted), and the relative L1 distance of its state to the FP64 pipeline's
+    after the same steps."""
+    cells = p.nx * p.ny
+    b = out64.cpu().numpy()
+    out = {}
+    for prec in ("fp32", "df64", "fp64"):
+        s, ms, prof, _, o = run_solver(torch, hweno, p, prec, args.steps, args.warmup, world, profile=True,
+                                       fused=True)
+        ms = max_over_ranks(ms, world)
+        a = o.cpu().numpy()
+        fz_ms, fz_n = prof["fused_stage"]
+        gbs = ALGO_BYTES_PER_CELL_STAGE * cells * fz_n / (fz_ms * 1e-3) / 1e9
+        flops = _rec_flop_per_cell(4) * cells * fz_n / (fz_ms * 1e-3)
+        pk = peaks["fp32_tflops"] if prec == "fp32" else peaks["fp64_tflops"]
+        out[f"fused_{prec}"] = {
+            "value": aggregate(cells, 3, args.steps, world, ms), "ms_per_step": ms / args.steps,
+            "launches_per_step": fz_n / args.steps,
+            "dtype": {"fp32": "f32 (state and RK accumulation f64)", "df64": "f32x2 double-float",
+                      "fp64": "f64"}[prec],
+            "rel_l1_vs_fp64_pipeline_after_steps": float(np.abs(a - b).sum() / np.abs(b).sum()),
+            "steps_compared": args.warmup + args.steps,
+            "roofline_hbm": {"bound": "hbm", "achieved": gbs, "peak": hbm_gbps, "unit": "GB/s",
+                             "frac": gbs / hbm_gbps, "peak_source": hbm_src,
+                             "bytes_per_cell_stage": ALGO_BYTES_PER_CELL_STAGE,
+                             "traffic": (traffic_per_cell(f"fused2d_{prec}") or 0) * cells or None},
+            "roofline_alu": {"bound": "alu", "achieved": flops / 1e12, "peak": pk, "unit": "TFLOP/s",
+                             "frac": flops / 1e12 / pk,
+                             "note": "reconstruction flop per cell once (FP64-equivalent count for double-float) "
+                                     "against the measured FMA rate of the precision that executes it"}}
+        s.close()
+    return out
+
+
+def run_double_mach(torch, hweno):
+    """Example 3.9 (double Mach reflection) at the paper's 1600 x 400 to
+    t = 0.2, FP64, KXRCF, CFL 0.6, device-driven: with the modified first
+    moments used inside L only, and written back into the state (where the
+    run stops at a p < 0 cell average next to the start of the wall)."""
+    import math
+    from paper_2201_12193_gb300 import workloads as W
+    p = W.double_mach_2d(400)
+    out = {}
+    for name, persist in (("L_only", False), ("persist", True)):
+        s = hweno.Solver.from_problem(p)
+        s.set_persistence(persist)
+        s.set_stream(torch.cuda.current_stream())
+        s.set_moments(torch.from_numpy(p.m).cuda())
+        t0 = time.perf_counter()
+        reached, steps, err = 0.0, 0, None
+        while reached < p.t_end - 1e-14:
+            try:
+                t, n = s.advance(min(0.01, p.t_end - reached), CFL)
+            except hweno.HwenoError as e:
+                err = str(e)[:160]
+                break
+            reached += t
+            steps += n
+        secs = time.perf_counter() - t0
+        r = {"t_reached": reached, "steps": steps, "seconds": secs, "failed": err,
+             "value": p.nx * p.ny * 3 * steps / secs if secs else None}
+        if err is None:
+            m = s.get_moments()
+            rho = m[0, 0]
+            pr = 0.4 * (m[3, 0] - 0.5 * (m[1, 0] ** 2 + m[2, 0] ** 2) / rho)
+            xc = (np.arange(p.nx) + 0.5) * p.dx
+            xs = 1.0 / 6.0 + (1.0 + 20.0 * p.t_end) / math.sqrt(3.0)
+            r.update({"min_rho": float(rho.min()), "min_p": float(pr.min()), "max_rho": float(rho.max()),
+                      "top_row_shock_x": float(xc[np.argmax(rho[-1] < 0.5 * (8.0 + 1.4))]), "exact_trace_x": xs,
+                      "troubled_fraction_last_stage": float(s.troubled_mask()[-1].mean())})
+        out[name] = r
+        s.close()
+    return {"double_mach_1600x400_to_t0.2": {"workload": "2d_euler_double_mach_reflection_1600x400", "unit": UNIT,
+                                             **out}}
+
+
+def run_decomposed(args, world, rank, local):
+    """N > 1: the headline problem split into N row slabs, one per rank, with the
+    4-row halo exchange before every stage over NCCL and the CFL wave speeds
+    max-reduced (decomp.DistSlab); strong scaling of the same 2048^2 grid."""
+    import torch
+
+    from paper_2201_12193_gb300 import build, decomp, hweno, workloads as W
+    torch.cuda.set_device(local)
+    build.build()
+    p = W.four_quadrant_2d(args.n, seed=0)
+    d = decomp.DistSlab(p, rank, world)
+    lay = d.lay
+    rows = np.arange(lay["r0"] - lay["lo"], lay["r1"] + lay["hi"]) % p.ny
+    local_m = np.ascontiguousarray(p.m[:, :, rows, :])
+    d.set_moments(torch.from_numpy(local_m).cuda())
+    for _ in range(args.warmup):
+        d.step(d.max_dt(CFL))
+    d.solver.sync()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = vis.split(",")[local] if vis and vis.split(",")[local].strip().isdigit() else local
+    clocks = ClockSampler(smi_index)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        d.step(d.max_dt(CFL))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    clk = clocks.stop()
+    cells = p.nx * p.ny
+    value = cells * 3 * args.steps / (ms * 1e-3)
+    # end to end: each rank's slab from pinned host memory, the step, the owned rows back
+    host = torch.from_numpy(local_m.copy()).pin_memory()
+    res = torch.empty_like(host).pin_memory()
+    k = max(2, min(args.steps, 4))
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(k):
+        d.solver.set_moments(host.numpy())
+        d.step(d.max_dt(CFL))
+        d.solver.get_moments(res.numpy())
+    t = max_over_ranks(time.perf_counter() - t0, world)
+    d.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "nx": p.nx, "ny": p.ny, "precision": "fp64", "indicator": "kxrcf",
+                           "cfl": CFL, "parallelism": f"row slabs x{world} (4-row halo exchange per stage, NCCL)",
+                           "l2": "inputs larger than L2"},
+                "roofline": None, "e2e": {"value": cells * 3 * k / t, "unit": UNIT, "steps": k,
+                                          "h2d_bytes_per_step": int(host.numel() * 8),
+                                          "d2h_bytes_per_step": int(res.numel() * 8)},
+                "gpu_launches": None, "clocks": clk}
+        print(json.dumps(line))
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -599,6 +775,8 @@ def run_ours(args, world, rank, local):
     smi_index = vis.split(",")[local] if vis and vis.split(",")[local].strip().isdigit() else local
     clocks = ClockSampler(smi_index)
 
+    peaks = alu_peaks(hweno)                    # before the timed region, not inside it
+    hbm_gbps, hbm_src = hbm_peak()
     s64, ms, prof, clk, out64 = run_solver(torch, hweno, p, args.precision, args.steps, args.warmup, world,
                                            profile=True, clocks=clocks)
     ms = max_over_ranks(ms, world)
@@ -612,17 +790,21 @@ def run_ours(args, world, rank, local):
     roof = None
     if flop:
         achieved = flop / (kms * 1e-3)
-        roof = {"bound": "alu", "kernel": f"rec2d<double,4> ({kind})", "achieved": achieved / 1e12,
-                "peak": FP64_PEAK_NOMINAL / 1e12, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_NOMINAL,
-                "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (recipe table); FMA probe measured 1.05",
-                "traffic": None, "launches": kn, "avg_ms": kms / kn, "share": kms / total_kernel_ms}
-        bpc = _rec_traffic_per_cell() if args.precision == "fp64" else None
+        pk = peaks["fp64_tflops"] * 1e12 if args.precision == "fp64" else peaks["fp32_tflops"] * 1e12
+        roof = {"bound": "alu", "kernel": f"rec2d<{'double' if args.precision == 'fp64' else 'float'},4> ({kind})",
+                "achieved": achieved / 1e12, "peak": pk / 1e12, "unit": "TFLOP/s", "frac": achieved / pk,
+                "peak_source": f"{args.precision.upper()} FMA throughput measured in this run by hweno_alu_probe "
+                               f"(of measured); nominal FP64 from unit counts {peaks['fp64_nominal_tflops']:.3f}",
+                "frac_of_nominal_fp64": achieved / (peaks["fp64_nominal_tflops"] * 1e12),
+                "flop_per_cell": _rec_flop_per_cell(s64.nvar), "traffic": None, "launches": kn, "avg_ms": kms / kn,
+                "share": kms / total_kernel_ms}
+        bpc = traffic_per_cell(f"rec2d_{args.precision}") if args.precision == "fp64" else None
         if bpc:
             roof["traffic"] = bpc * cells
-            roof["traffic_unit"] = "bytes per launch (ncu dram read+write, profiles/rec2d_fp64_four_quadrant_traffic.md)"
+            roof["traffic_unit"] = "bytes per launch (ncu dram read+write per cell x cells, profiles/dram_traffic.json)"
     kernels = {k: {"ms": v[0], "launches": v[1], "share": v[0] / total_kernel_ms} for k, v in prof.items()}
     hbm = {"algorithmic_GBps": ALGO_BYTES_PER_CELL_STAGE * cells * 3 * args.steps / (ms * 1e-3) / 1e9,
-           "peak_GBps": 6796.2}
+           "peak_GBps": hbm_gbps, "peak_source": hbm_src}
     hbm["frac"] = hbm["algorithmic_GBps"] / hbm["peak_GBps"]
     launches = sum(v[1] for v in prof.values()) + 2 * args.steps     # + wave-speed reduction kernels
     s64.close()
@@ -657,10 +839,15 @@ def run_ours(args, world, rank, local):
                         "executes ~6-15 FP32 instructions per double-float operation"}
         sx.close()
 
+    if not args.no_forms and not args.no_fused:
+        forms.update(run_fused_forms(torch, hweno, args, p, world, out64, peaks, hbm_gbps, hbm_src))
+
     if not args.no_forms and not args.no_1d:
         forms.update(run_shu_osher(torch, hweno, world))
     if args.full_run:
         forms.update(run_four_quadrant_full(torch, hweno, world, rank))
+    if args.dmr:
+        forms.update(run_double_mach(torch, hweno))
 
     if not args.no_forms and not args.no_batch:
         forms.update(run_batched(torch, hweno, args, world, rank))
@@ -707,8 +894,8 @@ def run_ours(args, world, rank, local):
                 "config": {"workload": WORKLOAD, "nx": p.nx, "ny": p.ny, "precision": "fp64", "indicator": "kxrcf",
                            "cfl": CFL, "seed_per_rank": "rank", "parallelism": f"replicas x{world}",
                            "l2": "inputs larger than L2 (state 403 MB, point values 2.1 GB per stage)"},
-                "roofline": roof, "hbm": hbm, "kernels": kernels, "forms": forms, "e2e": e2e, "cpu_baseline": cpu,
-                "gpu_launches": launches * 1, "clocks": clk}
+                "roofline": roof, "hbm": hbm, "alu_peaks": peaks, "kernels": kernels, "forms": forms, "e2e": e2e,
+                "cpu_baseline": cpu, "gpu_launches": launches * 1, "clocks": clk}
         print(json.dumps(line))
 
 
@@ -751,7 +938,10 @@ def main():
         run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
         return
     world, rank, local = dist_init()
-    run_ours(args, world, rank, local)
+    if world > 1:
+        run_decomposed(args, world, rank, local)
+    else:
+        run_ours(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -379,6 +379,16 @@ hweno_status hweno_batch_status(hweno_t h, unsigned* bits, int n);
 hweno_status hweno_profile(hweno_t h, int enable);
 hweno_status hweno_profile_read(hweno_t h, double* ms, int* launches, int nkinds);
 
+/* Arithmetic throughput probe (measurement only; no counterpart in the
+ * paper): the fused multiply-add rate of the current device in FLOP/s
+ * (precision 0 = FP64, 1 = FP32), from `iters` iterations of 8 independent
+ * FMA chains per thread over 4 blocks of 256 threads per multiprocessor, timed
+ * with CUDA events on cuda_stream after a warm-up launch; an FMA counts 2 flop.
+ * The roofline denominator of the reconstruction kernels, which are bound by
+ * FP64 (or FP32) arithmetic, not by memory.  Synchronises.  EINVAL for bad
+ * arguments, ECUDA if a launch fails. */
+hweno_status hweno_alu_probe(int precision, long long iters, double* flop_per_s, void* cuda_stream);
+
 /* CFL reduction that allocates nothing (the paper has no counterpart; it
  * serves callers that cannot call cudaMalloc, e.g. code running under a frozen
  * memory budget or where the implicit synchronisation of an allocation is not

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libhweno.so")
 SOURCES = ["hweno_api.cu", "hweno_1d.cu", "hweno_2d.cu", "hweno_2d_fp32.cu", "hweno_2d_df64.cu", "hweno_2d_batch.cu",
-           "hweno_2d_batch_df64.cu", "hweno_reduce.cu", "hweno_noalloc.cu", "hweno_mlp.cu"]
+           "hweno_2d_batch_df64.cu", "hweno_reduce.cu", "hweno_noalloc.cu", "hweno_mlp.cu", "hweno_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

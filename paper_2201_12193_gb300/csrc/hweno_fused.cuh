@@ -147,22 +147,78 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 3 : 1)
     }
   }
   const bool kx = P.indicator == IND_KXRCF;
-  for (int q = 0; q < hown + 8; ++q) {
-    const int jm = j0 - 4 + q;   // moments enter; rows jm-1, jm-2, jm-3, jm-4 follow
-    // ---- Step 0: one row of moments into the ring, boundary images applied
-    {
-      const int s5 = ring5(jm);
-      const int jc = iclamp(jm, -4, P.ny + 3);
-      for (int t = tid; t < 12 * FZ_MC; t += FZ_NT) {
+  // A moment row is loaded one iteration ahead (registers) and stored into the
+  // ring at the start of the next, so its memory latency overlaps a whole
+  // iteration of arithmetic; likewise the Runge-Kutta operands of the row
+  // being updated are loaded at the start of its iteration.
+  constexpr int NPRE = (12 * FZ_MC + FZ_NT - 1) / FZ_NT;
+  double pre[NPRE];
+  unsigned preneg = 0;
+  auto prefetch = [&](int jrow) {
+    const int jc = iclamp(jrow, -4, P.ny + 3);
+    preneg = 0;
+#pragma unroll
+    for (int u = 0; u < NPRE; ++u) {
+      const int t = tid + u * FZ_NT;
+      pre[u] = 0.0;
+      if (t < 12 * FZ_MC) {
         const int pl = t / FZ_MC, cm = t - pl * FZ_MC;
         const int var = pl / 3, mom = pl - var * 3;
         const Img m = image_kind(P, iclamp(i0 - 4 + cm, -4, P.nx + 3), jc);
-        const double v = S.Uin[sidx(P, var, mom, m.i, m.j)];
-        int neg = (m.neg >> var) & 1;
-        if (mom == 1 && m.sx < 0) neg ^= 1;
-        if (mom == 2 && m.sy < 0) neg ^= 1;
-        sm.M[s5][pl][cm] = from_double<T>(neg ? -v : v);
+        pre[u] = S.Uin[sidx(P, var, mom, m.i, m.j)];
+        unsigned neg = (m.neg >> var) & 1;
+        if (mom == 1 && m.sx < 0) neg ^= 1u;
+        if (mom == 2 && m.sy < 0) neg ^= 1u;
+        preneg |= neg << u;
       }
+    }
+  };
+  prefetch(j0 - 4);
+  // Ghost cells at non-periodic sides: a ghost's flag is its image's (the
+  // indicator's inflow faces are not mirror-symmetric at a transmissive side,
+  // where the normal velocity keeps its sign), and the point values of the
+  // ghost next to the side are the mirrored final values of its image, as the
+  // pipeline reads them.  Image column (window) / row of a position, or the
+  // position itself where the side is periodic or the cell is inside.
+  auto img_col = [&](int c) -> int {
+    const int i = i0 - 3 + c;
+    if (i < 0 && P.bc[0] != BC_PERIODIC) return -1 - i - i0 + 3;
+    if (i >= P.nx && P.bc[1] != BC_PERIODIC) return 2 * P.nx - 1 - i - i0 + 3;
+    return c;
+  };
+  auto img_row = [&](int r) -> int {
+    if (r < 0 && P.bc[2] != BC_PERIODIC) return -1 - r;
+    if (r >= P.ny && P.bc[3] != BC_PERIODIC) return 2 * P.ny - 1 - r;
+    return r;
+  };
+  for (int q = 0; q < hown + 8; ++q) {
+    const int jm = j0 - 4 + q;   // moments enter; rows jm-1, jm-2, jm-3, jm-4 follow
+    // ---- Step 0: the prefetched row of moments into the ring, boundary images applied
+    {
+      const int s5 = ring5(jm);
+#pragma unroll
+      for (int u = 0; u < NPRE; ++u) {
+        const int t = tid + u * FZ_NT;
+        if (t < 12 * FZ_MC) {
+          const int pl = t / FZ_MC, cm = t - pl * FZ_MC;
+          sm.M[s5][pl][cm] = from_double<T>(((preneg >> u) & 1u) ? -pre[u] : pre[u]);
+        }
+      }
+    }
+    if (q + 1 < hown + 8) prefetch(jm + 1);
+    // the Runge-Kutta operands of row jm - 4 (updated at the end of this iteration)
+    double rin[3] = {0.0, 0.0, 0.0}, rn[3] = {0.0, 0.0, 0.0};
+    bool rfn = false;
+    if (q >= 8 && tid < 4 * FZ_W && i0 + (tid >> 2) < P.nx) {
+      const int ju = jm - 4, i = i0 + (tid >> 2), v = tid & 3;
+      const long long so = (long long)ju * P.pitch + i;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const long long si = (long long)(v * 3 + m) * P.plane + so;
+        rin[m] = S.Uin[si];
+        if (!S.Lout) rn[m] = S.Un[si];
+      }
+      rfn = P.persist && S.maskN && S.maskN[(long long)ju * P.nx + i] != 0;
     }
     __syncthreads();
     // ---- Step 1: point values of row jg, every window column, one variable per thread
@@ -236,7 +292,8 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 3 : 1)
       sm.F[s3][c] = flag ? 1 : 0;
       const int i = i0 - 3 + c;
       double mod[8];
-      if (flag) {
+      // a ghost's modified moments are needed wherever its image is troubled
+      if (flag || img_col(c) != c || img_row(jf) != jf) {
         fz_modify<4>(P, S.Uin, i, jf, mod);
 #pragma unroll
         for (int k = 0; k < 8; ++k) sm.Mod[s3][k][c] = mod[k];
@@ -273,7 +330,13 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 3 : 1)
           int kind, ox, oy;
           d4_slot(e, kind, ox, oy);
           const int r3 = ring3(jr + oy);
-          if (kind > 0 && sm.F[r3][c + ox])
+          // the stencil cell's flag, a ghost's taken from its image (when the
+          // image's row is in the ring; else the ghost itself is being
+          // re-reconstructed, and its values are replaced by the mirror below)
+          int fr = img_row(jr + oy), fc = img_col(c + ox);
+          if (fr < jr - 1 || fr > jr + 1) fr = jr + oy;
+          if (fc < 0 || fc >= FZ_WC) fc = c + ox;
+          if (kind > 0 && sm.F[ring3(fr)][fc])
             d[e] = from_double<T>(sm.Mod[r3][v * 2 + kind - 1][c + ox]);
           else
             d[e] = sm.M[ring5(jr + oy)][v * 3 + kind][c + 1 + ox];
@@ -286,8 +349,31 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 3 : 1)
       }
     }
     __syncthreads();
-    // ---- Step 3: fluxes of row ju (x faces; y faces above it, and below it in the first row)
+    // ---- ghosts next to non-periodic sides: mirrored final point values of their images
     const int ju = jm - 4;
+    if (q >= 8) {
+      const int cl = 2 - i0, cr = P.nx - i0 + 3;          // window columns of x ghosts i = -1, i = nx
+      const bool gl = cl >= 2 && P.bc[0] != BC_PERIODIC, gr = cr <= FZ_WC - 3 && P.bc[1] != BC_PERIODIC;
+      const bool gb = ju == 0 && P.bc[2] != BC_PERIODIC, gt = ju == P.ny - 1 && P.bc[3] != BC_PERIODIC;
+      if (gl || gr || gb || gt) {
+        const int s = ring5(ju);
+        for (int t = tid; t < 64; t += FZ_NT) {     // x: row ju, (var, point)
+          const int v = t >> 4, pt = t & 15, k = pt >> 2, l = pt & 3;
+          if (gl) sm.G[s][v][pt][cl] = (v == 1 && P.bc[0] == BC_REFLECTIVE ? T(-1) : T(1)) * sm.G[s][v][(3 - k) * 4 + l][cl + 1];
+          if (gr) sm.G[s][v][pt][cr] = (v == 1 && P.bc[1] == BC_REFLECTIVE ? T(-1) : T(1)) * sm.G[s][v][(3 - k) * 4 + l][cr - 1];
+        }
+        if (gb || gt) {                              // y: the ghost row below / above row ju
+          const int sg = ring5(gb ? ju - 1 : ju + 1);
+          const T sgn = P.bc[gb ? 2 : 3] == BC_REFLECTIVE ? T(-1) : T(1);
+          for (int t = tid; t < 64 * FZ_WC; t += FZ_NT) {
+            const int c = t % FZ_WC, vp = t / FZ_WC, v = vp >> 4, pt = vp & 15, k = pt >> 2, l = pt & 3;
+            sm.G[sg][v][pt][c] = (v == 2 ? sgn : T(1)) * sm.G[s][v][k * 4 + 3 - l][c];
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // ---- Step 3: fluxes of row ju (x faces; y faces above it, and below it in the first row)
     if (q >= 8) {
       const int s = ring5(ju), sb = ring5(ju - 1), st = ring5(ju + 1);
       constexpr int NX = 4 * (FZ_W + 1), NY = 4 * FZ_W;
@@ -381,19 +467,18 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 3 : 1)
       double newavg = 0.0;
       if (live) {
         const long long so = (long long)ju * P.pitch + i;
-        const long long cell = (long long)ju * P.nx + i;
         const bool fk = sm.F[ring3(ju)][c] != 0 && (P.persist || S.Lout);
-        const bool fn = P.persist && S.maskN && S.maskN[cell] != 0;
+        const bool fn = rfn;
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
           const long long si = (long long)(v * 3 + m) * P.plane + so;
-          const double uin = (m > 0 && fk) ? sm.Mod[ring3(ju)][v * 2 + m - 1][c] : S.Uin[si];
+          const double uin = (m > 0 && fk) ? sm.Mod[ring3(ju)][v * 2 + m - 1][c] : rin[m];
           if (S.Lout) {
             S.Lout[si] = L[m];
             if (S.Umod) S.Umod[si] = uin;
             continue;
           }
-          const double un = (m > 0 && fn) ? S.ModN[(long long)(v * 2 + m - 1) * P.plane + so] : S.Un[si];
+          const double un = (m > 0 && fn) ? S.ModN[(long long)(v * 2 + m - 1) * P.plane + so] : rn[m];
           const double r = S.cA * un + S.cB * (uin + dt * L[m]);
           S.Uout[si] = r;
           if (m == 0) newavg = r;

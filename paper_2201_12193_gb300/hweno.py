@@ -83,6 +83,7 @@ def lib():
         L.hweno_batch_set_barrier.argtypes = [H, ctypes.c_longlong, ctypes.c_int]
         L.hweno_batch_uses_graph.argtypes = [H]
         L.hweno_batch_status.argtypes = [H, ctypes.POINTER(ctypes.c_uint), ctypes.c_int]
+        L.hweno_alu_probe.argtypes = [ctypes.c_int, ctypes.c_longlong, D, ctypes.c_void_p]
         L.hweno_mlp_nparam.restype = ctypes.c_int
         L.hweno_set_mlp.argtypes = [H, ctypes.c_void_p, ctypes.c_int, ctypes.c_float]
         L.hweno_mlp_fallbacks.argtypes = [H, ctypes.POINTER(ctypes.c_longlong)]
@@ -401,6 +402,17 @@ def max_dt_noalloc(grid, gamma, m, cfl, out, stream=None):
                                     ctypes.c_void_p(o), ctypes.c_void_p(s))
     if st != 0:
         raise HwenoError(st, "hweno_max_dt_noalloc failed (see stderr)")
+
+
+def alu_probe(precision="fp64", iters=None, stream=None):
+    """Measured FMA throughput of the current device in FLOP/s ("fp64" or "fp32")."""
+    if iters is None:
+        iters = 40000 if precision == "fp64" else 2000000
+    out = ctypes.c_double()
+    st = lib().hweno_alu_probe({"fp64": 0, "fp32": 1}[precision], int(iters), ctypes.byref(out), _stream(stream))
+    if st != 0:
+        raise HwenoError(st, "hweno_alu_probe failed")
+    return out.value
 
 
 def mlp_nparam():
