@@ -389,6 +389,14 @@ hweno_status hweno_profile_read(hweno_t h, double* ms, int* launches, int nkinds
  * arguments, ECUDA if a launch fails. */
 hweno_status hweno_alu_probe(int precision, long long iters, double* flop_per_s, void* cuda_stream);
 
+/* The kernels' double -> float rounding (FP32-bulk precision; no counterpart
+ * in the paper): out[t] = in[t] rounded to the nearest float, ties to even, by
+ * integer operations (no FP64 instruction) for results in the normal float
+ * range, by the FP64 conversion otherwise.  Device pointers, n values,
+ * asynchronous on cuda_stream.  A check hook: the tests compare it with the
+ * FP64 conversion bit for bit. */
+hweno_status hweno_f32_round(const double* in, float* out, long long n, void* cuda_stream);
+
 /* CFL reduction that allocates nothing (the paper has no counterpart; it
  * serves callers that cannot call cudaMalloc, e.g. code running under a frozen
  * memory budget or where the implicit synchronisation of an allocation is not

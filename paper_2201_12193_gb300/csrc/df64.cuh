@@ -125,7 +125,30 @@ __device__ __forceinline__ bool operator==(df64 a, df64 b) { return a.hi == b.hi
 template <typename T> struct is_df64 { static constexpr bool value = false; };
 template <> struct is_df64<df64> { static constexpr bool value = true; };
 
-// A run-time double in the compute type (df64 by the integer split).
+// A double rounded to the nearest float (ties to even) with integer operations
+// only, so the conversion takes no FP64-pipe instruction (GB300 issues FP64 at a
+// small fraction of the FP32 rate).  IEEE 754 binary64 -> binary32: keep the
+// sign, rebias the exponent (1023 -> 127), keep the top 23 of the 52 fraction
+// bits and round on the 29 dropped bits (above half up; exactly half up when
+// the kept fraction is odd); a carry out of the fraction raises the exponent,
+// and out of the largest finite float gives infinity, as rounding must.
+// Results that are not normal floats (zero, subnormal, non-finite inputs)
+// take the FP64 conversion.
+__device__ __forceinline__ float f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned h = (unsigned)(b >> 32), l = (unsigned)b;
+  const int e = (int)((h >> 20) & 0x7FFu);
+  if (e < 897 || e > 1150) return __double2float_rn(x);
+  const unsigned keep = ((h & 0xFFFFFu) << 3) | (l >> 29);
+  const unsigned rest = l & 0x1FFFFFFFu;
+  unsigned f = (h & 0x80000000u) | ((unsigned)(e - 896) << 23) | keep;
+  if (rest > 0x10000000u || (rest == 0x10000000u && (keep & 1u))) f += 1u;
+  return __uint_as_float(f);
+}
+
+// A run-time double in the compute type (df64 by the integer split; float by
+// the FP64 conversion, which measured faster than f32_rn in the gathers of the
+// multi-launch reconstruction, where the FP64 pipe is not the bound).
 template <typename T> __device__ __forceinline__ T from_double(double x) { return T(x); }
 template <> __device__ __forceinline__ df64 from_double<df64>(double x) { return df_split(x); }
 

@@ -256,8 +256,8 @@ __global__ void __launch_bounds__(UB) update1d_kernel(Prob P, const T* __restric
       for (int v = 0; v < NV; ++v) F[v] += gl_w<T>(k) * f[v];
     }
   }
-  const double idx = 1.0 / P.dx;
-  const T tidx = T(idx);
+  const double idx = P.crdx.d;
+  const T tidx = pc<T>(P.crdx);
   // modified first moments in the combination (persist), and always in the Umod output of Lout
   const bool fk = S.mask[i] != 0 && (P.persist || S.Lout);
   const bool fn = P.persist && S.maskN && S.maskN[i] != 0;

@@ -408,8 +408,8 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
   }
   // eq. (2D-equ-int-approximation); the average equation in FP64 from the
   // face integrals so that the flux differences telescope in every precision
-  const double idx = 1.0 / P.dx, idy = 1.0 / P.dy;
-  const T tidx = T(idx), tidy = T(idy);
+  const double idx = P.crdx.d, idy = P.crdy.d;
+  const T tidx = pc<T>(P.crdx), tidy = pc<T>(P.crdy);
   const long long so = (long long)j * P.pitch + i;
   const long long cell = (long long)j * P.nx + i;
   // modified first moments in the combination (persist), and always in the Umod output of Lout

@@ -87,6 +87,25 @@ hweno_status fail(hweno_t h, hweno_status s, const std::string& msg) {
   } while (0)
 
 size_t ncell(const hweno_s* h) { return (size_t)h->P.nx * (size_t)h->P.ny; }
+
+// A double in the three compute precisions (the device conversions' roundings).
+hw::PConst pconst(double v) {
+  hw::PConst c;
+  c.d = v;
+  c.f = (float)v;
+  c.x = hw::df64(v);
+  return c;
+}
+
+// The per-precision constants of a problem (after dx, dy and gamma are set).
+void fill_consts(Prob& P) {
+  P.cgamma = pconst(P.gamma);
+  P.cdx = pconst(P.dx);
+  P.cdy = pconst(P.dy);
+  P.crdx = pconst(1.0 / P.dx);
+  P.crdy = pconst(1.0 / P.dy);
+  P.cdx2 = pconst(P.dx * P.dx);
+}
 size_t nstate(const hweno_s* h) { return (size_t)h->P.nvar * h->P.nmom * ncell(h); }
 
 // Linear weights of eq. (linear-weight) and the smoothness-indicator rows of
@@ -314,6 +333,7 @@ hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gam
   P.persist = 1;
   P.jlo = 0;
   P.jhi = P.ny;
+  fill_consts(P);
   cudaDeviceGetAttribute(&P.nsm, cudaDevAttrMultiProcessorCount, h->dev);
   h->fp32 = h->g.precision;
   build_tables(h);
@@ -985,6 +1005,7 @@ hweno_status hweno_create_batch(const hweno_grid* grids, const hweno_bc* bcs, in
     P.dx = (g.x1 - g.x0) / P.nx; P.dy = (g.y1 - g.y0) / P.ny;
     P.gamma = gamma; P.adv_a = 0.0; P.adv_b = 0.0; P.nsm = nsm; P.positivity = 1; P.persist = 1;
     P.jlo = 0; P.jhi = P.ny;
+    fill_consts(P);
     q.uoff = tu; q.goff = tg; q.aoff = ta; q.moff = tm; q.coff = tc;
     tu += 12 * P.plane; tg += 64 * P.gplane; ta += 5 * P.gplane; tm += 8 * P.plane; tc += (long long)P.nx * P.ny;
     h->probs.push_back(q);

@@ -25,6 +25,20 @@ constexpr unsigned ST_NONFINITE = 1u;     // a non-finite value in the new state
 constexpr unsigned ST_NONPOSITIVE = 2u;   // rho <= 0 or p <= 0 in a new cell average (Euler)
 constexpr unsigned ST_NODT = 8u;          // no CFL step length (rho <= 0 or a non-finite wave speed)
 
+// A problem constant in the three compute precisions, converted once on the
+// host (the same roundings as the device conversions: float by round to
+// nearest, double-float as the nearest float plus the nearest float of the
+// rest), so kernels do not spend FP64 instructions converting it per use.
+struct PConst {
+  double d;
+  float f;
+  df64 x;
+};
+template <typename T> __device__ __forceinline__ T pc(const PConst& c);
+template <> __device__ __forceinline__ double pc<double>(const PConst& c) { return c.d; }
+template <> __device__ __forceinline__ float pc<float>(const PConst& c) { return c.f; }
+template <> __device__ __forceinline__ df64 pc<df64>(const PConst& c) { return c.x; }
+
 // Problem description passed by value to every kernel.
 struct Prob {
   int nx, ny;             // cells (ny = 1 in 1D)
@@ -51,6 +65,7 @@ struct Prob {
                           //    stage input and enter the Runge-Kutta combination; 0: they serve
                           //    L only and the combination takes the stage states as they entered
   int fused;              // 2D Euler: one fused kernel per stage where it applies (else the pipeline)
+  PConst cgamma, cdx, cdy, crdx, crdy, cdx2;   // gamma, dx, dy, 1/dx, 1/dy, dx^2
   int jlo, jhi;           // owned rows [jlo, jhi): the rows a row-slab of a decomposed grid owns (the
                           //    others are halo rows refilled from the neighbours before each stage);
                           //    only they enter the status checks, the CFL reduction and the totals
@@ -179,12 +194,12 @@ __device__ __forceinline__ void phys_flux(const Prob& P, const T* u, int dir, T*
     if (P.eq == EQ_ADV) f[0] = T(dir == 0 ? P.adv_a : P.adv_b) * u[0];
     else f[0] = T(0.5) * u[0] * u[0];
   } else if constexpr (NV == 3) {
-    const T g = T(P.gamma);
+    const T g = pc<T>(P.cgamma);
     const T inv = T(1) / u[0], mu = u[1] * inv, E = u[2];
     const T p = (g - T(1)) * (E - T(0.5) * u[1] * mu);
     f[0] = u[1]; f[1] = u[1] * mu + p; f[2] = mu * (E + p);
   } else {
-    const T g = T(P.gamma);
+    const T g = pc<T>(P.cgamma);
     const T inv = T(1) / u[0], mu = u[1] * inv, nu = u[2] * inv, E = u[3];
     const T p = (g - T(1)) * (E - T(0.5) * (u[1] * mu + u[2] * nu));
     if (dir == 0) { f[0] = u[1]; f[1] = u[1] * mu + p; f[2] = u[1] * nu; f[3] = mu * (E + p); }
@@ -195,7 +210,7 @@ __device__ __forceinline__ void phys_flux(const Prob& P, const T* u, int dir, T*
 // Euler flux with the reciprocal of the density supplied by the caller.
 template <typename T, int NV>
 __device__ __forceinline__ void euler_flux_inv(const Prob& P, const T* u, T inv, int dir, T* f) {
-  const T g = T(P.gamma);
+  const T g = pc<T>(P.cgamma);
   if constexpr (NV == 3) {
     const T mu = u[1] * inv, E = u[2];
     const T p = (g - T(1)) * (E - T(0.5) * u[1] * mu);
@@ -264,7 +279,7 @@ __device__ __forceinline__ T scalar_velocity(const Prob& P, T u, int dir) {
 template <typename T, int NV>
 __device__ __forceinline__ void hllc(const Prob& P, const T* uL, const T* uR, int dir, T* F) {
   constexpr bool two = NV == 4;
-  const T g = T(P.gamma);
+  const T g = pc<T>(P.cgamma);
   const int in = 1 + dir, it = 2 - dir;
   constexpr int iE = NV - 1;
   const T rL = uL[0], rR = uR[0];
@@ -518,7 +533,7 @@ __device__ __forceinline__ T kxrcf2d(const Prob& P, const Weights<T>& W, const T
   auto rho_at = [&](const Img& m, long long om, int k, int l) -> T {
     return m.fs >= 0 ? from_double<T>(P.fixtab[4 * m.fs]) : G[(long long)mpt(m, k, l) * P.gplane + om];
   };
-  const T dx = T(P.dx), dy = T(P.dy);
+  const T dx = pc<T>(P.cdx), dy = pc<T>(P.cdy);
   T s = T(0), len = T(0);
   if (vxl > T(KX_VDEAD)) {
 #pragma unroll
@@ -542,7 +557,7 @@ __device__ __forceinline__ T kxrcf2d(const Prob& P, const Weights<T>& W, const T
   }
   const T nrm = aux[4 * P.gplane + o];
   if (len == T(0) || nrm == T(0)) return T(0);
-  return tabs(s) / len / (T(P.dx * P.dx) * nrm);   // h^{(l+1)/3}, l = 5, h = dx
+  return tabs(s) / len / (pc<T>(P.cdx2) * nrm);   // h^{(l+1)/3}, l = 5, h = dx
 }
 
 // ---------------------------------------------------------------- TVB indicator

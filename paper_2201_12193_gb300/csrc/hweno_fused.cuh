@@ -33,7 +33,7 @@ constexpr int FZ_H = 64;               // owned rows per block
 
 template <typename T>
 struct FusedSmem {
-  T G[5][4][16][FZ_WC];      // point values of 5 rows (ring by row): pass 1, then final
+  T G[4][4][16][FZ_WC];      // point values of 4 rows (ring by row): pass 1, then final
   T M[5][12][FZ_MC];         // moments of 5 rows (ring) in the compute precision, plane var*3 + moment
   double Mod[3][8][FZ_WC];   // modified first moments (FP64), plane var*2 + (moment-1), 3 rows (ring)
   T A[3][5][FZ_WC];          // KXRCF partials: face velocities x-, x+, y-, y+ and the density norm
@@ -46,6 +46,7 @@ struct FusedSmem {
 };
 
 __device__ __forceinline__ int ring5(int r) { return (r + 20) % 5; }   // rows >= -4
+__device__ __forceinline__ int ring4(int r) { return (r + 20) & 3; }
 // Butterfly shuffle of a value of the compute precision (all 32 lanes take part).
 template <typename T> __device__ __forceinline__ T shfl_xor_t(T x, int o) { return __shfl_xor_sync(0xffffffffu, x, o); }
 template <> __device__ __forceinline__ df64 shfl_xor_t<df64>(df64 x, int o) {
@@ -86,7 +87,7 @@ __device__ __forceinline__ T fz_kxrcf(const Prob& P, const FusedSmem<T>& sm, int
   const T vxr = T(0.5) * (sm.A[ac][1][c] + sm.A[ac][0][c + 1]);
   const T vyb = T(0.5) * (sm.A[ab][3][c] + sm.A[ac][2][c]);
   const T vyt = T(0.5) * (sm.A[ac][3][c] + sm.A[at][2][c]);
-  const T dx = T(P.dx), dy = T(P.dy);
+  const T dx = pc<T>(P.cdx), dy = pc<T>(P.cdy);
   T s = T(0), len = T(0);
   if (vxl > T(KX_VDEAD)) {
 #pragma unroll
@@ -110,7 +111,7 @@ __device__ __forceinline__ T fz_kxrcf(const Prob& P, const FusedSmem<T>& sm, int
   }
   const T nrm = sm.A[ac][4][c];
   if (len == T(0) || nrm == T(0)) return T(0);
-  return tabs(s) / len / (T(P.dx * P.dx) * nrm);
+  return tabs(s) / len / (pc<T>(P.cdx2) * nrm);
 }
 
 struct FzOut {
@@ -121,7 +122,7 @@ struct FzOut {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 3 : 1)
+__global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 4 : 2)
     fused2d_kernel(Prob P, Weights<T> W, Beta2<T> B, Rk S, FzOut O) {
   static_assert(FZ_WC == 32, "one warp spans the window's columns");
   extern __shared__ __align__(16) unsigned char fz_raw[];
@@ -201,7 +202,10 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 3 : 1)
         const int t = tid + u * FZ_NT;
         if (t < 12 * FZ_MC) {
           const int pl = t / FZ_MC, cm = t - pl * FZ_MC;
-          sm.M[s5][pl][cm] = from_double<T>(((preneg >> u) & 1u) ? -pre[u] : pre[u]);
+          const double x = ((preneg >> u) & 1u) ? -pre[u] : pre[u];
+          // FP32 bulk: round with integer operations (no FP64 instruction per moment)
+          if constexpr (std::is_same<T, float>::value) sm.M[s5][pl][cm] = f32_rn(x);
+          else sm.M[s5][pl][cm] = from_double<T>(x);
         }
       }
     }
@@ -234,14 +238,14 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 3 : 1)
       }
       T out[16];
       recon2d<T>(W, B, d, out);
-      const int s5 = ring5(jg);
+      const int s4 = ring4(jg);
 #pragma unroll
-      for (int p = 0; p < 16; ++p) sm.G[s5][v][p][c] = out[p];
+      for (int p = 0; p < 16; ++p) sm.G[s4][v][p][c] = out[p];
     }
     __syncthreads();
     // KXRCF partials of row jg: GL-weighted face velocities and the density norm
     if (q >= 2 && tid < FZ_WC) {
-      const int c = tid, s5 = ring5(jg), s3 = ring3(jg);
+      const int c = tid, s5 = ring4(jg), s3 = ring3(jg);
       T nrm = T(0);
 #pragma unroll
       for (int p = 0; p < 16; ++p) nrm = tmax(nrm, tabs(sm.G[s5][0][p][c]));
@@ -285,7 +289,7 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 3 : 1)
       if (c >= 1 && c <= FZ_WC - 2) {
         if (P.indicator == IND_ALL) flag = true;
         else if (kx) {
-          a = fz_kxrcf<T>(P, sm, ring5(jf - 1), ring5(jf), ring5(jf + 1), ring3(jf - 1), s3, ring3(jf + 1), c);
+          a = fz_kxrcf<T>(P, sm, ring4(jf - 1), ring4(jf), ring4(jf + 1), ring3(jf - 1), s3, ring3(jf + 1), c);
           flag = a > T(1);
         }
       }
@@ -343,55 +347,59 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 3 : 1)
         }
         T out[16];
         recon2d<T>(W, B, d, out);
-        const int s5 = ring5(jr);
+        const int s4 = ring4(jr);
 #pragma unroll
-        for (int p = 0; p < 16; ++p) sm.G[s5][v][p][c] = out[p];
+        for (int p = 0; p < 16; ++p) sm.G[s4][v][p][c] = out[p];
       }
     }
     __syncthreads();
     // ---- ghosts next to non-periodic sides: mirrored final point values of their images
+    // (x: the ghost columns of row ju; y: the ghost row below the first row of the
+    // grid, one iteration early, and the one above the last row)
     const int ju = jm - 4;
-    if (q >= 8) {
+    if (q >= 7) {
       const int cl = 2 - i0, cr = P.nx - i0 + 3;          // window columns of x ghosts i = -1, i = nx
-      const bool gl = cl >= 2 && P.bc[0] != BC_PERIODIC, gr = cr <= FZ_WC - 3 && P.bc[1] != BC_PERIODIC;
-      const bool gb = ju == 0 && P.bc[2] != BC_PERIODIC, gt = ju == P.ny - 1 && P.bc[3] != BC_PERIODIC;
+      const bool gl = q >= 8 && cl >= 2 && P.bc[0] != BC_PERIODIC;
+      const bool gr = q >= 8 && cr <= FZ_WC - 3 && P.bc[1] != BC_PERIODIC;
+      const bool gb = q == 7 && ju + 1 == 0 && P.bc[2] != BC_PERIODIC;
+      const bool gt = q >= 8 && ju == P.ny - 1 && P.bc[3] != BC_PERIODIC;
       if (gl || gr || gb || gt) {
-        const int s = ring5(ju);
+        const int s = ring4(ju);
         for (int t = tid; t < 64; t += FZ_NT) {     // x: row ju, (var, point)
           const int v = t >> 4, pt = t & 15, k = pt >> 2, l = pt & 3;
           if (gl) sm.G[s][v][pt][cl] = (v == 1 && P.bc[0] == BC_REFLECTIVE ? T(-1) : T(1)) * sm.G[s][v][(3 - k) * 4 + l][cl + 1];
           if (gr) sm.G[s][v][pt][cr] = (v == 1 && P.bc[1] == BC_REFLECTIVE ? T(-1) : T(1)) * sm.G[s][v][(3 - k) * 4 + l][cr - 1];
         }
-        if (gb || gt) {                              // y: the ghost row below / above row ju
-          const int sg = ring5(gb ? ju - 1 : ju + 1);
+        if (gb || gt) {                              // y: ghost row -1 from row 0, or row ny from row ny - 1
+          const int sg = gb ? ring4(-1) : ring4(ju + 1), si = gb ? ring4(0) : s;
           const T sgn = P.bc[gb ? 2 : 3] == BC_REFLECTIVE ? T(-1) : T(1);
           for (int t = tid; t < 64 * FZ_WC; t += FZ_NT) {
             const int c = t % FZ_WC, vp = t / FZ_WC, v = vp >> 4, pt = vp & 15, k = pt >> 2, l = pt & 3;
-            sm.G[sg][v][pt][c] = (v == 2 ? sgn : T(1)) * sm.G[s][v][k * 4 + 3 - l][c];
+            sm.G[sg][v][pt][c] = (v == 2 ? sgn : T(1)) * sm.G[si][v][k * 4 + 3 - l][c];
           }
         }
       }
       __syncthreads();
     }
-    // ---- Step 3: fluxes of row ju (x faces; y faces above it, and below it in the first row)
-    if (q >= 8) {
-      const int s = ring5(ju), sb = ring5(ju - 1), st = ring5(ju + 1);
+    // ---- Step 3: fluxes.  q == 7: the y faces below the segment's first row;
+    // q >= 8: the x faces of row ju and the y faces above it
+    if (q >= 7) {
+      const int s = ring4(ju), st = ring4(ju + 1);
       constexpr int NX = 4 * (FZ_W + 1), NY = 4 * FZ_W;
-      const int total = NX + NY + (q == 8 ? NY : 0);
+      const int nx_items = q >= 8 ? NX : 0;
+      const int total = nx_items + NY;
       for (int it = tid; it < total; it += FZ_NT) {
         T uL[4], uR[4];
-        if (it < NX) {
+        if (it < nx_items) {
           const int f = it >> 2, l = it & 3;
 #pragma unroll
           for (int v = 0; v < 4; ++v) { uL[v] = sm.G[s][v][12 + l][2 + f]; uR[v] = sm.G[s][v][l][3 + f]; }
           num_flux<T, 4>(P, uL, uR, 0, sm.XF[f][l]);
         } else {
-          const int g = (it - NX) % NY, f = g >> 2, k = g & 3;
-          const bool below = it >= NX + NY;
-          const int lo = below ? sb : s, hi = below ? s : st;
+          const int g = it - nx_items, f = g >> 2, k = g & 3;
 #pragma unroll
-          for (int v = 0; v < 4; ++v) { uL[v] = sm.G[lo][v][k * 4 + 3][3 + f]; uR[v] = sm.G[hi][v][k * 4][3 + f]; }
-          num_flux<T, 4>(P, uL, uR, 1, sm.YF[(below ? ju : ju + 1) & 1][f][k]);
+          for (int v = 0; v < 4; ++v) { uL[v] = sm.G[s][v][k * 4 + 3][3 + f]; uR[v] = sm.G[st][v][k * 4][3 + f]; }
+          num_flux<T, 4>(P, uL, uR, 1, sm.YF[(ju + 1) & 1][f][k]);
         }
       }
     }
@@ -403,7 +411,7 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 3 : 1)
       // every lane of a warp takes part in the shuffles; lanes past the owned
       // cells (act false) compute on cell 0 and write nothing
       const bool act = tid < 4 * FZ_W;
-      const int f = act ? tid >> 2 : 0, g = tid & 3, c = 3 + f, i = i0 + f, s = ring5(ju);
+      const int f = act ? tid >> 2 : 0, g = tid & 3, c = 3 + f, i = i0 + f, s = ring4(ju);
       T Fc[4], Gc[4];
       {
         T rho[4], inv[4];
@@ -457,8 +465,8 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 3 : 1)
         if (v == k) { Fcv = Fc[k]; Gcv = Gc[k]; }
       // eq. (2D-equ-int-approximation); the average equation in FP64 from the
       // face integrals so that the flux differences telescope in every precision
-      const double idx = 1.0 / P.dx, idy = 1.0 / P.dy;
-      const T tidx = T(idx), tidy = T(idy);
+      const double idx = P.crdx.d, idy = P.crdy.d;
+      const T tidx = pc<T>(P.crdx), tidy = pc<T>(P.crdy);
       double L[3];
       L[0] = -((double)Fp - (double)Fm) * idx - ((double)Gp - (double)Gm) * idy;
       L[1] = (double)(-(Fp + Fm) * T(0.5) * tidx + Fcv * tidx - (Gpx - Gmx) * tidy);
@@ -491,9 +499,9 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 3 : 1)
       const double a2 = __shfl_sync(0xffffffffu, newavg, base + 2);
       const double a3 = __shfl_sync(0xffffffffu, newavg, base + 3);
       if (live && v == 0 && !S.Lout && ju >= P.jlo && ju < P.jhi) {
+        // p = (gamma - 1)(E - |rho v|^2 / (2 rho)) > 0 with rho > 0, without a division
         const double rho = newavg;
-        const double p = (P.gamma - 1.0) * (a3 - 0.5 * (a1 * a1 + a2 * a2) / rho);
-        if (!(rho > 0.0) || !(p > 0.0)) atomicOr(S.status, ST_NONPOSITIVE);
+        if (!(rho > 0.0) || !(2.0 * a3 * rho > a1 * a1 + a2 * a2)) atomicOr(S.status, ST_NONPOSITIVE);
       }
     }
     // the next iteration's first writes (moment ring, then after a barrier the

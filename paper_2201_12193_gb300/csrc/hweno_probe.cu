@@ -10,6 +10,7 @@
 #include <stdio.h>
 
 #include "hweno.h"
+#include "hweno_device.cuh"
 
 namespace {
 
@@ -62,7 +63,22 @@ cudaError_t run_probe(long long iters, double* flop_per_s, cudaStream_t st) {
   return cudaSuccess;
 }
 
+// The fused FP32 kernel's double -> float rounding (hw::f32_rn) applied to n values.
+__global__ void f32_round_kernel(const double* __restrict__ in, float* __restrict__ out, long long n) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    out[t] = hw::f32_rn(in[t]);
+}
+
 }  // namespace
+
+extern "C" hweno_status hweno_f32_round(const double* in, float* out, long long n, void* cuda_stream) {
+  if ((!in || !out) && n > 0) return HWENO_EINVAL;
+  if (n < 0) return HWENO_EINVAL;
+  if (n == 0) return HWENO_OK;
+  const long long blocks = (n + PT - 1) / PT < 4096 ? (n + PT - 1) / PT : 4096;
+  f32_round_kernel<<<(int)blocks, PT, 0, (cudaStream_t)cuda_stream>>>(in, out, n);
+  return cudaGetLastError() == cudaSuccess ? HWENO_OK : HWENO_ECUDA;
+}
 
 extern "C" hweno_status hweno_alu_probe(int precision, long long iters, double* flop_per_s, void* cuda_stream) {
   if (!flop_per_s || iters < 1 || (precision != 0 && precision != 1)) return HWENO_EINVAL;

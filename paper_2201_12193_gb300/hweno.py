@@ -84,6 +84,7 @@ def lib():
         L.hweno_batch_uses_graph.argtypes = [H]
         L.hweno_batch_status.argtypes = [H, ctypes.POINTER(ctypes.c_uint), ctypes.c_int]
         L.hweno_alu_probe.argtypes = [ctypes.c_int, ctypes.c_longlong, D, ctypes.c_void_p]
+        L.hweno_f32_round.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_void_p]
         L.hweno_mlp_nparam.restype = ctypes.c_int
         L.hweno_set_mlp.argtypes = [H, ctypes.c_void_p, ctypes.c_int, ctypes.c_float]
         L.hweno_mlp_fallbacks.argtypes = [H, ctypes.POINTER(ctypes.c_longlong)]
@@ -413,6 +414,17 @@ def alu_probe(precision="fp64", iters=None, stream=None):
     if st != 0:
         raise HwenoError(st, "hweno_alu_probe failed")
     return out.value
+
+
+def f32_round(x, out, stream=None):
+    """The kernels' double -> float rounding of CUDA float64 tensor x into float32 tensor out."""
+    a, dev, n = _ptr(_f64(x))
+    o, odev, on = _ptr(out)
+    if not (dev and odev) or on != n or str(out.dtype) != "torch.float32":
+        raise ValueError("x (float64) and out (float32) must be CUDA tensors of the same size")
+    st = lib().hweno_f32_round(ctypes.c_void_p(a), ctypes.c_void_p(o), n, _stream(stream))
+    if st != 0:
+        raise HwenoError(st, "hweno_f32_round failed")
 
 
 def mlp_nparam():

@@ -797,3 +797,27 @@ def test_inflow_rejected_where_unsupported():
     with pytest.raises(hweno.HwenoError):
         s.step(1e-4)                                   # inflow sides without states
     s.close()
+
+
+def test_float_rounding_of_the_fp32_path_is_round_to_nearest():
+    """The integer-only double -> float rounding the FP32-bulk kernels use equals
+    the FP64 conversion bit for bit: random doubles over the whole normal float
+    range, exact ties (both parities), the largest float and the rounding to
+    infinity, the subnormal and zero range, and non-finite values."""
+    rng = np.random.default_rng(11)
+    x = [rng.standard_normal(1 << 20) * np.exp2(rng.integers(-126, 128, 1 << 20))]
+    f = rng.standard_normal(1 << 16).astype(np.float32).astype(np.float64)
+    ulp = np.abs(np.spacing(f.astype(np.float32))).astype(np.float64)
+    x += [f + 0.5 * ulp, f - 0.5 * ulp, f + 0.25 * ulp, f + 0.75 * ulp]          # ties and near-ties
+    big = float(np.finfo(np.float32).max)
+    x += [np.array([big, -big, big * (1 + 2.0 ** -25), big * (1 + 2.0 ** -24), 1e39, -1e39, 2.0 ** -126,
+                    2.0 ** -127, 2.0 ** -149, 2.0 ** -150, 1e-45, 0.0, -0.0, np.inf, -np.inf, 1.0, -1.0])]
+    x = torch.from_numpy(np.concatenate(x)).cuda()
+    out = torch.empty(x.numel(), dtype=torch.float32, device="cuda")
+    hweno.f32_round(x, out)
+    want = x.float()
+    assert torch.equal(out.view(torch.int32), want.view(torch.int32))
+    nan = torch.tensor([np.nan], dtype=torch.float64, device="cuda")
+    o1 = torch.empty(1, dtype=torch.float32, device="cuda")
+    hweno.f32_round(nan, o1)
+    assert torch.isnan(o1).all()
