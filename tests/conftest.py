@@ -13,7 +13,16 @@ if HERE not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
-    config.addinivalue_line("markers", "slow: longer CPU test")
+    config.addinivalue_line("markers", "slow: longer CPU test (minutes); runs with HWENO_SLOW=1")
+
+
+def pytest_collection_modifyitems(config, items):
+    if os.environ.get("HWENO_SLOW") == "1":
+        return
+    skip = pytest.mark.skip(reason="slow: set HWENO_SLOW=1 to run")
+    for item in items:
+        if "slow" in item.keywords:
+            item.add_marker(skip)
 
 
 @pytest.fixture(scope="session")
