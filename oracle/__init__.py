@@ -48,16 +48,17 @@ class Cfg(ctypes.Structure):
                 ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("t", ctypes.c_double),
                 ("seg_on", ctypes.c_int * 4), ("seg_c0", ctypes.c_double * 4), ("seg_speed", ctypes.c_double * 4),
                 ("fa", (ctypes.c_double * 4) * 4), ("fb", (ctypes.c_double * 4) * 4),
-                ("mod_in_L_only", ctypes.c_int)]
+                ("mod_in_L_only", ctypes.c_int), ("sol_i", ctypes.c_int), ("sol_j", ctypes.c_int)]
 
 
 def make_cfg(dim, nx, ny=1, dx=1.0, dy=1.0, eq="euler", adv=(1.0, 0.0), gamma=1.4,
              indicator="kxrcf", gbar=(1.0, 10.0, 100.0, 1000.0), bc=("periodic",) * 4, tvb_m=0.0,
-             charwise=False, x0=0.0, y0=0.0, t=0.0, fixed=None, mod_in_L_only=False) -> Cfg:
+             charwise=False, x0=0.0, y0=0.0, t=0.0, fixed=None, mod_in_L_only=False, solid=None) -> Cfg:
     """fixed: per side (x-lo, x-hi, y-lo, y-hi) None or a dict with the
     fixed ghost states: "a" inside the segment (centre coordinate along the
     side below c0 + speed * t; no segment when "c0" is absent), "b" elsewhere
-    on an "inflow" side."""
+    on an "inflow" side.  solid: None or (i0, j1): cells with i >= i0 and
+    j < j1 are solid (a forward-facing step; 2D Euler)."""
     c = Cfg()
     c.dim, c.nx, c.ny = dim, nx, (ny if dim == 2 else 1)
     c.dx, c.dy = dx, (dy if dim == 2 else 1.0)
@@ -69,6 +70,8 @@ def make_cfg(dim, nx, ny=1, dx=1.0, dy=1.0, eq="euler", adv=(1.0, 0.0), gamma=1.
     c.charwise = int(bool(charwise))
     c.x0, c.y0, c.t = x0, y0, t
     c.mod_in_L_only = int(bool(mod_in_L_only))
+    if solid is not None:
+        c.sol_i, c.sol_j = int(solid[0]), int(solid[1])
     for k, f in enumerate(fixed or [None] * 4):
         if not f:
             continue

@@ -76,6 +76,11 @@ typedef struct {
   int mod_in_L_only; /* 1: the modified first moments serve L only; the Runge-Kutta
                         combination takes the unmodified stage states (reading B
                         of the modification's persistence) */
+  /* Solid block (2D Euler; the forward step of Sec. 3, Example 3.10): cells
+   * with i >= sol_i and j < sol_j are solid, bounded by a vertical wall face
+   * at i = sol_i (when sol_i > 0) and a horizontal one at j = sol_j (when
+   * sol_j < ny); sol_j = 0: none. */
+  int sol_i, sol_j;
 } orc_cfg;
 
 /* ------------------------------------------------------------------ */
@@ -496,6 +501,26 @@ static const double *fixed_state(const orc_cfg *c, int side, double pos) {
   return NULL;
 }
 
+static int is_solid(const orc_cfg *c, int i, int j) {
+  return c->dim == 2 && c->sol_j > 0 && i >= c->sol_i && i < c->nx && j >= 0 && j < c->sol_j;
+}
+
+/* Reading (the paper gives no rule for solid cells inside the domain): a solid
+ * cell within reach of the fluid is the wall image of a fluid cell across the
+ * nearer face of the block -- a cell a columns right of the vertical face and
+ * b rows below the horizontal one mirrors across the vertical face when
+ * a < b, across the horizontal face when b < a, and across both (the corner
+ * diagonal) when a = b; the wall-normal momentum of each crossed face is
+ * negated with the normal first moment, as at a reflective side. */
+static void solid_image(const orc_cfg *c, image_t *r) {
+  if (!is_solid(c, r->i, r->j)) return;
+  const int a = r->i - c->sol_i + 1, b = c->sol_j - r->j;
+  const int hasx = c->sol_i > 0, hasy = c->sol_j < c->ny;
+  const int mx = hasx && (!hasy || a <= b), my = hasy && (!hasx || b <= a);
+  if (mx) { r->i = 2 * c->sol_i - 1 - r->i; r->sx = -r->sx; r->rx ^= 1; }
+  if (my) { r->j = 2 * c->sol_j - 1 - r->j; r->sy = -r->sy; r->ry ^= 1; }
+}
+
 static image_t cell_image(const orc_cfg *c, int i, int j) {
   image_t r = {i, j, 1, 1, 0, 0, NULL};
   if (c->dim == 2 && (j < 0 || j >= c->ny)) {
@@ -512,6 +537,7 @@ static image_t cell_image(const orc_cfg *c, int i, int j) {
     if (c->bc[side] == 0) { r.i = ((i % c->nx) + c->nx) % c->nx; }
     else { r.i = i < 0 ? -1 - i : 2 * c->nx - 1 - i; r.sx = -1; r.rx = c->bc[side] == 2; }
   }
+  solid_image(c, &r);
   return r;
 }
 
@@ -681,6 +707,7 @@ static void reconstruct_all(const orc_cfg *c, const double *m, double *G, const 
     for (int i = 0; i < c->nx; ++i) {
       size_t cell = (size_t)j * c->nx + i;
       if (only && !only[cell]) continue;
+      if (is_solid(c, i, j)) continue;      /* never read: solid cells are images */
       if (c->charwise && c->dim == 1 && c->eq == 2) {
         double R[3][3], Lm[3][3], u0[3];
         for (int v = 0; v < 3; ++v) u0[v] = mom_at(c, m, v, 0, i, 0);
@@ -755,19 +782,20 @@ static double kxrcf_aleph(const orc_cfg *c, const double *G, int i, int j) {
     vyt += gl_weight(k) * 0.5 * (kx_velocity(c, u, 1) + kx_velocity(c, un, 1));
   }
   double s = 0.0, len = 0.0;
-  if (vxl > KX_VDEAD) {
+  /* Reading: a face shared with a solid cell is a wall, never an inflow face */
+  if (vxl > KX_VDEAD && !is_solid(c, i - 1, j)) {
     for (int l = 0; l < 4; ++l) s += c->dy * gl_weight(l) * (gl_at(c, G, 0, i, j, 0, l) - gl_at(c, G, 0, i - 1, j, 3, l));
     len += c->dy;
   }
-  if (-vxr > KX_VDEAD) {
+  if (-vxr > KX_VDEAD && !is_solid(c, i + 1, j)) {
     for (int l = 0; l < 4; ++l) s += c->dy * gl_weight(l) * (gl_at(c, G, 0, i, j, 3, l) - gl_at(c, G, 0, i + 1, j, 0, l));
     len += c->dy;
   }
-  if (vyb > KX_VDEAD) {
+  if (vyb > KX_VDEAD && !is_solid(c, i, j - 1)) {
     for (int k = 0; k < 4; ++k) s += c->dx * gl_weight(k) * (gl_at(c, G, 0, i, j, k, 0) - gl_at(c, G, 0, i, j - 1, k, 3));
     len += c->dx;
   }
-  if (-vyt > KX_VDEAD) {
+  if (-vyt > KX_VDEAD && !is_solid(c, i, j + 1)) {
     for (int k = 0; k < 4; ++k) s += c->dx * gl_weight(k) * (gl_at(c, G, 0, i, j, k, 3) - gl_at(c, G, 0, i, j + 1, k, 0));
     len += c->dx;
   }
@@ -885,6 +913,7 @@ int orc_rhs(const orc_cfg *c, const double *U, double *Umod, double *Lout,
       for (int i = 0; i < c->nx; ++i) {
         size_t cell = (size_t)j * c->nx + i;
         double a = 0.0;
+        if (is_solid(c, i, j)) { if (aleph) aleph[cell] = 0.0; continue; }
         if (c->indicator == 1) a = kxrcf_aleph(c, G, i, j);
         if (aleph) aleph[cell] = a;
         flag[cell] = c->indicator == 2 ? 1 : (c->indicator == 1 && a > 1.0);
@@ -919,24 +948,43 @@ int orc_rhs(const orc_cfg *c, const double *U, double *Umod, double *Lout,
         continue;
       }
       /* 2D: face integrals by eq. (integral2)/(integral3), cell integrals by eq. (integral1) */
+      if (is_solid(c, i, j)) continue;          /* solid cells are not updated (L = 0) */
+      /* Reading: at a face shared with a solid cell the outer state is the
+       * reflection of the cell's own (the wall-normal momentum negated) -- the
+       * wall flux of a reflective side, also at the block's corner, whose
+       * diagonal image serves only the stencils */
+      const int wxp = is_solid(c, i + 1, j), wxm = is_solid(c, i - 1, j);
+      const int wyp = is_solid(c, i, j + 1), wym = is_solid(c, i, j - 1);
       double Fx_p[4] = {0}, Fx_m[4] = {0}, Fx_pe[4] = {0}, Fx_me[4] = {0};
       double Gy_p[4] = {0}, Gy_m[4] = {0}, Gy_px[4] = {0}, Gy_mx[4] = {0};
       double Fc[4] = {0}, Gc[4] = {0};
       for (int l = 0; l < 4; ++l) {
         double wl = gl_weight(l), eta = gl_node(l);
-        for (int v = 0; v < nv; ++v) { uL[v] = gl_at(c, G, v, i, j, 3, l); uR[v] = gl_at(c, G, v, i + 1, j, 0, l); }
+        for (int v = 0; v < nv; ++v) {
+          uL[v] = gl_at(c, G, v, i, j, 3, l);
+          uR[v] = wxp ? (v == 1 ? -uL[v] : uL[v]) : gl_at(c, G, v, i + 1, j, 0, l);
+        }
         num_flux(c, uL, uR, 0, fh);
         for (int v = 0; v < nv; ++v) { Fx_p[v] += wl * fh[v]; Fx_pe[v] += wl * eta * fh[v]; }
-        for (int v = 0; v < nv; ++v) { uL[v] = gl_at(c, G, v, i - 1, j, 3, l); uR[v] = gl_at(c, G, v, i, j, 0, l); }
+        for (int v = 0; v < nv; ++v) {
+          uR[v] = gl_at(c, G, v, i, j, 0, l);
+          uL[v] = wxm ? (v == 1 ? -uR[v] : uR[v]) : gl_at(c, G, v, i - 1, j, 3, l);
+        }
         num_flux(c, uL, uR, 0, fh);
         for (int v = 0; v < nv; ++v) { Fx_m[v] += wl * fh[v]; Fx_me[v] += wl * eta * fh[v]; }
       }
       for (int k = 0; k < 4; ++k) {
         double wk = gl_weight(k), xi = gl_node(k);
-        for (int v = 0; v < nv; ++v) { uL[v] = gl_at(c, G, v, i, j, k, 3); uR[v] = gl_at(c, G, v, i, j + 1, k, 0); }
+        for (int v = 0; v < nv; ++v) {
+          uL[v] = gl_at(c, G, v, i, j, k, 3);
+          uR[v] = wyp ? (v == 2 ? -uL[v] : uL[v]) : gl_at(c, G, v, i, j + 1, k, 0);
+        }
         num_flux(c, uL, uR, 1, fh);
         for (int v = 0; v < nv; ++v) { Gy_p[v] += wk * fh[v]; Gy_px[v] += wk * xi * fh[v]; }
-        for (int v = 0; v < nv; ++v) { uL[v] = gl_at(c, G, v, i, j - 1, k, 3); uR[v] = gl_at(c, G, v, i, j, k, 0); }
+        for (int v = 0; v < nv; ++v) {
+          uR[v] = gl_at(c, G, v, i, j, k, 0);
+          uL[v] = wym ? (v == 2 ? -uR[v] : uR[v]) : gl_at(c, G, v, i, j - 1, k, 3);
+        }
         num_flux(c, uL, uR, 1, fh);
         for (int v = 0; v < nv; ++v) { Gy_m[v] += wk * fh[v]; Gy_mx[v] += wk * xi * fh[v]; }
       }
@@ -1014,6 +1062,7 @@ void orc_wave_speeds(const orc_cfg *c, const double *m, int jlo, int jhi, double
   double ax = 0.0, ay = 0.0;
   for (int j = jlo; j < jhi; ++j)
     for (int i = 0; i < c->nx; ++i) {
+      if (is_solid(c, i, j)) continue;
       double u[4];
       for (int v = 0; v < nv; ++v) u[v] = *MOM(c, (double *)m, v, 0, i, j);
       double sx, sy = 0.0;
@@ -1152,7 +1201,9 @@ void orc_totals(const orc_cfg *c, const double *m, double *sums) {
   double area = c->dx * (c->dim == 1 ? 1.0 : c->dy);
   for (int v = 0; v < nv; ++v) {
     long double s = 0.0L;
-    for (int j = 0; j < ny; ++j) for (int i = 0; i < c->nx; ++i) s += *MOM(c, (double *)m, v, 0, i, j);
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < c->nx; ++i)
+        if (!is_solid(c, i, j)) s += *MOM(c, (double *)m, v, 0, i, j);
     sums[v] = (double)(s * area);
   }
 }
