@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--no-fused", action="store_true", help="skip the fused-stage forms")
     ap.add_argument("--dmr", action="store_true",
                     help="also run Example 3.9 (double Mach reflection) at 1600 x 400 to t = 0.2")
+    ap.add_argument("--step", action="store_true",
+                    help="also run Example 3.10 (forward-facing step) at 600 x 200 to t = 4")
     ap.add_argument("--full-run", action="store_true",
                     help="also run the 2048^2 four-quadrant problem to t = 0.25 in FP64 and FP32-bulk")
     ap.add_argument("--learned-n", type=int, default=4096, help=argparse.SUPPRESS)
@@ -701,6 +703,47 @@ def run_double_mach(torch, hweno):
                                              **out}}
 
 
+def run_forward_step(torch, hweno):
+    """Example 3.10 (Mach 3 flow over a forward-facing step) at the paper's
+    600 x 200, FP64, KXRCF, CFL 0.6, host-driven steps with the positivity
+    check on, until t = 4 or the first refused step (the component-wise
+    reconstruction does not pass the step's corner: the run stops about
+    twenty steps in): steps, time reached, the refusal, throughput over the
+    steps taken and extreme values of the fluid cells."""
+    from paper_2201_12193_gb300 import workloads as W
+    p = W.forward_step_2d(200)
+    s = hweno.Solver.from_problem(p)
+    s.set_stream(torch.cuda.current_stream())
+    s.set_moments(torch.from_numpy(p.m).cuda())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    t, n, err = 0.0, 0, None
+    try:
+        while t < p.t_end and n < 100000:
+            dt = min(s.max_dt(CFL), p.t_end - t)
+            s.step(dt)
+            t += dt
+            n += 1
+    except hweno.HwenoError as e:
+        err = str(e)[:160]
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    m = s.get_moments()
+    i0, j1 = p.meta["solid"]
+    fluid = np.ones((p.ny, p.nx), bool)
+    fluid[:j1, i0:] = False
+    rho = m[0, 0]
+    pr = 0.4 * (m[3, 0] - 0.5 * (m[1, 0] ** 2 + m[2, 0] ** 2) / rho)
+    jp, ip = np.unravel_index(np.argmin(np.where(fluid, pr, np.inf)), pr.shape)
+    out = {"workload": "2d_euler_forward_step_600x200", "t_end": p.t_end, "t_reached": t, "steps": n,
+           "refused": err, "seconds": secs, "unit": UNIT,
+           "value": int(fluid.sum()) * 3 * n / secs if n else None,
+           "min_rho": float(rho[fluid].min()), "max_rho": float(rho[fluid].max()), "min_p": float(pr[fluid].min()),
+           "min_p_cell": [int(ip), int(jp)], "corner_cell": [int(i0), int(j1)]}
+    s.close()
+    return {"forward_step_600x200": out}
+
+
 def run_decomposed(args, world, rank, local):
     """N > 1: the headline problem split into N row slabs, one per rank, with the
     4-row halo exchange before every stage over NCCL and the CFL wave speeds
@@ -848,6 +891,8 @@ def run_ours(args, world, rank, local):
         forms.update(run_four_quadrant_full(torch, hweno, world, rank))
     if args.dmr:
         forms.update(run_double_mach(torch, hweno))
+    if args.step:
+        forms.update(run_forward_step(torch, hweno))
 
     if not args.no_forms and not args.no_batch:
         forms.update(run_batched(torch, hweno, args, world, rank))

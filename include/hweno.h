@@ -295,6 +295,25 @@ hweno_status hweno_advance(hweno_t h, double t_end, double cfl, long long max_st
  * does).  Applies to single and batch handles. */
 hweno_status hweno_set_positivity_check(hweno_t h, int on);
 
+/* Solid block (the forward-facing step of Sec. 3, Example 3.10; no rule for it
+ * in the paper): cells with i >= i0 and j < j1 are solid, bounded by a
+ * vertical wall face at i = i0 (when i0 > 0) and a horizontal one at j = j1
+ * (when j1 < ny).  Reading: a solid cell in the stencil of a fluid cell is
+ * that cell's wall image -- mirrored across the vertical face when the
+ * viewing cell lies left of it, across the horizontal face when it lies
+ * above it, across both (through the corner) for the cell diagonal to the
+ * corner -- each crossed face negating its wall-normal momentum and normal
+ * first moment; a face shared with a solid cell carries the
+ * reflective wall flux of the fluid side's own values and is never a KXRCF
+ * inflow face; solid cells are not reconstructed, flagged or updated (their
+ * state passes through) and take no part in the CFL rule or the totals.
+ * j1 = 0 removes the block.  Single 2D Euler FP64 handles without the learned
+ * indicator or the fused stage (else ESTATE); EINVAL unless 0 <= i0 < nx,
+ * 1 <= j1 <= ny, at least 4 fluid cells lie beyond each face and the sides
+ * the block touches (the right one when i0 > 0, the bottom one when j1 < ny)
+ * are not periodic. */
+hweno_status hweno_set_solid(hweno_t h, int i0, int j1);
+
 /* One fused kernel per Runge-Kutta stage (on = 1) instead of the pipeline of
  * four launches (on = 0, default): Steps 1-3 of Sec. 2.2 (reconstruction,
  * eq. (KXRCF_), eq. (vi), the troubled re-reconstruction, HLLC fluxes,

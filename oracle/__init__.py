@@ -58,7 +58,9 @@ def make_cfg(dim, nx, ny=1, dx=1.0, dy=1.0, eq="euler", adv=(1.0, 0.0), gamma=1.
     fixed ghost states: "a" inside the segment (centre coordinate along the
     side below c0 + speed * t; no segment when "c0" is absent), "b" elsewhere
     on an "inflow" side.  solid: None or (i0, j1): cells with i >= i0 and
-    j < j1 are solid (a forward-facing step; 2D Euler)."""
+    j < j1 are solid (a forward-facing step; 2D Euler).  The block touches
+    the right side (when i0 > 0) and the bottom side (when j1 < ny), which
+    therefore may not be periodic: a wrap would meet the block from behind."""
     c = Cfg()
     c.dim, c.nx, c.ny = dim, nx, (ny if dim == 2 else 1)
     c.dx, c.dy = dx, (dy if dim == 2 else 1.0)
@@ -72,6 +74,8 @@ def make_cfg(dim, nx, ny=1, dx=1.0, dy=1.0, eq="euler", adv=(1.0, 0.0), gamma=1.
     c.mod_in_L_only = int(bool(mod_in_L_only))
     if solid is not None:
         c.sol_i, c.sol_j = int(solid[0]), int(solid[1])
+        if (c.sol_i > 0 and bc[1] == "periodic") or (c.sol_j < c.ny and bc[2] == "periodic"):
+            raise ValueError("solid block: the sides it touches may not be periodic")
     for k, f in enumerate(fixed or [None] * 4):
         if not f:
             continue

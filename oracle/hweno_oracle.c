@@ -505,23 +505,27 @@ static int is_solid(const orc_cfg *c, int i, int j) {
   return c->dim == 2 && c->sol_j > 0 && i >= c->sol_i && i < c->nx && j >= 0 && j < c->sol_j;
 }
 
-/* Reading (the paper gives no rule for solid cells inside the domain): a solid
- * cell within reach of the fluid is the wall image of a fluid cell across the
- * nearer face of the block -- a cell a columns right of the vertical face and
- * b rows below the horizontal one mirrors across the vertical face when
- * a < b, across the horizontal face when b < a, and across both (the corner
- * diagonal) when a = b; the wall-normal momentum of each crossed face is
- * negated with the normal first moment, as at a reflective side. */
-static void solid_image(const orc_cfg *c, image_t *r) {
+/* Reading (the paper gives no rule for solid cells inside the domain; R27):
+ * the block's faces are reflective walls, so a solid cell in the stencil of
+ * the fluid cell (vi, vj) is that cell's wall image -- mirrored across the
+ * vertical face x = sol_i when the viewer lies left of it (vi < sol_i), across
+ * the horizontal face y = sol_j when the viewer lies above it (vj >= sol_j),
+ * across both (a point reflection through the corner) for the one viewer
+ * diagonal to the corner.  Each crossed face negates its wall-normal
+ * momentum and its normal first moment, as a reflective side does.  The
+ * image depends on the viewer: the corner cell seen from its left
+ * neighbour is that neighbour's mirror in x, seen from above the mirror in
+ * y of the cell above it, as for the ghosts of the two rectangles the
+ * L-shaped fluid region is made of. */
+static void solid_image(const orc_cfg *c, int vi, int vj, image_t *r) {
   if (!is_solid(c, r->i, r->j)) return;
-  const int a = r->i - c->sol_i + 1, b = c->sol_j - r->j;
-  const int hasx = c->sol_i > 0, hasy = c->sol_j < c->ny;
-  const int mx = hasx && (!hasy || a <= b), my = hasy && (!hasx || b <= a);
-  if (mx) { r->i = 2 * c->sol_i - 1 - r->i; r->sx = -r->sx; r->rx ^= 1; }
-  if (my) { r->j = 2 * c->sol_j - 1 - r->j; r->sy = -r->sy; r->ry ^= 1; }
+  if (vi < c->sol_i) { r->i = 2 * c->sol_i - 1 - r->i; r->sx = -r->sx; r->rx ^= 1; }
+  if (vj >= c->sol_j) { r->j = 2 * c->sol_j - 1 - r->j; r->sy = -r->sy; r->ry ^= 1; }
 }
 
-static image_t cell_image(const orc_cfg *c, int i, int j) {
+/* The image of cell (i, j), inside the grid or a ghost, as the stencil of the
+ * fluid cell (vi, vj) sees it: boundary sides first, then the solid block. */
+static image_t cell_image(const orc_cfg *c, int vi, int vj, int i, int j) {
   image_t r = {i, j, 1, 1, 0, 0, NULL};
   if (c->dim == 2 && (j < 0 || j >= c->ny)) {
     int side = j < 0 ? 2 : 3;
@@ -537,7 +541,7 @@ static image_t cell_image(const orc_cfg *c, int i, int j) {
     if (c->bc[side] == 0) { r.i = ((i % c->nx) + c->nx) % c->nx; }
     else { r.i = i < 0 ? -1 - i : 2 * c->nx - 1 - i; r.sx = -1; r.rx = c->bc[side] == 2; }
   }
-  solid_image(c, &r);
+  solid_image(c, vi, vj, &r);
   return r;
 }
 
@@ -555,9 +559,9 @@ static double *MOM(const orc_cfg *c, double *m, int var, int mom, int i, int j) 
   return m + (((size_t)var * nmoms(c) + mom) * ncell(c) + (size_t)j * c->nx + i);
 }
 
-/* moment of any (possibly ghost) cell */
-static double mom_at(const orc_cfg *c, const double *m, int var, int mom, int i, int j) {
-  image_t im = cell_image(c, i, j);
+/* moment of the stencil cell (i + ox, j + oy) of the cell (i, j), possibly a ghost */
+static double mom_at(const orc_cfg *c, const double *m, int var, int mom, int i, int j, int ox, int oy) {
+  image_t im = cell_image(c, i, j, i + ox, j + oy);
   if (im.fix) return mom == 0 ? wall_sign(&im, var) * im.fix[var] : 0.0;
   double v = *MOM(c, (double *)m, var, mom, im.i, im.j);
   if (mom == 1) v *= im.sx;
@@ -565,9 +569,10 @@ static double mom_at(const orc_cfg *c, const double *m, int var, int mom, int i,
   return v * wall_sign(&im, var);
 }
 
-/* GL values array G[cell][var][16]; value of any (possibly ghost) cell at node (k,l) */
-static double gl_at(const orc_cfg *c, const double *G, int var, int i, int j, int k, int l) {
-  image_t im = cell_image(c, i, j);
+/* GL values array G[cell][var][16]; value at node (k,l) of the neighbour
+ * (i + ox, j + oy) of the cell (i, j), possibly a ghost */
+static double gl_at(const orc_cfg *c, const double *G, int var, int i, int j, int ox, int oy, int k, int l) {
+  image_t im = cell_image(c, i, j, i + ox, j + oy);
   if (im.fix) return wall_sign(&im, var) * im.fix[var];
   if (im.sx < 0) k = 3 - k;
   if (im.sy < 0) l = 3 - l;
@@ -609,7 +614,18 @@ static double kx_velocity(const orc_cfg *c, const double *u, int dir) {
  * Reading (2D): the rotated 1D flux with the tangential velocity carried in
  * the star state.  Reading (branches): 0<=sL -> fL; else 0<=s* -> f*L; else
  * 0<=sR -> f*R; else fR.  p*, s* literal, no clamp. */
+/* wall = 1: the face of a solid block, uR (or uL) the reflection of the other
+ * side; the star branch is taken whatever the sign of the wave-speed
+ * estimate s_L (s_R), so the flux has no mass or energy part (s* = 0) and the
+ * normal momentum flux is the star pressure.  Reading (R27): the estimate of
+ * eq. (COEF) gives s_L > 0 for flow running into a wall faster than about
+ * its sound speed, where the first branch of eq. (f_HLLC) would let the gas
+ * through the wall. */
+static void hllc_w(const orc_cfg *c, const double *uL, const double *uR, int dir, double *F, int wall);
 static void hllc(const orc_cfg *c, const double *uL, const double *uR, int dir, double *F) {
+  hllc_w(c, uL, uR, dir, F, 0);
+}
+static void hllc_w(const orc_cfg *c, const double *uL, const double *uR, int dir, double *F, int wall) {
   double g = c->gamma;
   int two = c->dim == 2;
   int in = 1 + dir, it = 2 - dir;   /* momentum components: normal / tangential (2D) */
@@ -631,10 +647,10 @@ static void hllc(const orc_cfg *c, const double *uL, const double *uR, int dir, 
   double fL[4], fR[4];
   phys_flux(c, uL, dir, fL);
   phys_flux(c, uR, dir, fR);
-  if (0.0 <= sL) { for (int v = 0; v < nv; ++v) F[v] = fL[v]; return; }
+  if (!wall && 0.0 <= sL) { for (int v = 0; v < nv; ++v) F[v] = fL[v]; return; }
   const double *uK; const double *fK; double sK, rK, mK, tK, EK, pK;
   if (0.0 <= ss) { uK = uL; fK = fL; sK = sL; rK = rL; mK = mL; tK = tL; EK = EL; pK = pL; }
-  else if (0.0 <= sR) { uK = uR; fK = fR; sK = sR; rK = rR; mK = mR; tK = tR; EK = ER; pK = pR; }
+  else if (wall || 0.0 <= sR) { uK = uR; fK = fR; sK = sR; rK = rR; mK = mR; tK = tR; EK = ER; pK = pR; }
   else { for (int v = 0; v < nv; ++v) F[v] = fR[v]; return; }
   double fac = rK * (sK - mK) / (sK - ss);
   double us[4];
@@ -667,17 +683,17 @@ static void num_flux(const orc_cfg *c, const double *uL, const double *uR, int d
 static void gather_stencil(const orc_cfg *c, const double *m, int var, int i, int j, stencil_t *st) {
   if (c->dim == 1) {
     for (int o = -1; o <= 1; ++o) {
-      st->ub[o + 1] = mom_at(c, m, var, 0, i + o, 0);
-      st->vb[o + 1] = mom_at(c, m, var, 1, i + o, 0);
+      st->ub[o + 1] = mom_at(c, m, var, 0, i, 0, o, 0);
+      st->vb[o + 1] = mom_at(c, m, var, 1, i, 0, o, 0);
     }
     return;
   }
   for (int oy = -1; oy <= 1; ++oy)
     for (int ox = -1; ox <= 1; ++ox) {
       int idx = (oy + 1) * 3 + (ox + 1);
-      st->ub[idx] = mom_at(c, m, var, 0, i + ox, j + oy);
-      st->vb[idx] = mom_at(c, m, var, 1, i + ox, j + oy);
-      st->wb[idx] = mom_at(c, m, var, 2, i + ox, j + oy);
+      st->ub[idx] = mom_at(c, m, var, 0, i, j, ox, oy);
+      st->vb[idx] = mom_at(c, m, var, 1, i, j, ox, oy);
+      st->wb[idx] = mom_at(c, m, var, 2, i, j, ox, oy);
     }
 }
 
@@ -710,7 +726,7 @@ static void reconstruct_all(const orc_cfg *c, const double *m, double *G, const 
       if (is_solid(c, i, j)) continue;      /* never read: solid cells are images */
       if (c->charwise && c->dim == 1 && c->eq == 2) {
         double R[3][3], Lm[3][3], u0[3];
-        for (int v = 0; v < 3; ++v) u0[v] = mom_at(c, m, v, 0, i, 0);
+        for (int v = 0; v < 3; ++v) u0[v] = mom_at(c, m, v, 0, i, 0, 0, 0);
         euler1d_eig(c->gamma, u0, R, Lm);
         stencil_t sv[3];
         for (int v = 0; v < 3; ++v) gather_stencil(c, m, v, i, j, &sv[v]);
@@ -756,51 +772,51 @@ static double kxrcf_aleph(const orc_cfg *c, const double *G, int i, int j) {
   double h = c->dx;
   if (c->dim == 1) {
     /* face velocities */
-    for (int v = 0; v < nv; ++v) { un[v] = gl_at(c, G, v, i - 1, 0, 3, 0); u[v] = gl_at(c, G, v, i, 0, 0, 0); }
+    for (int v = 0; v < nv; ++v) { un[v] = gl_at(c, G, v, i, 0, -1, 0, 3, 0); u[v] = gl_at(c, G, v, i, 0, 0, 0, 0, 0); }
     double vl = 0.5 * (kx_velocity(c, un, 0) + kx_velocity(c, u, 0));
-    for (int v = 0; v < nv; ++v) { u[v] = gl_at(c, G, v, i, 0, 3, 0); un[v] = gl_at(c, G, v, i + 1, 0, 0, 0); }
+    for (int v = 0; v < nv; ++v) { u[v] = gl_at(c, G, v, i, 0, 0, 0, 3, 0); un[v] = gl_at(c, G, v, i, 0, 1, 0, 0, 0); }
     double vr = 0.5 * (kx_velocity(c, u, 0) + kx_velocity(c, un, 0));
-    double jl = gl_at(c, G, 0, i, 0, 0, 0) - gl_at(c, G, 0, i - 1, 0, 3, 0);
-    double jr = gl_at(c, G, 0, i, 0, 3, 0) - gl_at(c, G, 0, i + 1, 0, 0, 0);
+    double jl = gl_at(c, G, 0, i, 0, 0, 0, 0, 0) - gl_at(c, G, 0, i, 0, -1, 0, 3, 0);
+    double jr = gl_at(c, G, 0, i, 0, 0, 0, 3, 0) - gl_at(c, G, 0, i, 0, 1, 0, 0, 0);
     double s = jl * (vl > KX_VDEAD ? 1.0 : 0.0) + jr * (-vr > KX_VDEAD ? 1.0 : 0.0);
     double nrm = 0.0;
-    for (int k = 0; k < 4; ++k) { double a = fabs(gl_at(c, G, 0, i, 0, k, 0)); if (a > nrm) nrm = a; }
+    for (int k = 0; k < 4; ++k) { double a = fabs(gl_at(c, G, 0, i, 0, 0, 0, k, 0)); if (a > nrm) nrm = a; }
     if (nrm == 0.0) return 0.0;
     return fabs(s) / (h * h * nrm);
   }
   double vxl = 0.0, vxr = 0.0, vyb = 0.0, vyt = 0.0;
   for (int l = 0; l < 4; ++l) {
-    for (int v = 0; v < nv; ++v) { un[v] = gl_at(c, G, v, i - 1, j, 3, l); u[v] = gl_at(c, G, v, i, j, 0, l); }
+    for (int v = 0; v < nv; ++v) { un[v] = gl_at(c, G, v, i, j, -1, 0, 3, l); u[v] = gl_at(c, G, v, i, j, 0, 0, 0, l); }
     vxl += gl_weight(l) * 0.5 * (kx_velocity(c, un, 0) + kx_velocity(c, u, 0));
-    for (int v = 0; v < nv; ++v) { u[v] = gl_at(c, G, v, i, j, 3, l); un[v] = gl_at(c, G, v, i + 1, j, 0, l); }
+    for (int v = 0; v < nv; ++v) { u[v] = gl_at(c, G, v, i, j, 0, 0, 3, l); un[v] = gl_at(c, G, v, i, j, 1, 0, 0, l); }
     vxr += gl_weight(l) * 0.5 * (kx_velocity(c, u, 0) + kx_velocity(c, un, 0));
   }
   for (int k = 0; k < 4; ++k) {
-    for (int v = 0; v < nv; ++v) { un[v] = gl_at(c, G, v, i, j - 1, k, 3); u[v] = gl_at(c, G, v, i, j, k, 0); }
+    for (int v = 0; v < nv; ++v) { un[v] = gl_at(c, G, v, i, j, 0, -1, k, 3); u[v] = gl_at(c, G, v, i, j, 0, 0, k, 0); }
     vyb += gl_weight(k) * 0.5 * (kx_velocity(c, un, 1) + kx_velocity(c, u, 1));
-    for (int v = 0; v < nv; ++v) { u[v] = gl_at(c, G, v, i, j, k, 3); un[v] = gl_at(c, G, v, i, j + 1, k, 0); }
+    for (int v = 0; v < nv; ++v) { u[v] = gl_at(c, G, v, i, j, 0, 0, k, 3); un[v] = gl_at(c, G, v, i, j, 0, 1, k, 0); }
     vyt += gl_weight(k) * 0.5 * (kx_velocity(c, u, 1) + kx_velocity(c, un, 1));
   }
   double s = 0.0, len = 0.0;
   /* Reading: a face shared with a solid cell is a wall, never an inflow face */
   if (vxl > KX_VDEAD && !is_solid(c, i - 1, j)) {
-    for (int l = 0; l < 4; ++l) s += c->dy * gl_weight(l) * (gl_at(c, G, 0, i, j, 0, l) - gl_at(c, G, 0, i - 1, j, 3, l));
+    for (int l = 0; l < 4; ++l) s += c->dy * gl_weight(l) * (gl_at(c, G, 0, i, j, 0, 0, 0, l) - gl_at(c, G, 0, i, j, -1, 0, 3, l));
     len += c->dy;
   }
   if (-vxr > KX_VDEAD && !is_solid(c, i + 1, j)) {
-    for (int l = 0; l < 4; ++l) s += c->dy * gl_weight(l) * (gl_at(c, G, 0, i, j, 3, l) - gl_at(c, G, 0, i + 1, j, 0, l));
+    for (int l = 0; l < 4; ++l) s += c->dy * gl_weight(l) * (gl_at(c, G, 0, i, j, 0, 0, 3, l) - gl_at(c, G, 0, i, j, 1, 0, 0, l));
     len += c->dy;
   }
   if (vyb > KX_VDEAD && !is_solid(c, i, j - 1)) {
-    for (int k = 0; k < 4; ++k) s += c->dx * gl_weight(k) * (gl_at(c, G, 0, i, j, k, 0) - gl_at(c, G, 0, i, j - 1, k, 3));
+    for (int k = 0; k < 4; ++k) s += c->dx * gl_weight(k) * (gl_at(c, G, 0, i, j, 0, 0, k, 0) - gl_at(c, G, 0, i, j, 0, -1, k, 3));
     len += c->dx;
   }
   if (-vyt > KX_VDEAD && !is_solid(c, i, j + 1)) {
-    for (int k = 0; k < 4; ++k) s += c->dx * gl_weight(k) * (gl_at(c, G, 0, i, j, k, 3) - gl_at(c, G, 0, i, j + 1, k, 0));
+    for (int k = 0; k < 4; ++k) s += c->dx * gl_weight(k) * (gl_at(c, G, 0, i, j, 0, 0, k, 3) - gl_at(c, G, 0, i, j, 0, 1, k, 0));
     len += c->dx;
   }
   double nrm = 0.0;
-  for (int k = 0; k < 4; ++k) for (int l = 0; l < 4; ++l) { double a = fabs(gl_at(c, G, 0, i, j, k, l)); if (a > nrm) nrm = a; }
+  for (int k = 0; k < 4; ++k) for (int l = 0; l < 4; ++l) { double a = fabs(gl_at(c, G, 0, i, j, 0, 0, k, l)); if (a > nrm) nrm = a; }
   if (len == 0.0 || nrm == 0.0) return 0.0;
   return fabs(s) / len / (h * h * nrm);
 }
@@ -830,13 +846,13 @@ static int tvb_changes(double a, double b, double cc, double bound) {
 
 static int tvb_flag(const orc_cfg *c, const double *U, int i, int j) {
   const double bound = c->tvb_m * c->dx * c->dx;
-  const double u0 = mom_at(c, U, 0, 0, i, j);
-  const double ax = 6.0 * mom_at(c, U, 0, 1, i, j);
-  const double dxp = mom_at(c, U, 0, 0, i + 1, j) - u0, dxm = u0 - mom_at(c, U, 0, 0, i - 1, j);
+  const double u0 = mom_at(c, U, 0, 0, i, j, 0, 0);
+  const double ax = 6.0 * mom_at(c, U, 0, 1, i, j, 0, 0);
+  const double dxp = mom_at(c, U, 0, 0, i, j, 1, 0) - u0, dxm = u0 - mom_at(c, U, 0, 0, i, j, -1, 0);
   if (tvb_changes(ax, dxp, dxm, bound)) return 1;
   if (c->dim == 1) return 0;
-  const double ay = 6.0 * mom_at(c, U, 0, 2, i, j);
-  const double dyp = mom_at(c, U, 0, 0, i, j + 1) - u0, dym = u0 - mom_at(c, U, 0, 0, i, j - 1);
+  const double ay = 6.0 * mom_at(c, U, 0, 2, i, j, 0, 0);
+  const double dyp = mom_at(c, U, 0, 0, i, j, 0, 1) - u0, dym = u0 - mom_at(c, U, 0, 0, i, j, 0, -1);
   return tvb_changes(ay, dyp, dym, bound);
 }
 
@@ -851,13 +867,13 @@ static void modify_cells(const orc_cfg *c, const double *U, double *Umod, const 
       size_t cell = (size_t)j * c->nx + i;
       if (!sel[cell]) continue;
       for (int v = 0; v < nv; ++v) {
-        *MOM(c, Umod, v, 1, i, j) = w[0] * mom_at(c, U, v, 0, i - 1, j) + w[1] * mom_at(c, U, v, 0, i, j)
-                                  + w[2] * mom_at(c, U, v, 0, i + 1, j)
-                                  + w[3] * mom_at(c, U, v, 1, i - 1, j) + w[4] * mom_at(c, U, v, 1, i + 1, j);
+        *MOM(c, Umod, v, 1, i, j) = w[0] * mom_at(c, U, v, 0, i, j, -1, 0) + w[1] * mom_at(c, U, v, 0, i, j, 0, 0)
+                                  + w[2] * mom_at(c, U, v, 0, i, j, 1, 0)
+                                  + w[3] * mom_at(c, U, v, 1, i, j, -1, 0) + w[4] * mom_at(c, U, v, 1, i, j, 1, 0);
         if (c->dim == 2)
-          *MOM(c, Umod, v, 2, i, j) = w[0] * mom_at(c, U, v, 0, i, j - 1) + w[1] * mom_at(c, U, v, 0, i, j)
-                                    + w[2] * mom_at(c, U, v, 0, i, j + 1)
-                                    + w[3] * mom_at(c, U, v, 2, i, j - 1) + w[4] * mom_at(c, U, v, 2, i, j + 1);
+          *MOM(c, Umod, v, 2, i, j) = w[0] * mom_at(c, U, v, 0, i, j, 0, -1) + w[1] * mom_at(c, U, v, 0, i, j, 0, 0)
+                                    + w[2] * mom_at(c, U, v, 0, i, j, 0, 1)
+                                    + w[3] * mom_at(c, U, v, 2, i, j, 0, -1) + w[4] * mom_at(c, U, v, 2, i, j, 0, 1);
       }
     }
 }
@@ -931,13 +947,13 @@ int orc_rhs(const orc_cfg *c, const double *U, double *Umod, double *Lout,
       double uL[4], uR[4], fh[4], fp[4];
       if (c->dim == 1) {
         double fm[4], fpl[4], F[4] = {0, 0, 0, 0};
-        for (int v = 0; v < nv; ++v) { uL[v] = gl_at(c, G, v, i - 1, 0, 3, 0); uR[v] = gl_at(c, G, v, i, 0, 0, 0); }
+        for (int v = 0; v < nv; ++v) { uL[v] = gl_at(c, G, v, i, 0, -1, 0, 3, 0); uR[v] = gl_at(c, G, v, i, 0, 0, 0, 0, 0); }
         num_flux(c, uL, uR, 0, fm);
-        for (int v = 0; v < nv; ++v) { uL[v] = gl_at(c, G, v, i, 0, 3, 0); uR[v] = gl_at(c, G, v, i + 1, 0, 0, 0); }
+        for (int v = 0; v < nv; ++v) { uL[v] = gl_at(c, G, v, i, 0, 0, 0, 3, 0); uR[v] = gl_at(c, G, v, i, 0, 1, 0, 0, 0); }
         num_flux(c, uL, uR, 0, fpl);
         for (int k = 0; k < 4; ++k) {           /* eq. (F) */
           double u[4];
-          for (int v = 0; v < nv; ++v) u[v] = gl_at(c, G, v, i, 0, k, 0);
+          for (int v = 0; v < nv; ++v) u[v] = gl_at(c, G, v, i, 0, 0, 0, k, 0);
           phys_flux(c, u, 0, fp);
           for (int v = 0; v < nv; ++v) F[v] += gl_weight(k) * fp[v];
         }
@@ -961,37 +977,37 @@ int orc_rhs(const orc_cfg *c, const double *U, double *Umod, double *Lout,
       for (int l = 0; l < 4; ++l) {
         double wl = gl_weight(l), eta = gl_node(l);
         for (int v = 0; v < nv; ++v) {
-          uL[v] = gl_at(c, G, v, i, j, 3, l);
-          uR[v] = wxp ? (v == 1 ? -uL[v] : uL[v]) : gl_at(c, G, v, i + 1, j, 0, l);
+          uL[v] = gl_at(c, G, v, i, j, 0, 0, 3, l);
+          uR[v] = wxp ? (v == 1 ? -uL[v] : uL[v]) : gl_at(c, G, v, i, j, 1, 0, 0, l);
         }
-        num_flux(c, uL, uR, 0, fh);
+        if (wxp) hllc_w(c, uL, uR, 0, fh, 1); else num_flux(c, uL, uR, 0, fh);
         for (int v = 0; v < nv; ++v) { Fx_p[v] += wl * fh[v]; Fx_pe[v] += wl * eta * fh[v]; }
         for (int v = 0; v < nv; ++v) {
-          uR[v] = gl_at(c, G, v, i, j, 0, l);
-          uL[v] = wxm ? (v == 1 ? -uR[v] : uR[v]) : gl_at(c, G, v, i - 1, j, 3, l);
+          uR[v] = gl_at(c, G, v, i, j, 0, 0, 0, l);
+          uL[v] = wxm ? (v == 1 ? -uR[v] : uR[v]) : gl_at(c, G, v, i, j, -1, 0, 3, l);
         }
-        num_flux(c, uL, uR, 0, fh);
+        if (wxm) hllc_w(c, uL, uR, 0, fh, 1); else num_flux(c, uL, uR, 0, fh);
         for (int v = 0; v < nv; ++v) { Fx_m[v] += wl * fh[v]; Fx_me[v] += wl * eta * fh[v]; }
       }
       for (int k = 0; k < 4; ++k) {
         double wk = gl_weight(k), xi = gl_node(k);
         for (int v = 0; v < nv; ++v) {
-          uL[v] = gl_at(c, G, v, i, j, k, 3);
-          uR[v] = wyp ? (v == 2 ? -uL[v] : uL[v]) : gl_at(c, G, v, i, j + 1, k, 0);
+          uL[v] = gl_at(c, G, v, i, j, 0, 0, k, 3);
+          uR[v] = wyp ? (v == 2 ? -uL[v] : uL[v]) : gl_at(c, G, v, i, j, 0, 1, k, 0);
         }
-        num_flux(c, uL, uR, 1, fh);
+        if (wyp) hllc_w(c, uL, uR, 1, fh, 1); else num_flux(c, uL, uR, 1, fh);
         for (int v = 0; v < nv; ++v) { Gy_p[v] += wk * fh[v]; Gy_px[v] += wk * xi * fh[v]; }
         for (int v = 0; v < nv; ++v) {
-          uR[v] = gl_at(c, G, v, i, j, k, 0);
-          uL[v] = wym ? (v == 2 ? -uR[v] : uR[v]) : gl_at(c, G, v, i, j - 1, k, 3);
+          uR[v] = gl_at(c, G, v, i, j, 0, 0, k, 0);
+          uL[v] = wym ? (v == 2 ? -uR[v] : uR[v]) : gl_at(c, G, v, i, j, 0, -1, k, 3);
         }
-        num_flux(c, uL, uR, 1, fh);
+        if (wym) hllc_w(c, uL, uR, 1, fh, 1); else num_flux(c, uL, uR, 1, fh);
         for (int v = 0; v < nv; ++v) { Gy_m[v] += wk * fh[v]; Gy_mx[v] += wk * xi * fh[v]; }
       }
       for (int k = 0; k < 4; ++k)
         for (int l = 0; l < 4; ++l) {
           double u[4], fx[4], gy[4];
-          for (int v = 0; v < nv; ++v) u[v] = gl_at(c, G, v, i, j, k, l);
+          for (int v = 0; v < nv; ++v) u[v] = gl_at(c, G, v, i, j, 0, 0, k, l);
           phys_flux(c, u, 0, fx);
           phys_flux(c, u, 1, gy);
           for (int v = 0; v < nv; ++v) {

@@ -20,6 +20,7 @@ struct Nbr {
   int yj[3], ys[3];     // image row and sign of the y first moment, for oy = -1, 0, 1
   int neg[3][3];        // variables negated by reflective walls, [oy + 1][ox + 1]
   int fs[3][3];         // fixed-state ghost entry (-1: none), set when FIX
+  int ci[3][3], cj[3][3], csx[3][3], csy[3][3];   // FIX: the full image of each cell
 };
 
 template <bool FIX>
@@ -39,14 +40,19 @@ __device__ __forceinline__ Nbr neighbours(const Prob& P, int i, int j) {
 #pragma unroll
     for (int ox = 0; ox < 3; ++ox) n.neg[oy][ox] = nx[ox] | ny[oy];
   if constexpr (FIX) {
-    // fixed-state ghosts break the separable form: the full image of each cell
+    // fixed-state ghosts and the solid block break the separable form: the full
+    // image of each cell (equal to the separable one wherever neither applies)
 #pragma unroll
     for (int oy = 0; oy < 3; ++oy)
 #pragma unroll
       for (int ox = 0; ox < 3; ++ox) {
-        const Img m = image(P, i + ox - 1, j + oy - 1);
+        const Img m = image(P, i + ox - 1, j + oy - 1, i, j);
         n.fs[oy][ox] = m.fs;
-        if (m.fs >= 0) n.neg[oy][ox] = m.neg;
+        n.neg[oy][ox] = m.fs >= 0 ? m.neg : (P.sol_j > 0 ? m.neg : n.neg[oy][ox]);
+        n.ci[oy][ox] = m.fs >= 0 ? n.xi[ox] : m.i;
+        n.cj[oy][ox] = m.fs >= 0 ? n.yj[oy] : m.j;
+        n.csx[oy][ox] = m.fs >= 0 ? n.xs[ox] : m.sx;
+        n.csy[oy][ox] = m.fs >= 0 ? n.ys[oy] : m.sy;
       }
   }
   return n;
@@ -69,7 +75,8 @@ __device__ __forceinline__ double load_mom(const Prob& P, const double* __restri
     const int fs = n.fs[oy + 1][ox + 1];
     if (fs >= 0) return kind == 0 ? ((n.neg[oy + 1][ox + 1] >> var) & 1 ? -1.0 : 1.0) * P.fixtab[4 * fs + var] : 0.0;
   }
-  const int ci = n.xi[ox + 1], cj = n.yj[oy + 1];
+  const int ci = FIX ? n.ci[oy + 1][ox + 1] : n.xi[ox + 1], cj = FIX ? n.cj[oy + 1][ox + 1] : n.yj[oy + 1];
+  const int sxm = FIX ? n.csx[oy + 1][ox + 1] : n.xs[ox + 1], sym = FIX ? n.csy[oy + 1][ox + 1] : n.ys[oy + 1];
   const long long so = (long long)cj * P.pitch + ci;
   if constexpr (SIGNBIT) {
     // FP64 / FP32 paths: the sign bit flipped by integer work (no FP64
@@ -83,8 +90,8 @@ __device__ __forceinline__ double load_mom(const Prob& P, const double* __restri
         v = Mod[(long long)(var * 2 + kind - 1) * P.plane + so];
       else
         v = U[(long long)(var * 3 + kind) * P.plane + so];
-      if (kind == 1 && n.xs[ox + 1] < 0) flip ^= 1ull;
-      if (kind == 2 && n.ys[oy + 1] < 0) flip ^= 1ull;
+      if (kind == 1 && sxm < 0) flip ^= 1ull;
+      if (kind == 2 && sym < 0) flip ^= 1ull;
     }
     return __longlong_as_double(__double_as_longlong(v) ^ (long long)(flip << 63));
   } else {
@@ -98,8 +105,8 @@ __device__ __forceinline__ double load_mom(const Prob& P, const double* __restri
       v = Mod[(long long)(var * 2 + kind - 1) * P.plane + so];
     else
       v = U[(long long)(var * 3 + kind) * P.plane + so];
-    if (kind == 1 && n.xs[ox + 1] < 0) v = -v;
-    if (kind == 2 && n.ys[oy + 1] < 0) v = -v;
+    if (kind == 1 && sxm < 0) v = -v;
+    if (kind == 2 && sym < 0) v = -v;
     return (n.neg[oy + 1][ox + 1] >> var) & 1 ? -v : v;
   }
 }
@@ -198,6 +205,7 @@ __global__ void __launch_bounds__(RB, (is_df64<T>::value ? 4 : 1)) rec2d_kernel(
   if (FLAGGED && rerec && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(rerec, (unsigned long long)n);
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int cell = FLAGGED ? list[t] : (int)t;
+    if (FIX && is_solid(P, cell % P.nx, cell / P.nx)) continue;   // solid cells are images, never read
     rec2d_cell<T, NV, MODE, FIX>(P, W, B, U, mask, Mod, cell % P.nx, cell / P.nx, G, aux);
   }
 }
@@ -207,6 +215,10 @@ template <typename T>
 __device__ __forceinline__ bool flag2d_cell(const Prob& P, const Weights<T>& W, const double* __restrict__ U,
                                             const T* __restrict__ G, const T* __restrict__ aux, int i, int j,
                                             double* __restrict__ aleph) {
+  if (P.sol_j > 0 && is_solid(P, i, j)) {
+    if (aleph) aleph[(long long)j * P.nx + i] = 0.0;
+    return false;
+  }
   if (P.indicator == IND_ALL) return true;
   if (P.indicator == IND_TVB) return tvb_cell(P, U, i, j);
   if (P.indicator != IND_KXRCF) return false;
@@ -220,7 +232,8 @@ __device__ __forceinline__ bool flag2d_cell(const Prob& P, const Weights<T>& W, 
 template <int NV>
 __device__ __forceinline__ void modify2d_cell(const Prob& P, const double* __restrict__ U, double* __restrict__ Mod,
                                               int i, int j) {
-  const Img L = image(P, i - 1, j), R = image(P, i + 1, j), Bo = image(P, i, j - 1), Tp = image(P, i, j + 1);
+  const Img L = image(P, i - 1, j, i, j), R = image(P, i + 1, j, i, j), Bo = image(P, i, j - 1, i, j),
+            Tp = image(P, i, j + 1, i, j);
   const long long o = (long long)j * P.pitch + i;
   // moment (kind 1: x, 2: y first moment) of an edge neighbour; a fixed-state
   // ghost has its state as average and zero first moments
@@ -341,20 +354,70 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
       const int l = f & 3, face = f >> 2, c = face % (TXV + 1), r = face / (TXV + 1);
       const int il = i0 + c - 1, jj = j0 + r;
       if (jj >= P.ny || il >= P.nx) continue;
-      gl_state<T, NV>(P, G, image(P, il, jj), 3, l, uL);
-      gl_state<T, NV>(P, G, image(P, il + 1, jj), 0, l, uR);
-      num_flux<T, NV>(P, uL, uR, 0, xf[r][c][l]);
+      const bool sl = P.sol_j > 0 && is_solid(P, il, jj), sr = P.sol_j > 0 && is_solid(P, il + 1, jj);
+      // a face no fluid cell uses (solid on one side, solid or outside on the
+      // other) is skipped: only solid cells would read it, and they are not updated
+      if (P.sol_j > 0 && (sl || il < 0) && (sr || il + 1 >= P.nx)) continue;
+      // a face shared with a solid cell: the outer state is the reflection of the fluid side's own
+      if (!sl) gl_state<T, NV>(P, G, image(P, il, jj), 3, l, uL);
+      if (!sr) gl_state<T, NV>(P, G, image(P, il + 1, jj), 0, l, uR);
+      if (sr && !sl) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) uR[v] = v == 1 ? -uL[v] : uL[v];
+      }
+      if (sl && !sr) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) uL[v] = v == 1 ? -uR[v] : uR[v];
+      }
+      if constexpr (NV == 4) {
+        if (sl || sr) hllc<T, NV, true>(P, uL, uR, 0, xf[r][c][l]);
+        else num_flux<T, NV>(P, uL, uR, 0, xf[r][c][l]);
+      } else {
+        num_flux<T, NV>(P, uL, uR, 0, xf[r][c][l]);
+      }
     } else {
       const int g = f - NXP, k = g & 3, face = g >> 2, c = face % TXV, r = face / TXV;
       const int ii = i0 + c, jb = j0 + r - 1;
       if (ii >= P.nx || jb >= P.ny) continue;
-      gl_state<T, NV>(P, G, image(P, ii, jb), k, 3, uL);
-      gl_state<T, NV>(P, G, image(P, ii, jb + 1), k, 0, uR);
-      num_flux<T, NV>(P, uL, uR, 1, yf[r][c][k]);
+      const bool sb = P.sol_j > 0 && is_solid(P, ii, jb), st = P.sol_j > 0 && is_solid(P, ii, jb + 1);
+      if (P.sol_j > 0 && (sb || jb < 0) && (st || jb + 1 >= P.ny)) continue;
+      if (!sb) gl_state<T, NV>(P, G, image(P, ii, jb), k, 3, uL);
+      if (!st) gl_state<T, NV>(P, G, image(P, ii, jb + 1), k, 0, uR);
+      if (st && !sb) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) uR[v] = v == 2 ? -uL[v] : uL[v];
+      }
+      if (sb && !st) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) uL[v] = v == 2 ? -uR[v] : uR[v];
+      }
+      if constexpr (NV == 4) {
+        if (sb || st) hllc<T, NV, true>(P, uL, uR, 1, yf[r][c][k]);
+        else num_flux<T, NV>(P, uL, uR, 1, yf[r][c][k]);
+      } else {
+        num_flux<T, NV>(P, uL, uR, 1, yf[r][c][k]);
+      }
     }
   }
   __syncthreads();
   if (!live) return;
+  if (P.sol_j > 0 && is_solid(P, i, j)) {   // solid cells are not updated: the state passes through
+    if (!S.Lout) {
+#pragma unroll 1
+      for (int q = 0; q < NV * 3; ++q) {
+        const long long si = (long long)q * P.plane + (long long)j * P.pitch + i;
+        S.Uout[si] = S.Uin[si];
+      }
+    } else {
+#pragma unroll 1
+      for (int q = 0; q < NV * 3; ++q) {
+        const long long si = (long long)q * P.plane + (long long)j * P.pitch + i;
+        S.Lout[si] = 0.0;
+        if (S.Umod) S.Umod[si] = S.Uin[si];
+      }
+    }
+    return;
+  }
   // face integrals (eq. (integral2), (integral3)) and the cell quadrature (eq. (integral1))
   T Fp[NV], Fm[NV], Fpe[NV], Fme[NV], Gp[NV], Gm[NV], Gpx[NV], Gmx[NV], Fc[NV], Gc[NV];
 #pragma unroll
@@ -479,7 +542,7 @@ void launch_rec2d(int blocks, cudaStream_t st, const Prob& P, const Weights<T>& 
                   const double* U, const uint8_t* mask, const double* Mod, const int* list, const int* count, T* G,
                   T* aux, unsigned long long* rerec) {
   if constexpr (NV == 4 && std::is_same<T, double>::value) {
-    if (P.fixtab) {
+    if (P.fixtab || P.sol_j > 0) {
       rec2d_kernel<T, NV, MODE, true><<<blocks, RB, 0, st>>>(P, W, Bt, U, mask, Mod, list, count, G, aux, rerec);
       return;
     }

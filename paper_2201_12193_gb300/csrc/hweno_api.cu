@@ -838,12 +838,29 @@ hweno_status hweno_set_positivity_check(hweno_t h, int on) {
 hweno_status hweno_set_fused(hweno_t h, int on) {
   if (!h) return HWENO_EINVAL;
   if (on != 0 && on != 1) return fail(h, HWENO_EINVAL, "set_fused: on must be 0 or 1");
-  if (on && (h->batch || h->g.dim != 2 || h->g.eq != HWENO_EULER ||
+  if (on && (h->batch || h->g.dim != 2 || h->g.eq != HWENO_EULER || h->P.sol_j > 0 ||
              (h->g.indicator != HWENO_IND_NONE && h->g.indicator != HWENO_IND_KXRCF &&
               h->g.indicator != HWENO_IND_ALL)))
     return fail(h, HWENO_ESTATE, "set_fused: the fused stage is for single 2D Euler handles with the KXRCF, "
                                  "none or all indicator");
   h->P.fused = on;
+  drop_graphs(h);
+  return HWENO_OK;
+}
+
+hweno_status hweno_set_solid(hweno_t h, int i0, int j1) {
+  if (!h) return HWENO_EINVAL;
+  if (h->batch || h->g.dim != 2 || h->g.eq != HWENO_EULER || h->g.precision != 0 || h->g.indicator == 3)
+    return fail(h, HWENO_ESTATE, "set_solid: single 2D Euler FP64 handles without the learned indicator");
+  if (j1 == 0) { h->P.sol_i = 0; h->P.sol_j = 0; drop_graphs(h); return HWENO_OK; }
+  const int nx = h->P.nx, ny = h->P.ny;
+  if (i0 < 0 || i0 >= nx || j1 < 1 || j1 > ny || (i0 > 0 && i0 < 4) || (j1 < ny && ny - j1 < 4))
+    return fail(h, HWENO_EINVAL, "set_solid: need 0 <= i0 < nx, 1 <= j1 <= ny and 4 fluid cells beyond each face");
+  if ((i0 > 0 && h->P.bc[1] == HWENO_BC_PERIODIC) || (j1 < ny && h->P.bc[2] == HWENO_BC_PERIODIC))
+    return fail(h, HWENO_EINVAL, "set_solid: the sides the block touches may not be periodic");
+  if (h->P.fused) return fail(h, HWENO_ESTATE, "set_solid: the fused stage has no solid block (hweno_set_fused 0)");
+  h->P.sol_i = i0;
+  h->P.sol_j = j1;
   drop_graphs(h);
   return HWENO_OK;
 }

@@ -66,6 +66,8 @@ struct Prob {
                           //    L only and the combination takes the stage states as they entered
   int fused;              // 2D Euler: one fused kernel per stage where it applies (else the pipeline)
   PConst cgamma, cdx, cdy, crdx, crdy, cdx2;   // gamma, dx, dy, 1/dx, 1/dy, dx^2
+  int sol_i, sol_j;       // solid block (2D Euler, the forward step): cells i >= sol_i, j < sol_j;
+                          //    sol_j = 0: none
   int jlo, jhi;           // owned rows [jlo, jhi): the rows a row-slab of a decomposed grid owns (the
                           //    others are halo rows refilled from the neighbours before each stage);
                           //    only they enter the status checks, the CFL reduction and the totals
@@ -124,6 +126,29 @@ struct Img { int i, j, sx, sy, neg, fs; };
 
 __device__ __forceinline__ int wrap(int i, int n) { i %= n; return i < 0 ? i + n : i; }
 
+// Solid block of the forward-facing step (Example 3.10): in-domain cells with
+// i >= sol_i and j < sol_j.
+__device__ __forceinline__ bool is_solid(const Prob& P, int i, int j) {
+  return P.sol_j > 0 && i >= P.sol_i && i < P.nx && j >= 0 && j < P.sol_j;
+}
+
+// The block's faces are reflective walls: a solid cell in the stencil of the
+// fluid cell (vi, vj) is that cell's wall image, mirrored across the vertical
+// face when the viewer lies left of it (vi < sol_i), across the horizontal
+// face when the viewer lies above it (vj >= sol_j), across both (a point
+// reflection through the corner) for the one viewer diagonal to the corner;
+// each crossed face negates its wall-normal momentum and its normal first
+// moment.  The image depends on the viewer (the corner cell seen from its left
+// neighbour is that neighbour's x mirror, from above the y mirror of the cell
+// above it).
+__device__ __forceinline__ void solid_image(const Prob& P, int vi, int vj, Img& r) {
+  if (r.fs >= 0 || !is_solid(P, r.i, r.j)) return;
+  if (vi < P.sol_i) { r.i = 2 * P.sol_i - 1 - r.i; r.sx = -r.sx; r.neg ^= 2; }
+  if (vj >= P.sol_j) { r.j = 2 * P.sol_j - 1 - r.j; r.sy = -r.sy; r.neg ^= 4; }
+}
+
+// The image of cell (i, j) by the boundary sides alone (a cell of the solid
+// block maps to itself; callers that can meet one use the viewer form below).
 __device__ __forceinline__ Img image(const Prob& P, int i, int j) {
   Img r{i, j, 1, 1, 0, -1};
   if (j < 0 || j >= P.ny) {
@@ -146,6 +171,14 @@ __device__ __forceinline__ Img image(const Prob& P, int i, int j) {
     if (k == BC_PERIODIC) r.i = wrap(i, P.nx);
     else { r.i = i < 0 ? -1 - i : 2 * P.nx - 1 - i; r.sx = -1; if (k == BC_REFLECTIVE) r.neg |= 2; }
   }
+  return r;
+}
+
+// The image of cell (i, j) as the stencil of the fluid cell (vi, vj) sees it:
+// boundary sides first, then the solid block.
+__device__ __forceinline__ Img image(const Prob& P, int i, int j, int vi, int vj) {
+  Img r = image(P, i, j);
+  if (P.sol_j > 0) solid_image(P, vi, vj, r);
   return r;
 }
 
@@ -276,7 +309,13 @@ __device__ __forceinline__ T scalar_velocity(const Prob& P, T u, int dir) {
 // HLLC flux, eqs. (f_HLLC), (COEF), (uLR_), as a rotated 1D solver in direction
 // dir (the tangential velocity is carried through the star state).
 // Branch order: 0 <= sL -> fL; 0 <= s* -> f*L; 0 <= sR -> f*R; else fR.
-template <typename T, int NV>
+// WALL: the face of the forward step's solid block (one side the reflection of
+// the other): the star branch is taken whatever the sign of the wave-speed
+// estimate, so the flux carries no mass or energy (s* = 0) and the normal
+// momentum flux is the star pressure -- the estimate of eq. (COEF) gives
+// s_L > 0 for flow running into a wall faster than about its sound speed,
+// where the first branch of eq. (f_HLLC) would let the gas through the wall.
+template <typename T, int NV, bool WALL = false>
 __device__ __forceinline__ void hllc(const Prob& P, const T* uL, const T* uR, int dir, T* F) {
   constexpr bool two = NV == 4;
   const T g = pc<T>(P.cgamma);
@@ -306,7 +345,7 @@ __device__ __forceinline__ void hllc(const Prob& P, const T* uL, const T* uR, in
   const T coefL = ps <= pL ? T(1) : sqrt(T(1) + k * (ps / pL - T(1)));
   const T coefR = ps <= pR ? T(1) : sqrt(T(1) + k * (ps / pR - T(1)));
   const T sL = mL - cL * coefL, sR = mR + cR * coefR;
-  const bool useL = T(0) <= sL || T(0) <= ss;     // left physical or left star flux
+  const bool useL = (!WALL && T(0) <= sL) || T(0) <= ss;     // left physical or left star flux
   const T rK = useL ? rL : rR, mK = useL ? mL : mR, tK = useL ? tL : tR;
   const T EK = useL ? EL : ER, pK = useL ? pL : pR, sK = useL ? sL : sR;
   // physical normal flux of the chosen side
@@ -317,7 +356,7 @@ __device__ __forceinline__ void hllc(const Prob& P, const T* uL, const T* uR, in
   fK[1] = dir == 0 ? rK * mK * mK + pK : rK * mK * tK;
   if constexpr (two) fK[2] = dir == 0 ? rK * mK * tK : rK * mK * mK + pK;
   fK[iE] = mK * (EK + pK);
-  if (T(0) <= sL || !(T(0) <= sR || T(0) <= ss)) {   // supersonic: fL or fR
+  if (!WALL && (T(0) <= sL || !(T(0) <= sR || T(0) <= ss))) {   // supersonic: fL or fR
 #pragma unroll
     for (int v = 0; v < NV; ++v) F[v] = fK[v];
     return;
@@ -517,7 +556,8 @@ template <typename T>
 __device__ __forceinline__ T kxrcf2d(const Prob& P, const Weights<T>& W, const T* __restrict__ G,
                                      const T* __restrict__ aux, int i, int j) {
   const long long o = goff(P, i, j);
-  const Img L = image(P, i - 1, j), R = image(P, i + 1, j), Bo = image(P, i, j - 1), Tp = image(P, i, j + 1);
+  const Img L = image(P, i - 1, j, i, j), R = image(P, i + 1, j, i, j), Bo = image(P, i, j - 1, i, j),
+            Tp = image(P, i, j + 1, i, j);
   const long long oL = goff(P, L.i, L.j), oR = goff(P, R.i, R.j), oB = goff(P, Bo.i, Bo.j), oT = goff(P, Tp.i, Tp.j);
   // the neighbours' face velocities (the x ones negated through an x wall, the y
   // ones through a y wall); a fixed-state ghost's is its own state's velocity
@@ -535,22 +575,25 @@ __device__ __forceinline__ T kxrcf2d(const Prob& P, const Weights<T>& W, const T
   };
   const T dx = pc<T>(P.cdx), dy = pc<T>(P.cdy);
   T s = T(0), len = T(0);
-  if (vxl > T(KX_VDEAD)) {
+  // a face shared with a solid cell (the forward step's block) is a wall, never an inflow face
+  const bool wl = P.sol_j > 0 && is_solid(P, i - 1, j), wr = P.sol_j > 0 && is_solid(P, i + 1, j);
+  const bool wb = P.sol_j > 0 && is_solid(P, i, j - 1), wt = P.sol_j > 0 && is_solid(P, i, j + 1);
+  if (vxl > T(KX_VDEAD) && !wl) {
 #pragma unroll
     for (int l = 0; l < 4; ++l) s += dy * gl_w<T>(l) * (G[(long long)(l)*P.gplane + o] - rho_at(L, oL, 3, l));
     len += dy;
   }
-  if (-vxr > T(KX_VDEAD)) {
+  if (-vxr > T(KX_VDEAD) && !wr) {
 #pragma unroll
     for (int l = 0; l < 4; ++l) s += dy * gl_w<T>(l) * (G[(long long)(12 + l) * P.gplane + o] - rho_at(R, oR, 0, l));
     len += dy;
   }
-  if (vyb > T(KX_VDEAD)) {
+  if (vyb > T(KX_VDEAD) && !wb) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) s += dx * gl_w<T>(k) * (G[(long long)(k * 4) * P.gplane + o] - rho_at(Bo, oB, k, 3));
     len += dx;
   }
-  if (-vyt > T(KX_VDEAD)) {
+  if (-vyt > T(KX_VDEAD) && !wt) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) s += dx * gl_w<T>(k) * (G[(long long)(k * 4 + 3) * P.gplane + o] - rho_at(Tp, oT, k, 0));
     len += dx;
@@ -579,11 +622,11 @@ __device__ __forceinline__ bool tvb_changes(double a, double b, double c, double
 __device__ __forceinline__ bool tvb_cell(const Prob& P, const double* __restrict__ U, int i, int j) {
   const double bound = P.tvb_m * P.dx * P.dx;
   const double u0 = U[sidx(P, 0, 0, i, j)];
-  const Img L = image(P, i - 1, j), R = image(P, i + 1, j);
+  const Img L = image(P, i - 1, j, i, j), R = image(P, i + 1, j, i, j);
   const double ax = 6.0 * U[sidx(P, 0, 1, i, j)];
   if (tvb_changes(ax, avg_img(P, U, R, 0) - u0, u0 - avg_img(P, U, L, 0), bound)) return true;
   if (P.nmom == 2) return false;
-  const Img Bo = image(P, i, j - 1), Tp = image(P, i, j + 1);
+  const Img Bo = image(P, i, j - 1, i, j), Tp = image(P, i, j + 1, i, j);
   const double ay = 6.0 * U[sidx(P, 0, 2, i, j)];
   return tvb_changes(ay, avg_img(P, U, Tp, 0) - u0, u0 - avg_img(P, U, Bo, 0), bound);
 }

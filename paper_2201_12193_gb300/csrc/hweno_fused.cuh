@@ -518,7 +518,7 @@ constexpr size_t fused_smem_bytes() { return sizeof(FusedSmem<T>); }
 // The fused stage applies to 2D Euler with KXRCF, every cell or no cell
 // troubled, and periodic / transmissive / reflective sides.
 inline bool fused_applies(const Prob& P, int nv) {
-  return P.fused && nv == 4 && !P.fixtab &&
+  return P.fused && nv == 4 && !P.fixtab && P.sol_j == 0 &&
          (P.indicator == IND_NONE || P.indicator == IND_KXRCF || P.indicator == IND_ALL);
 }
 

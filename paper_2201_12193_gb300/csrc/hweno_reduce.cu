@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(RT) wavespeed_kernel(Prob P, const double* __r
   const long long n = (long long)P.nx * (P.jhi - P.jlo);   // owned rows
   for (long long t = (long long)blockIdx.x * RT + threadIdx.x; t < n; t += (long long)gridDim.x * RT) {
     const int i = (int)(t % P.nx), j = P.jlo + (int)(t / P.nx);
+    if (P.sol_j > 0 && is_solid(P, i, j)) continue;    // the step's block takes no part
     double sx, sy;
     if (P.eq == EQ_ADV) { sx = fabs(P.adv_a); sy = fabs(P.adv_b); }
     else if (P.eq == EQ_BURGERS) { sx = sy = fabs(U[sidx(P, 0, 0, i, j)]); }
@@ -74,6 +75,7 @@ __global__ void __launch_bounds__(RT) totals_kernel(Prob P, const double* __rest
   const long long n = (long long)P.nx * (P.jhi - P.jlo);   // owned rows
   for (long long t = (long long)blockIdx.x * RT + threadIdx.x; t < n; t += (long long)gridDim.x * RT) {
     const int i = (int)(t % P.nx), j = P.jlo + (int)(t / P.nx);
+    if (P.sol_j > 0 && is_solid(P, i, j)) continue;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
       if (k < P.nvar) v[k] += U[sidx(P, k, 0, i, j)];

@@ -99,6 +99,7 @@ def lib():
         L.hweno_set_positivity_check.argtypes = [H, ctypes.c_int]
         L.hweno_set_persistence.argtypes = [H, ctypes.c_int]
         L.hweno_set_fused.argtypes = [H, ctypes.c_int]
+        L.hweno_set_solid.argtypes = [H, ctypes.c_int, ctypes.c_int]
         L.hweno_set_owned_rows.argtypes = [H, ctypes.c_int, ctypes.c_int]
         L.hweno_stage.argtypes = [H, ctypes.c_int, ctypes.c_double]
         L.hweno_copy_rows.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_int]
@@ -179,6 +180,8 @@ class Solver:
         for side, f in enumerate(p.fixed or ()):
             if f:
                 s.set_fixed_state(side, **f)
+        if p.meta.get("solid"):
+            s.set_solid(*p.meta["solid"])
         return s
 
     def set_fixed_state(self, side, a=None, b=None, c0=None, speed=0.0):
@@ -293,6 +296,10 @@ class Solver:
     def set_positivity_check(self, on=True):
         """Off: only non-finite values fail a step (rho <= 0 / p <= 0 averages carry on)."""
         self._check(lib().hweno_set_positivity_check(self._h, int(bool(on))))
+
+    def set_solid(self, i0, j1):
+        """Solid block: cells with i >= i0 and j < j1 (the forward step); j1 = 0 removes it."""
+        self._check(lib().hweno_set_solid(self._h, int(i0), int(j1)))
 
     def set_owned_rows(self, jlo, jhi):
         """Rows [jlo, jhi) this handle owns (row-slab decomposition)."""

@@ -317,6 +317,26 @@ def double_mach_2d(ny=400):
                    ("inflow", "transmissive", "reflective", "inflow"), m, t_end=0.2, fixed=fixed)
 
 
+def forward_step_2d(ny=200):
+    """Example 3.10, Mach 3 flow over a forward-facing step: [0,3] x [0,1]
+    (3 ny x ny square cells), a step of height 0.2 from x = 0.6 on (solid cells
+    i >= 0.6 ny, j < 0.2 ny).  Initial and inflow state (rho, u, v, p) =
+    (1.4, 3, 0, 1); inflow on the left, outflow (transmissive) on the right,
+    reflective walls at the top, the bottom and the step's faces.  To t = 4.
+    ny must be a multiple of 5 (the step's corner on a cell corner)."""
+    if ny % 5:
+        raise ValueError("ny must be a multiple of 5")
+    nx = 3 * ny
+    state = prim_to_cons_2d(1.4, 3.0, 0.0, 1.0)
+    m = np.zeros((4, 3, ny, nx))
+    for v in range(4):
+        m[v, 0] = state[v]
+    fixed = ({"b": tuple(float(x) for x in state)}, None, None, None)
+    return Problem("forward_step_2d", 2, nx, ny, 0.0, 3.0, 0.0, 1.0, "euler",
+                   ("inflow", "transmissive", "reflective", "reflective"), m, t_end=4.0, fixed=fixed,
+                   meta={"solid": (3 * ny // 5, ny // 5)})
+
+
 def batch_sizes(seed=0, count=256, choices=(64, 128, 256, 512)):
     """Grid sizes of a batch of independent problems, uniform in choices."""
     rng = np.random.default_rng(seed)

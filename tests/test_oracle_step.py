@@ -111,11 +111,12 @@ def test_step_at_rest_stays_at_rest_and_solid_cells_are_left_out(orc):
 
 def test_faces_on_the_block_are_never_inflow_faces(orc):
     """Gas at rest (rho = 1, p = 1) except the cell just above the corner's left
-    neighbour, which is denser (rho = 2) and moves right.  The corner solid
-    cell's diagonal image is that cell with both momenta negated, so across the
-    step's vertical face the left neighbour would see a flow into it and a
-    density jump of 1 (aleph in the hundreds); a face shared with a solid cell
-    is a wall, never an inflow face, so the cell stays untroubled."""
+    neighbour, which is denser (rho = 2) and moves right.  Seen from that cell
+    (diagonal to the corner) the corner solid cell is its point reflection,
+    moving left; seen from the corner's left neighbour it is that neighbour's
+    own mirror, at rest: across the step's vertical face the left neighbour
+    sees neither a flow into it nor a density jump (a face shared with a solid
+    cell is a wall, never an inflow face), so it stays untroubled."""
     nx, ny, h, sol = 16, 12, 0.1, (9, 4)
     rho = np.ones((ny, nx))
     u = np.zeros((ny, nx))
@@ -129,3 +130,27 @@ def test_faces_on_the_block_are_never_inflow_faces(orc):
     assert rc == 0
     a = a.reshape(ny, nx)
     assert a[sol[1] - 1, sol[0] - 1] < 1e-3 and not k.reshape(ny, nx)[sol[1] - 1, sol[0] - 1]
+
+
+def test_supersonic_flow_does_not_cross_the_step_face(orc):
+    """Mach 3 flow straight into the step's vertical face: the face carries no
+    mass and no energy (the cell in front of it keeps only its inflow: L of its
+    mass = rho u / dx, of its energy = (E + p) u / dx), although the wave-speed
+    estimate of eq. (COEF) would put the whole HLLC fan downstream of the face
+    (s_L = 3 - 2.14 > 0) and the first branch of eq. (f_HLLC) would let the
+    gas through.  Above the step every cell beyond the corner's column sees
+    the block as its own mirror in y, a uniform stencil: its L of the averages
+    is exactly zero (an image across the corner's diagonal would break the
+    uniformity in the cells next to it)."""
+    p = W.forward_step_2d(20)
+    i0, j1 = p.meta["solid"]
+    cfg = orc.make_cfg(2, p.nx, p.ny, dx=p.dx, dy=p.dy, bc=p.bc, fixed=p.fixed, solid=(i0, j1), indicator="none")
+    _, L, _, _, rc = orc.rhs(cfg, p.m)
+    assert rc == 0
+    rho, u, pr = 1.4, 3.0, 1.0
+    E = pr / 0.4 + 0.5 * rho * u * u
+    for j in range(j1 - 1):          # below the corner row (its top face is a wall too)
+        assert L[0, 0, j, i0 - 1] == pytest.approx(rho * u / p.dx, rel=1e-12)
+        assert L[3, 0, j, i0 - 1] == pytest.approx((E + pr) * u / p.dx, rel=1e-12)
+    assert np.abs(L[0, 0, j1:, :]).max() < 1e-8     # the uniform flow above the step is steady
+    assert not L[:, 0, j1:, i0 + 1:].any()
