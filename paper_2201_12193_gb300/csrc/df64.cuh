@@ -146,6 +146,25 @@ __device__ __forceinline__ float f32_rn(double x) {
   return __uint_as_float(f);
 }
 
+// A float widened to double with integer operations only (exact: every float is
+// a double): the sign kept, the exponent rebiased (127 -> 1023), the 23 fraction
+// bits placed at the top of the 52; zeros keep their sign; subnormal and
+// non-finite floats take the FP64 conversion.
+__device__ __forceinline__ double f64_of_f32(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned e = (b >> 23) & 0xFFu;
+  if (e == 0u || e == 0xFFu) {
+    if ((b & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    return (double)x;
+  }
+  const unsigned h = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)h, (int)((b & 0x7u) << 29));
+}
+
+// A compute-type value as a double (float by the integer widening above).
+template <typename T> __device__ __forceinline__ double to_f64(T x) { return (double)x; }
+template <> __device__ __forceinline__ double to_f64<float>(float x) { return f64_of_f32(x); }
+
 // A run-time double in the compute type (df64 by the integer split; float by
 // the FP64 conversion, which measured faster than f32_rn in the gathers of the
 // multi-launch reconstruction, where the FP64 pipe is not the bound).

@@ -111,25 +111,65 @@ __device__ __forceinline__ double load_mom(const Prob& P, const double* __restri
   }
 }
 
-template <typename T, int NV, int MODE, bool FIX = false>
+// FP32 form: the moment from the float copy of the state the update kernel
+// writes beside it (the state rounded to nearest), signs flipped by integer
+// work; modified first moments of flagged cells still come from the FP64 copy.
+template <int MODE>
+__device__ __forceinline__ float load_mom32(const Prob& P, const float* __restrict__ U32,
+                                            const uint8_t* __restrict__ mask, const double* __restrict__ Mod,
+                                            const Nbr& n, int var, int kind, int ox, int oy, bool usemod) {
+  const int ci = n.xi[ox + 1], cj = n.yj[oy + 1];
+  const long long so = (long long)cj * P.pitch + ci;
+  unsigned flip = (n.neg[oy + 1][ox + 1] >> var) & 1u;
+  float v;
+  if (kind == 0) {
+    v = U32[(long long)(var * 3) * P.plane + so];
+  } else {
+    if (MODE != REC_PLAIN && usemod && mask[(long long)cj * P.nx + ci] == 1)
+      v = float(Mod[(long long)(var * 2 + kind - 1) * P.plane + so]);
+    else
+      v = U32[(long long)(var * 3 + kind) * P.plane + so];
+    if (kind == 1 && n.xs[ox + 1] < 0) flip ^= 1u;
+    if (kind == 2 && n.ys[oy + 1] < 0) flip ^= 1u;
+  }
+  return __uint_as_float(__float_as_uint(v) ^ (flip << 31));
+}
+
+template <typename T, int NV, int MODE, bool FIX = false, bool S32 = false>
 __device__ __forceinline__ void rec2d_cell(const Prob& P, const Weights<T>& W, const Beta2<T>& B,
                                            const double* __restrict__ U, const uint8_t* __restrict__ mask,
                                            const double* __restrict__ Mod, int i, int j, T* __restrict__ G,
-                                           T* __restrict__ aux) {
+                                           T* __restrict__ aux, const float* __restrict__ U32 = nullptr) {
   constexpr bool FLAGGED = MODE == REC_FLAGGED;
   const bool usemod = MODE == REC_FLAGGED || (MODE == REC_MIXED && mask[(long long)j * P.nx + i] == 1);
   const Nbr nb = neighbours<FIX>(P, i, j);
   const long long o = goff(P, i, j);
+  // float copy, plain pass, all 3 x 3 cells inside the grid: no image to apply,
+  // the moments are read at fixed offsets from the cell's own
+  const bool inner = S32 && MODE == REC_PLAIN && i > 0 && i < P.nx - 1 && j > 0 && j < P.ny - 1;
+  const float* __restrict__ Uc = S32 ? U32 + ((long long)j * P.pitch + i) : nullptr;
   T rinv[16];
   T pxl = T(0), pxr = T(0), pyb = T(0), pyt = T(0), nrm = T(0);
 #pragma unroll 1
   for (int v = 0; v < NV; ++v) {
     T d[23];
+    if (inner) {
 #pragma unroll
-    for (int c = 0; c < 23; ++c) {
-      int kind, ox, oy;
-      d4_slot(c, kind, ox, oy);
-      d[c] = from_double<T>(load_mom<MODE, !is_df64<T>::value, FIX>(P, U, mask, Mod, nb, v, kind, ox, oy, usemod));
+      for (int c = 0; c < 23; ++c) {
+        int kind, ox, oy;
+        d4_slot(c, kind, ox, oy);
+        d[c] = T(Uc[(long long)(v * 3 + kind) * P.plane + (long long)oy * P.pitch + ox]);
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 23; ++c) {
+        int kind, ox, oy;
+        d4_slot(c, kind, ox, oy);
+        if constexpr (S32)
+          d[c] = load_mom32<MODE>(P, U32, mask, Mod, nb, v, kind, ox, oy, usemod);
+        else
+          d[c] = from_double<T>(load_mom<MODE, !is_df64<T>::value, FIX>(P, U, mask, Mod, nb, v, kind, ox, oy, usemod));
+      }
     }
     T out[16];
     recon2d<T>(W, B, d, out);
@@ -193,12 +233,13 @@ __device__ __forceinline__ void rec2d_cell(const Prob& P, const Weights<T>& W, c
 // reconstructed a second time.
 // Double-float: 4 resident blocks per SM (at most 128 registers, a few spills)
 // beat 3 (168 registers, none): 7.0 vs 8.3 ms per launch at 2048^2.
-template <typename T, int NV, int MODE, bool FIX = false>
-__global__ void __launch_bounds__(RB, (is_df64<T>::value ? 4 : 1)) rec2d_kernel(Prob P, Weights<T> W, Beta2<T> B, const double* __restrict__ U,
+template <typename T, int NV, int MODE, bool FIX = false, bool S32 = false>
+__global__ void __launch_bounds__(RB, (is_df64<T>::value || std::is_same<T, float>::value ? 4 : 1)) rec2d_kernel(Prob P, Weights<T> W, Beta2<T> B, const double* __restrict__ U,
                                                   const uint8_t* __restrict__ mask, const double* __restrict__ Mod,
                                                   const int* __restrict__ list, const int* __restrict__ count,
                                                   T* __restrict__ G, T* __restrict__ aux,
-                                                  unsigned long long* __restrict__ rerec) {
+                                                  unsigned long long* __restrict__ rerec,
+                                                  const float* __restrict__ U32 = nullptr) {
   constexpr bool FLAGGED = MODE == REC_FLAGGED;
   const long long ncell = (long long)P.nx * P.ny;
   const long long n = FLAGGED ? (long long)*count : ncell;
@@ -206,7 +247,7 @@ __global__ void __launch_bounds__(RB, (is_df64<T>::value ? 4 : 1)) rec2d_kernel(
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int cell = FLAGGED ? list[t] : (int)t;
     if (FIX && is_solid(P, cell % P.nx, cell / P.nx)) continue;   // solid cells are images, never read
-    rec2d_cell<T, NV, MODE, FIX>(P, W, B, U, mask, Mod, cell % P.nx, cell / P.nx, G, aux);
+    rec2d_cell<T, NV, MODE, FIX, S32>(P, W, B, U, mask, Mod, cell % P.nx, cell / P.nx, G, aux, U32);
   }
 }
 
@@ -324,6 +365,29 @@ __device__ __forceinline__ void gl_state(const Prob& P, const T* __restrict__ G,
   }
 }
 
+// The numerical flux of one face point, one inlined solver for both
+// directions: a y face is an x face with the two momentum components
+// exchanged (the HLLC expressions are the same, term for term); at a wall
+// face the star branch is taken.
+template <typename T, int NV>
+__device__ __forceinline__ void face_flux(const Prob& P, T (&uL)[NV], T (&uR)[NV], bool xd, bool wall, T* out) {
+  if constexpr (NV == 4) {
+    if (!xd) {
+      const T a = uL[1], b = uR[1];
+      uL[1] = uL[2]; uL[2] = a;
+      uR[1] = uR[2]; uR[2] = b;
+    }
+    T F[4];
+    hllc<T, 4>(P, uL, uR, 0, F, wall);
+    out[0] = F[0];
+    out[1] = xd ? F[1] : F[2];
+    out[2] = xd ? F[2] : F[1];
+    out[3] = F[3];
+  } else {
+    num_flux<T, NV>(P, uL, uR, xd ? 0 : 1, out);
+  }
+}
+
 struct Rk {
   const double* Uin; const double* Un; double* Uout;
   const uint8_t* mask; const double* Mod; const uint8_t* maskN; const double* ModN;
@@ -331,6 +395,7 @@ struct Rk {
   double* Lout; double* Umod;
   unsigned* status;
   const double* dtp;     // dt on the device (overrides dt); < 0: skip, Uout = Uin
+  float* U32out = nullptr;   // FP32 form: the float copy of Uout (the next stage's reconstruction input)
 };
 
 // Step 3 for the TXV x TYV tile at (i0, j0): face fluxes into shared memory, then
@@ -347,57 +412,50 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
   // from both (the flux differences then telescope exactly in FP64).
   // xf[r][c] is the face left of cell (i0 + c, j0 + r); yf[r][c] the face below it.
   constexpr int NXP = (TXV + 1) * TYV * 4, NYP = TXV * (TYV + 1) * 4;
+  // a tile whose faces all join cells inside the grid (no image, no solid cell):
+  // the point values at fixed offsets
+  const bool tin = P.sol_j == 0 && i0 >= 1 && i0 + TXV < P.nx && j0 >= 1 && j0 + TYV < P.ny;
   __syncthreads();   // the shared arrays may still be read for a previous tile
   for (int f = tid; f < NXP + NYP; f += TXV * TYV) {
+    // the face's GL point q, its slot (c, r) in the tile, its two cells a
+    // (left / below) and b (right / above) and their point indices
+    const bool xd = f < NXP;
+    const int g = xd ? f : f - NXP, q = g & 3, face = g >> 2;
+    const int c = xd ? face % (TXV + 1) : face % TXV, r = xd ? face / (TXV + 1) : face / TXV;
+    const int aI = xd ? i0 + c - 1 : i0 + c, aJ = xd ? j0 + r : j0 + r - 1;
+    const int bI = xd ? aI + 1 : aI, bJ = xd ? aJ : aJ + 1;
+    const int ka = xd ? 3 : q, la = xd ? q : 3, kb = xd ? 0 : q, lb = xd ? q : 0;
     T uL[NV], uR[NV];
-    if (f < NXP) {
-      const int l = f & 3, face = f >> 2, c = face % (TXV + 1), r = face / (TXV + 1);
-      const int il = i0 + c - 1, jj = j0 + r;
-      if (jj >= P.ny || il >= P.nx) continue;
-      const bool sl = P.sol_j > 0 && is_solid(P, il, jj), sr = P.sol_j > 0 && is_solid(P, il + 1, jj);
-      // a face no fluid cell uses (solid on one side, solid or outside on the
-      // other) is skipped: only solid cells would read it, and they are not updated
-      if (P.sol_j > 0 && (sl || il < 0) && (sr || il + 1 >= P.nx)) continue;
-      // a face shared with a solid cell: the outer state is the reflection of the fluid side's own
-      if (!sl) gl_state<T, NV>(P, G, image(P, il, jj), 3, l, uL);
-      if (!sr) gl_state<T, NV>(P, G, image(P, il + 1, jj), 0, l, uR);
-      if (sr && !sl) {
+    bool wall = false;
+    if (tin) {
+      const long long oa = goff(P, aI, aJ), ob = goff(P, bI, bJ);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) uR[v] = v == 1 ? -uL[v] : uL[v];
-      }
-      if (sl && !sr) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) uL[v] = v == 1 ? -uR[v] : uR[v];
-      }
-      if constexpr (NV == 4) {
-        if (sl || sr) hllc<T, NV, true>(P, uL, uR, 0, xf[r][c][l]);
-        else num_flux<T, NV>(P, uL, uR, 0, xf[r][c][l]);
-      } else {
-        num_flux<T, NV>(P, uL, uR, 0, xf[r][c][l]);
+      for (int v = 0; v < NV; ++v) {
+        uL[v] = G[(long long)(v * 16 + ka * 4 + la) * P.gplane + oa];
+        uR[v] = G[(long long)(v * 16 + kb * 4 + lb) * P.gplane + ob];
       }
     } else {
-      const int g = f - NXP, k = g & 3, face = g >> 2, c = face % TXV, r = face / TXV;
-      const int ii = i0 + c, jb = j0 + r - 1;
-      if (ii >= P.nx || jb >= P.ny) continue;
-      const bool sb = P.sol_j > 0 && is_solid(P, ii, jb), st = P.sol_j > 0 && is_solid(P, ii, jb + 1);
-      if (P.sol_j > 0 && (sb || jb < 0) && (st || jb + 1 >= P.ny)) continue;
-      if (!sb) gl_state<T, NV>(P, G, image(P, ii, jb), k, 3, uL);
-      if (!st) gl_state<T, NV>(P, G, image(P, ii, jb + 1), k, 0, uR);
-      if (st && !sb) {
+      if (aJ >= P.ny || aI >= P.nx) continue;
+      const bool sa = P.sol_j > 0 && is_solid(P, aI, aJ), sb = P.sol_j > 0 && is_solid(P, bI, bJ);
+      // a face no fluid cell uses (solid on one side, solid or outside on the
+      // other) is skipped: only solid cells would read it, and they are not updated
+      if (P.sol_j > 0 && (sa || aI < 0 || aJ < 0) && (sb || bI >= P.nx || bJ >= P.ny)) continue;
+      if (!sa) gl_state<T, NV>(P, G, image(P, aI, aJ), ka, la, uL);
+      if (!sb) gl_state<T, NV>(P, G, image(P, bI, bJ), kb, lb, uR);
+      // a face shared with a solid cell: the outer state is the reflection of
+      // the fluid side's own (the wall-normal momentum negated)
+      const int wn = xd ? 1 : 2;
+      if (sb && !sa) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) uR[v] = v == 2 ? -uL[v] : uL[v];
+        for (int v = 0; v < NV; ++v) uR[v] = v == wn ? -uL[v] : uL[v];
       }
-      if (sb && !st) {
+      if (sa && !sb) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) uL[v] = v == 2 ? -uR[v] : uR[v];
+        for (int v = 0; v < NV; ++v) uL[v] = v == wn ? -uR[v] : uR[v];
       }
-      if constexpr (NV == 4) {
-        if (sb || st) hllc<T, NV, true>(P, uL, uR, 1, yf[r][c][k]);
-        else num_flux<T, NV>(P, uL, uR, 1, yf[r][c][k]);
-      } else {
-        num_flux<T, NV>(P, uL, uR, 1, yf[r][c][k]);
-      }
+      wall = sa || sb;
     }
+    face_flux<T, NV>(P, uL, uR, xd, wall, xd ? xf[r][c][q] : yf[r][c][q]);
   }
   __syncthreads();
   if (!live) return;
@@ -407,6 +465,7 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
       for (int q = 0; q < NV * 3; ++q) {
         const long long si = (long long)q * P.plane + (long long)j * P.pitch + i;
         S.Uout[si] = S.Uin[si];
+        if (S.U32out) S.U32out[si] = f32_rn(S.Uin[si]);
       }
     } else {
 #pragma unroll 1
@@ -471,6 +530,7 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
   }
   // eq. (2D-equ-int-approximation); the average equation in FP64 from the
   // face integrals so that the flux differences telescope in every precision
+  // (FP32 values widened by integer work: the FP64 pipe keeps only the sums)
   const double idx = P.crdx.d, idy = P.crdy.d;
   const T tidx = pc<T>(P.crdx), tidy = pc<T>(P.crdy);
   const long long so = (long long)j * P.pitch + i;
@@ -478,13 +538,17 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
   // modified first moments in the combination (persist), and always in the Umod output of Lout
   const bool fk = S.mask[cell] != 0 && (P.persist || S.Lout);
   const bool fn = P.persist && S.maskN && S.maskN[cell] != 0;
+  // the first stage has no U^n term (cA = 0, cB = 1): U^(1) = U' + dt L
+  const bool first = S.cA == 0.0;
+  const bool owned = j >= P.jlo && j < P.jhi;
   double newavg[NV];
+  bool finite = true;
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
     double L[3];
-    L[0] = -((double)Fp[v] - (double)Fm[v]) * idx - ((double)Gp[v] - (double)Gm[v]) * idy;
-    L[1] = (double)(-(Fp[v] + Fm[v]) * T(0.5) * tidx + Fc[v] * tidx - (Gpx[v] - Gmx[v]) * tidy);
-    L[2] = (double)(-(Fpe[v] - Fme[v]) * tidx - (Gp[v] + Gm[v]) * T(0.5) * tidy + Gc[v] * tidy);
+    L[0] = -(to_f64(Fp[v]) - to_f64(Fm[v])) * idx - (to_f64(Gp[v]) - to_f64(Gm[v])) * idy;
+    L[1] = to_f64(-(Fp[v] + Fm[v]) * T(0.5) * tidx + Fc[v] * tidx - (Gpx[v] - Gmx[v]) * tidy);
+    L[2] = to_f64(-(Fpe[v] - Fme[v]) * tidx - (Gp[v] + Gm[v]) * T(0.5) * tidy + Gc[v] * tidy);
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       const long long si = (long long)(v * 3 + m) * P.plane + so;
@@ -494,22 +558,31 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
         if (S.Umod) S.Umod[si] = uin;
         continue;
       }
-      const double un = (m > 0 && fn) ? S.ModN[(long long)(v * 2 + m - 1) * P.plane + so] : S.Un[si];
-      const double r = S.cA * un + S.cB * (uin + S.dt * L[m]);
+      double r;
+      if (first) {
+        r = fma(S.dt, L[m], uin);
+      } else {
+        const double un = (m > 0 && fn) ? S.ModN[(long long)(v * 2 + m - 1) * P.plane + so] : S.Un[si];
+        r = S.cA * un + S.cB * (uin + S.dt * L[m]);
+      }
       S.Uout[si] = r;
+      if (S.U32out) S.U32out[si] = f32_rn(r);
       if (m == 0) newavg[v] = r;
-      if (!isfinite(r) && j >= P.jlo && j < P.jhi) atomicOr(S.status, ST_NONFINITE);
+      // non-finite by the exponent field (integer work, no FP64 compare)
+      finite = finite && ((__double_as_longlong(r) >> 52) & 0x7FF) != 0x7FF;
     }
   }
-  if (!S.Lout && P.eq == EQ_EULER && NV == 4 && j >= P.jlo && j < P.jhi) {
+  if (!S.Lout && !finite && owned) atomicOr(S.status, ST_NONFINITE);
+  if (!S.Lout && P.eq == EQ_EULER && NV == 4 && owned) {
+    // rho > 0 and p = (gamma - 1)(E - |m|^2 / (2 rho)) > 0, the latter as 2 E rho > |m|^2 (no division)
     const double rho = newavg[0];
-    const double p = (P.gamma - 1.0) * (newavg[NV - 1] - 0.5 * (newavg[1] * newavg[1] + newavg[2] * newavg[2]) / rho);
-    if (!(rho > 0.0) || !(p > 0.0)) atomicOr(S.status, ST_NONPOSITIVE);
+    const double m2 = newavg[1] * newavg[1] + newavg[2] * newavg[2];
+    if (!(rho > 0.0) || !(2.0 * newavg[NV - 1] * rho > m2)) atomicOr(S.status, ST_NONPOSITIVE);
   }
 }
 
 template <typename T, int NV>
-__global__ void __launch_bounds__(TX * TY) update2d_kernel(Prob P, const T* __restrict__ G, Rk S) {
+__global__ void __launch_bounds__(TX * TY, (std::is_same<T, float>::value ? 8 : 3)) update2d_kernel(Prob P, const T* __restrict__ G, Rk S) {
   __shared__ T xf[TY][TX + 1][4][NV];
   __shared__ T yf[TY + 1][TX][4][NV];
   if (S.dtp) {
@@ -520,6 +593,7 @@ __global__ void __launch_bounds__(TX * TY) update2d_kernel(Prob P, const T* __re
         for (int q = 0; q < NV * 3; ++q) {
           const long long si = (long long)q * P.plane + (long long)j * P.pitch + i;
           S.Uout[si] = S.Uin[si];
+          if (S.U32out) S.U32out[si] = f32_rn(S.Uin[si]);
         }
       return;
     }
@@ -540,7 +614,14 @@ namespace {
 template <typename T, int NV, int MODE>
 void launch_rec2d(int blocks, cudaStream_t st, const Prob& P, const Weights<T>& W, const Beta2<T>& Bt,
                   const double* U, const uint8_t* mask, const double* Mod, const int* list, const int* count, T* G,
-                  T* aux, unsigned long long* rerec) {
+                  T* aux, unsigned long long* rerec, const float* U32 = nullptr) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (U32) {   // FP32 form with the float copy of the state: no per-moment conversion
+      rec2d_kernel<T, NV, MODE, false, true><<<blocks, RB, 0, st>>>(P, W, Bt, U, mask, Mod, list, count, G, aux,
+                                                                    rerec, U32);
+      return;
+    }
+  }
   if constexpr (NV == 4 && std::is_same<T, double>::value) {
     if (P.fixtab || P.sol_j > 0) {
       rec2d_kernel<T, NV, MODE, true><<<blocks, RB, 0, st>>>(P, W, Bt, U, mask, Mod, list, count, G, aux, rerec);
@@ -590,7 +671,7 @@ void stage_t(const Prob& P, const HostTabs& HT, const Weights<T>& W, const Beta2
   } else {
     if (B.prof) B.prof->begin(0, st);
     launch_rec2d<T, NV, REC_PLAIN>(rblocks, st, P, W, Bt, S.Uin, nullptr, nullptr, nullptr, nullptr, (T*)B.G,
-                                   (T*)B.aux, nullptr);
+                                   (T*)B.aux, nullptr, S.U32in);
     if (B.prof) B.prof->end(st);
     if (B.prof) B.prof->begin(1, st);
     flag2d_kernel<T, NV><<<grd, blk, 0, st>>>(P, W, S.Uin, (const T*)B.G, (const T*)B.aux, S.mask, S.Mod, B.list,
@@ -600,10 +681,11 @@ void stage_t(const Prob& P, const HostTabs& HT, const Weights<T>& W, const Beta2
   if (P.indicator != IND_NONE) {
     if (B.prof) B.prof->begin(2, st);
     launch_rec2d<T, NV, REC_FLAGGED>(fblocks, st, P, W, Bt, S.Uin, S.mask, S.Mod, B.list, cnt, (T*)B.G, nullptr,
-                                     B.rerec);
+                                     B.rerec, S.U32in);
     if (B.prof) B.prof->end(st);
   }
-  Rk r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status, S.dtp};
+  Rk r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status, S.dtp,
+       std::is_same<T, float>::value ? S.U32out : nullptr};
   if (B.prof) B.prof->begin(3, st);
   update2d_kernel<T, NV><<<grd, blk, 0, st>>>(P, (const T*)B.G, r);
   if (B.prof) B.prof->end(st);

@@ -23,6 +23,7 @@ struct hweno_s {
   hw::HostTabs T{};
   int fp32 = 0;                  // compute precision (hw::PREC_*)
   double* U[3] = {nullptr, nullptr, nullptr};
+  float* U32[3] = {nullptr, nullptr, nullptr};   // FP32 form (single 2D handles): float copies of U[k]
   int cur = 0, prev = 0;
   bool have_state = false, stepped = false;
   hw::Bufs B{};
@@ -232,6 +233,7 @@ void free_all(hweno_s* h) {
   cudaFree(h->bar);
   cudaFree(h->pstatus);
   for (int k = 0; k < 3; ++k) cudaFree(h->U[k]);
+  for (int k = 0; k < 3; ++k) cudaFree(h->U32[k]);
   cudaFree(h->B.G);
   cudaFree(h->B.aux);
   cudaFree(h->B.list);
@@ -345,6 +347,11 @@ hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gam
   const size_t nc = (size_t)P.nx * P.ny;
   bool ok = true;
   for (int k = 0; k < 3; ++k) ok = ok && cudaMalloc(&h->U[k], sbytes) == cudaSuccess;
+  // FP32 form in 2D: the reconstruction reads a float copy of its input state,
+  // which the update kernel writes beside each FP64 output (no per-moment
+  // FP64 -> FP32 conversion in the 3 x 3 gathers)
+  const bool shadow = h->fp32 == hw::PREC_FP32 && h->g.dim == 2;
+  for (int k = 0; k < 3 && shadow; ++k) ok = ok && cudaMalloc(&h->U32[k], sbytes / 2) == cudaSuccess;
   ok = ok && cudaMalloc(&h->B.G, (size_t)P.nvar * npt * P.gplane * esz) == cudaSuccess;
   ok = ok && cudaMalloc(&h->B.aux, 5 * (size_t)P.gplane * esz) == cudaSuccess;
   ok = ok && cudaMalloc(&h->B.list, nc * sizeof(int)) == cudaSuccess;
@@ -379,6 +386,7 @@ hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gam
   cudaMemset(h->B.count, 0, 4 * sizeof(int));
   cudaMemset(h->B.rerec, 0, sizeof(unsigned long long));
   for (int k = 0; k < 3; ++k) cudaMemset(h->U[k], 0, sbytes);
+  for (int k = 0; k < 3 && shadow; ++k) cudaMemset(h->U32[k], 0, sbytes / 2);
   if (cudaDeviceSynchronize() != cudaSuccess) { free_all(h); delete h; return HWENO_ECUDA; }
   *out = h;
   return HWENO_OK;
@@ -404,6 +412,7 @@ hweno_status hweno_set_moments(hweno_t h, const double* m, size_t count, int on_
   CK(h, cudaMemcpy2DAsync(h->U[h->cur], h->P.pitch * sizeof(double), m, h->P.nx * sizeof(double),
                           h->P.nx * sizeof(double), rows, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                           h->stream));
+  if (h->U32[h->cur]) hw::run_shadow32(h->P, h->U[h->cur], h->U32[h->cur], 0, h->P.ny, h->stream);
   CK(h, cudaMemsetAsync(h->B.status, 0, sizeof(unsigned), h->stream));
   h->have_state = true;
   h->stepped = false;
@@ -440,6 +449,7 @@ void launch_stage(hweno_t h, int k, int a, double dt, double t) {
   const size_t nc = ncell(h);
   hw::StageCall S{};
   S.stage = k; S.Un = h->U[a]; S.dt = dt;
+  const int in = k == 0 ? a : (k == 1 ? b : c), out = k == 1 ? c : b;
   if (k == 0) {
     S.Uin = h->U[a]; S.Uout = h->U[b]; S.cA = 0.0; S.cB = 1.0;
     S.mask = h->mask3; S.Mod = h->ModN; S.maskN = nullptr; S.ModN = nullptr;
@@ -450,6 +460,8 @@ void launch_stage(hweno_t h, int k, int a, double dt, double t) {
     S.Uin = h->U[c]; S.Uout = h->U[b]; S.cA = 1.0 / 3.0; S.cB = 2.0 / 3.0;
     S.mask = h->mask3 + 2 * nc; S.Mod = h->ModK; S.maskN = h->mask3; S.ModN = h->ModN;
   }
+  S.U32in = h->U32[in];
+  S.U32out = h->U32[out];
   if (h->P.fixtab) hw::run_fixfill(h->fix, h->fixtab, t, nullptr, nullptr, 0.0, h->stream);
   if (h->g.dim == 1) hw::run_stage_1d(h->P, h->T, h->fp32, h->B, S, h->stream);
   else hw::run_stage_2d(h->P, h->T, h->fp32, h->B, S, h->stream);
@@ -541,6 +553,8 @@ hweno_status hweno_copy_rows(hweno_t h, int j0, int nrows, double* buf, int to_s
     else
       CK(h, cudaMemcpy2DAsync(bb, w, st, h->P.pitch * sizeof(double), w, nrows, cudaMemcpyDeviceToDevice, h->stream));
   }
+  float* U32 = h->U32[(a + h->next_stage) % 3];
+  if (to_state && U32) hw::run_shadow32(h->P, U, U32, j0, nrows, h->stream);
   return HWENO_OK;
 }
 
@@ -588,12 +602,15 @@ cudaError_t advance_steps(hweno_t h, int a, cudaStream_t st) {
     S.dtp = stt + 1;
     S.stage = 0; S.Uin = h->U[a]; S.Un = h->U[a]; S.Uout = h->U[b]; S.cA = 0.0; S.cB = 1.0;
     S.mask = h->mask3; S.Mod = h->ModN; S.maskN = nullptr; S.ModN = nullptr;
+    S.U32in = h->U32[a]; S.U32out = h->U32[b];
     run(S);
     S.stage = 1; S.Uin = h->U[b]; S.Un = h->U[a]; S.Uout = h->U[c]; S.cA = 0.75; S.cB = 0.25;
     S.mask = h->mask3 + nc; S.Mod = h->ModK; S.maskN = h->mask3; S.ModN = h->ModN;
+    S.U32in = h->U32[b]; S.U32out = h->U32[c];
     run(S);
     S.stage = 2; S.Uin = h->U[c]; S.Un = h->U[a]; S.Uout = h->U[b]; S.cA = 1.0 / 3.0; S.cB = 2.0 / 3.0;
     S.mask = h->mask3 + 2 * nc; S.Mod = h->ModK;
+    S.U32in = h->U32[c]; S.U32out = h->U32[b];
     run(S);
     a = b;
   }
@@ -843,6 +860,9 @@ hweno_status hweno_set_fused(hweno_t h, int on) {
               h->g.indicator != HWENO_IND_ALL)))
     return fail(h, HWENO_ESTATE, "set_fused: the fused stage is for single 2D Euler handles with the KXRCF, "
                                  "none or all indicator");
+  // the fused stage keeps no float copy of the state: renew it when the pipeline takes over
+  if (!on && h->P.fused && h->have_state && h->U32[h->cur])
+    hw::run_shadow32(h->P, h->U[h->cur], h->U32[h->cur], 0, h->P.ny, h->stream);
   h->P.fused = on;
   drop_graphs(h);
   return HWENO_OK;

@@ -309,14 +309,14 @@ __device__ __forceinline__ T scalar_velocity(const Prob& P, T u, int dir) {
 // HLLC flux, eqs. (f_HLLC), (COEF), (uLR_), as a rotated 1D solver in direction
 // dir (the tangential velocity is carried through the star state).
 // Branch order: 0 <= sL -> fL; 0 <= s* -> f*L; 0 <= sR -> f*R; else fR.
-// WALL: the face of the forward step's solid block (one side the reflection of
+// wall: the face of the forward step's solid block (one side the reflection of
 // the other): the star branch is taken whatever the sign of the wave-speed
 // estimate, so the flux carries no mass or energy (s* = 0) and the normal
 // momentum flux is the star pressure -- the estimate of eq. (COEF) gives
 // s_L > 0 for flow running into a wall faster than about its sound speed,
 // where the first branch of eq. (f_HLLC) would let the gas through the wall.
-template <typename T, int NV, bool WALL = false>
-__device__ __forceinline__ void hllc(const Prob& P, const T* uL, const T* uR, int dir, T* F) {
+template <typename T, int NV>
+__device__ __forceinline__ void hllc(const Prob& P, const T* uL, const T* uR, int dir, T* F, bool wall = false) {
   constexpr bool two = NV == 4;
   const T g = pc<T>(P.cgamma);
   const int in = 1 + dir, it = 2 - dir;
@@ -345,7 +345,7 @@ __device__ __forceinline__ void hllc(const Prob& P, const T* uL, const T* uR, in
   const T coefL = ps <= pL ? T(1) : sqrt(T(1) + k * (ps / pL - T(1)));
   const T coefR = ps <= pR ? T(1) : sqrt(T(1) + k * (ps / pR - T(1)));
   const T sL = mL - cL * coefL, sR = mR + cR * coefR;
-  const bool useL = (!WALL && T(0) <= sL) || T(0) <= ss;     // left physical or left star flux
+  const bool useL = (!wall && T(0) <= sL) || T(0) <= ss;     // left physical or left star flux
   const T rK = useL ? rL : rR, mK = useL ? mL : mR, tK = useL ? tL : tR;
   const T EK = useL ? EL : ER, pK = useL ? pL : pR, sK = useL ? sL : sR;
   // physical normal flux of the chosen side
@@ -356,7 +356,7 @@ __device__ __forceinline__ void hllc(const Prob& P, const T* uL, const T* uR, in
   fK[1] = dir == 0 ? rK * mK * mK + pK : rK * mK * tK;
   if constexpr (two) fK[2] = dir == 0 ? rK * mK * tK : rK * mK * mK + pK;
   fK[iE] = mK * (EK + pK);
-  if (!WALL && (T(0) <= sL || !(T(0) <= sR || T(0) <= ss))) {   // supersonic: fL or fR
+  if (!wall && (T(0) <= sL || !(T(0) <= sR || T(0) <= ss))) {   // supersonic: fL or fR
 #pragma unroll
     for (int v = 0; v < NV; ++v) F[v] = fK[v];
     return;

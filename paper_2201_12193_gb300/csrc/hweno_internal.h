@@ -98,6 +98,8 @@ struct StageCall {
   double* Lout;            // optional: write L(Uin') (state layout) instead of the RK update
   double* Umod;            // optional (with Lout): write Uin'
   double* aleph;           // optional: KXRCF values [ny*nx]
+  const float* U32in = nullptr;   // FP32 form: float copy of Uin (its reconstruction input), or null
+  float* U32out = nullptr;        // FP32 form: float copy of Uout, written by the update
 };
 
 void run_stage_1d(const Prob& P, const HostTabs& T, int prec, const Bufs& B, const StageCall& S, cudaStream_t st);
@@ -173,6 +175,8 @@ void run_wavespeed(const Prob& P, const double* U, double* partials, double* out
 void run_advance_dt(const Prob& P, const double* speeds, const double* par, double* st, unsigned* status,
                     cudaStream_t s);
 void run_totals(const Prob& P, const double* U, double* partials, double* out, cudaStream_t st);
+// FP32 form: rows [j0, j0 + nrows) of the float copy of state U, rounded to nearest.
+void run_shadow32(const Prob& P, const double* U, float* U32, int j0, int nrows, cudaStream_t st);
 
 // Fixed-state (inflow) ghost cells of a 2D Euler handle: per side, a segment
 // of ghost positions whose centre coordinate along the side is below

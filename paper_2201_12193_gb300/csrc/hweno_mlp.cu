@@ -275,13 +275,21 @@ struct TSmem {
   __nv_bfloat16 da1t[NH * S2];    // (dL/da1)^T
   float gw1[NH * NINP];
   float gw2[NH * NH];
-  float gb1[NH], gb2[NH], gw3[NH], gb3, loss;
+  // per-warp sums (one writer each), combined in warp order at the end
+  float gb1[TT / 32][NH], gb2[TT / 32][NH], gw3[TT / 32][NH], gb3[TT / 32], loss[TT / 32];
 };
+
+// Sum over the 8 lanes of a warp that share lane & 3, in a fixed tree order.
+__device__ __forceinline__ float sum_over_g(float v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 16);
+  return v;
+}
 
 __global__ void __launch_bounds__(TT) mlp_train_kernel(const float* __restrict__ th, const float* __restrict__ X,
                                                        const float* __restrict__ y, const float* __restrict__ wt,
-                                                       int n, float inv_n, float* __restrict__ grad,
-                                                       float* __restrict__ loss) {
+                                                       int n, float inv_n, float* __restrict__ part) {
   extern __shared__ __align__(16) unsigned char smem[];
   TSmem& S = *reinterpret_cast<TSmem*>(smem);
   load_weights(th, S.W);
@@ -291,8 +299,10 @@ __global__ void __launch_bounds__(TT) mlp_train_kernel(const float* __restrict__
   }
   for (int q = threadIdx.x; q < NH * NINP; q += TT) S.gw1[q] = 0.f;
   for (int q = threadIdx.x; q < NH * NH; q += TT) S.gw2[q] = 0.f;
-  for (int q = threadIdx.x; q < NH; q += TT) { S.gb1[q] = 0.f; S.gb2[q] = 0.f; S.gw3[q] = 0.f; }
-  if (threadIdx.x == 0) { S.gb3 = 0.f; S.loss = 0.f; }
+  for (int q = threadIdx.x; q < (TT / 32) * NH; q += TT) {
+    (&S.gb1[0][0])[q] = 0.f; (&S.gb2[0][0])[q] = 0.f; (&S.gw3[0][0])[q] = 0.f;
+  }
+  if (threadIdx.x < TT / 32) { S.gb3[threadIdx.x] = 0.f; S.loss[threadIdx.x] = 0.f; }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   for (int base = blockIdx.x * TR; base < n; base += gridDim.x * TR) {
     __syncthreads();
@@ -309,7 +319,7 @@ __global__ void __launch_bounds__(TT) mlp_train_kernel(const float* __restrict__
     Frag F;
     float z[2];
     tile_forward(S.xs, r0, S.W, F, z);
-    float dz[2];
+    float dz[2], ls = 0.f;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int row = base + r0 + g + 8 * h;
@@ -319,11 +329,14 @@ __global__ void __launch_bounds__(TT) mlp_train_kernel(const float* __restrict__
         const float w = wt ? wt[row] : 1.0f;
         const float yy = y[row];
         d = w * (p - yy) * inv_n;
-        if (t == 0) atomicAdd(&S.loss, -w * (yy * logf(p + 1e-12f) + (1.f - yy) * logf(1.f - p + 1e-12f)) * inv_n);
+        ls += -w * (yy * logf(p + 1e-12f) + (1.f - yy) * logf(1.f - p + 1e-12f)) * inv_n;
       }
       dz[h] = d;
     }
-    if (t == 0) atomicAdd(&S.gb3, dz[0] + dz[1]);
+    {   // the four lanes of a row hold the same dz: lanes t == 0 count it
+      const float lw = sum_over_g(t == 0 ? ls : 0.f), gw = sum_over_g(t == 0 ? dz[0] + dz[1] : 0.f);
+      if (lane == 0) { S.loss[warp] += lw; S.gb3[warp] += gw; }
+    }
     // layer 3 and layer 2 gradients (C-fragment positions of this thread)
     float da2[8][4];
 #pragma unroll
@@ -339,8 +352,12 @@ __global__ void __launch_bounds__(TT) mlp_train_kernel(const float* __restrict__
         da2[nb][e] = dzr * w3 * gelu_grad(a);
         if (e & 1) gb2b += da2[nb][e]; else gb2a += da2[nb][e];
       }
-      atomicAdd(&S.gw3[c], gw3a); atomicAdd(&S.gw3[c + 1], gw3b);
-      atomicAdd(&S.gb2[c], gb2a); atomicAdd(&S.gb2[c + 1], gb2b);
+      gw3a = sum_over_g(gw3a); gw3b = sum_over_g(gw3b);
+      gb2a = sum_over_g(gb2a); gb2b = sum_over_g(gb2b);
+      if (g == 0) {
+        S.gw3[warp][c] += gw3a; S.gw3[warp][c + 1] += gw3b;
+        S.gb2[warp][c] += gb2a; S.gb2[warp][c + 1] += gb2b;
+      }
       // transposed BF16 copies for the weight-gradient GEMMs
       S.da2t[c * S2 + r0 + g] = __float2bfloat16_rn(da2[nb][0]);
       S.da2t[(c + 1) * S2 + r0 + g] = __float2bfloat16_rn(da2[nb][1]);
@@ -386,7 +403,8 @@ __global__ void __launch_bounds__(TT) mlp_train_kernel(const float* __restrict__
         if (e & 1) gb1b += d; else gb1a += d;
         S.da1t[(c + (e & 1)) * S2 + r0 + g + (e >> 1) * 8] = __float2bfloat16_rn(d);
       }
-      atomicAdd(&S.gb1[c], gb1a); atomicAdd(&S.gb1[c + 1], gb1b);
+      gb1a = sum_over_g(gb1a); gb1b = sum_over_g(gb1b);
+      if (g == 0) { S.gb1[warp][c] += gb1a; S.gb1[warp][c + 1] += gb1b; }
     }
     __syncthreads();
     // weight gradients over the 64 rows of the tile: warp w owns output rows 16w..16w+15
@@ -443,17 +461,37 @@ __global__ void __launch_bounds__(TT) mlp_train_kernel(const float* __restrict__
     }
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < NH * NIN; q += TT) atomicAdd(&grad[OFF_W1 + q], S.gw1[(q / NIN) * NINP + q % NIN]);
-  for (int q = threadIdx.x; q < NH * NH; q += TT) atomicAdd(&grad[OFF_W2 + q], S.gw2[q]);
+  // this block's gradient and loss into its own row of part (NPARAM + 1 floats);
+  // train_sum_kernel adds the rows in block order
+  float* row = part + (long long)blockIdx.x * (NPARAM + 1);
+  for (int q = threadIdx.x; q < NH * NIN; q += TT) row[OFF_W1 + q] = S.gw1[(q / NIN) * NINP + q % NIN];
+  for (int q = threadIdx.x; q < NH * NH; q += TT) row[OFF_W2 + q] = S.gw2[q];
   for (int q = threadIdx.x; q < NH; q += TT) {
-    atomicAdd(&grad[OFF_B1 + q], S.gb1[q]);
-    atomicAdd(&grad[OFF_B2 + q], S.gb2[q]);
-    atomicAdd(&grad[OFF_W3 + q], S.gw3[q]);
+    float b1 = 0.f, b2 = 0.f, w3 = 0.f;
+#pragma unroll
+    for (int w = 0; w < TT / 32; ++w) { b1 += S.gb1[w][q]; b2 += S.gb2[w][q]; w3 += S.gw3[w][q]; }
+    row[OFF_B1 + q] = b1;
+    row[OFF_B2 + q] = b2;
+    row[OFF_W3 + q] = w3;
   }
   if (threadIdx.x == 0) {
-    atomicAdd(&grad[OFF_B3], S.gb3);
-    atomicAdd(loss, S.loss);
+    float b3 = 0.f, ls = 0.f;
+#pragma unroll
+    for (int w = 0; w < TT / 32; ++w) { b3 += S.gb3[w]; ls += S.loss[w]; }
+    row[OFF_B3] = b3;
+    row[NPARAM] = ls;
   }
+}
+
+// grad[q] += sum over blocks b (in order) of part[b][q]; *loss likewise from slot NPARAM.
+__global__ void train_sum_kernel(const float* __restrict__ part, int nblocks, float* __restrict__ grad,
+                                 float* __restrict__ loss) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q > NPARAM) return;
+  float s = 0.f;
+  for (int b = 0; b < nblocks; ++b) s += part[(long long)b * (NPARAM + 1) + q];
+  if (q < NPARAM) grad[q] += s;
+  else *loss += s;
 }
 
 __global__ void adam_kernel(float* __restrict__ th, const float* __restrict__ grad, float* __restrict__ m1,
@@ -585,7 +623,20 @@ cudaError_t run_mlp_train(const float* th, const float* X, const float* y, const
   cudaError_t e = cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   const int blocks = (int)std::min<long long>((n + TR - 1) / TR, (long long)nsm);
-  mlp_train_kernel<<<blocks, TT, sm, st>>>(th, X, y, w, n, 1.0f / (float)n, grad, loss);
+  // per-block partial sums, added in block order: the gradient does not depend
+  // on the order in which blocks finish (training runs are reproducible)
+  static float* part = nullptr;
+  static size_t cap = 0;
+  const size_t need = (size_t)blocks * (NPARAM + 1);
+  if (need > cap) {
+    if (part) cudaFree(part);
+    part = nullptr;
+    cap = 0;
+    if ((e = cudaMalloc(&part, need * sizeof(float))) != cudaSuccess) return e;
+    cap = need;
+  }
+  mlp_train_kernel<<<blocks, TT, sm, st>>>(th, X, y, w, n, 1.0f / (float)n, part);
+  train_sum_kernel<<<(NPARAM + 1 + 255) / 256, 256, 0, st>>>(part, blocks, grad, loss);
   return cudaGetLastError();
 }
 

@@ -162,7 +162,26 @@ __global__ void fixfill_kernel(FixSpec F, double* __restrict__ tab, double t, co
   for (int v = 0; v < 4; ++v) tab[4 * (long long)q + v] = src ? src[v] : 0.0;
 }
 
+// The float copy of rows [j0, j0 + nrows) of every moment plane (FP32 form):
+// each state value rounded to nearest by integer work, as the update kernel
+// rounds the values it writes.
+__global__ void shadow32_kernel(Prob P, const double* __restrict__ U, float* __restrict__ U32, int j0, int nrows) {
+  const long long per = (long long)nrows * P.nx, n = (long long)P.nvar * P.nmom * per;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const long long q = t / per, r = t % per;
+    const long long si = q * P.plane + (long long)(j0 + r / P.nx) * P.pitch + r % P.nx;
+    U32[si] = f32_rn(U[si]);
+  }
+}
+
 }  // namespace
+
+void run_shadow32(const Prob& P, const double* U, float* U32, int j0, int nrows, cudaStream_t st) {
+  const long long n = (long long)P.nvar * P.nmom * nrows * P.nx;
+  if (n <= 0) return;
+  const int nb = (int)std::min<long long>((n + RT - 1) / RT, (long long)P.nsm * 16);
+  shadow32_kernel<<<nb, RT, 0, st>>>(P, U, U32, j0, nrows);
+}
 
 void run_fixfill(const FixSpec& F, double* tab, double t, const double* tn, const double* dtp, double c,
                  cudaStream_t st) {

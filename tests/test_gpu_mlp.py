@@ -344,3 +344,16 @@ def test_activation_matches_exact_erf():
     z_gpu = np.log(pr / (1 - pr))
     z_ref, _ = ref.forward(th, X.astype(np.float64), bf=True)
     assert np.abs(z_gpu - z_ref).max() <= 1e-4
+
+
+def test_training_is_reproducible():
+    """The gradient is summed per block and then over blocks in block order
+    (no floating-point atomics), so two training runs from the same seed give
+    the same parameters bit for bit."""
+    from paper_2201_12193_gb300 import learn
+    probs = learn.training_problems(seed=3, n=64, count=2)
+    X, y, w = learn.harvest(probs, steps=4, pos_weight=3.0)
+    a, ha = learn.train(X, y, w, epochs=3, batch=2048, lr=3e-3)
+    b, hb = learn.train(X, y, w, epochs=3, batch=2048, lr=3e-3)
+    np.testing.assert_array_equal(a, b)
+    assert ha == hb
