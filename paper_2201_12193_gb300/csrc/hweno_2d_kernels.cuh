@@ -191,7 +191,7 @@ __device__ __forceinline__ void rec2d_cell(const Prob& P, const Weights<T>& W, c
             for (int q = 0; q < 12; ++q) rinv[bp[q]] = r[q];
           } else {
 #pragma unroll
-            for (int q = 0; q < 12; ++q) rinv[bp[q]] = T(1) / out[bp[q]];
+            for (int q = 0; q < 12; ++q) rinv[bp[q]] = rcp(out[bp[q]]);
           }
         } else if (P.eq == EQ_BURGERS) {
 #pragma unroll

@@ -221,6 +221,12 @@ __device__ __forceinline__ double avg_img(const Prob& P, const double* __restric
 // ---------------------------------------------------------------- physics
 // Physical flux of eq. (1D-Euler) / (2D-Euler) or of the scalar laws in
 // direction dir (0 = x, 1 = y); NV = 1 (scalar), 3 (1D Euler), 4 (2D Euler).
+// 1/x correctly rounded (the same value as the IEEE division 1/x) by the
+// reciprocal intrinsics of the two hardware precisions; double-float divides.
+template <typename T> __device__ __forceinline__ T rcp(T x) { return T(1) / x; }
+template <> __device__ __forceinline__ float rcp<float>(float x) { return __frcp_rn(x); }
+template <> __device__ __forceinline__ double rcp<double>(double x) { return __drcp_rn(x); }
+
 template <typename T, int NV>
 __device__ __forceinline__ void phys_flux(const Prob& P, const T* u, int dir, T* f) {
   if constexpr (NV == 1) {
@@ -228,12 +234,12 @@ __device__ __forceinline__ void phys_flux(const Prob& P, const T* u, int dir, T*
     else f[0] = T(0.5) * u[0] * u[0];
   } else if constexpr (NV == 3) {
     const T g = pc<T>(P.cgamma);
-    const T inv = T(1) / u[0], mu = u[1] * inv, E = u[2];
+    const T inv = rcp(u[0]), mu = u[1] * inv, E = u[2];
     const T p = (g - T(1)) * (E - T(0.5) * u[1] * mu);
     f[0] = u[1]; f[1] = u[1] * mu + p; f[2] = mu * (E + p);
   } else {
     const T g = pc<T>(P.cgamma);
-    const T inv = T(1) / u[0], mu = u[1] * inv, nu = u[2] * inv, E = u[3];
+    const T inv = rcp(u[0]), mu = u[1] * inv, nu = u[2] * inv, E = u[3];
     const T p = (g - T(1)) * (E - T(0.5) * (u[1] * mu + u[2] * nu));
     if (dir == 0) { f[0] = u[1]; f[1] = u[1] * mu + p; f[2] = u[1] * nu; f[3] = mu * (E + p); }
     else          { f[0] = u[2]; f[1] = u[2] * mu; f[2] = u[2] * nu + p; f[3] = nu * (E + p); }
@@ -265,7 +271,7 @@ __device__ __forceinline__ void batch_inverse(const T (&x)[N], T (&inv)[N]) {
   pre[0] = x[0];
 #pragma unroll
   for (int i = 1; i < N; ++i) pre[i] = pre[i - 1] * x[i];
-  T r = T(1) / pre[N - 1];
+  T r = rcp(pre[N - 1]);
 #pragma unroll
   for (int i = N - 1; i > 0; --i) {
     inv[i] = r * pre[i - 1];
@@ -322,15 +328,9 @@ __device__ __forceinline__ void hllc(const Prob& P, const T* uL, const T* uR, in
   const int in = 1 + dir, it = 2 - dir;
   constexpr int iE = NV - 1;
   const T rL = uL[0], rR = uR[0];
-  T iL, iR;
-  if constexpr (sizeof(T) == 8) {   // FP64: one division for both reciprocals
-    const T q = T(1) / (rL * rR);
-    iL = rR * q;
-    iR = rL * q;
-  } else {
-    iL = T(1) / rL;
-    iR = T(1) / rR;
-  }
+  // one reciprocal for both densities' reciprocals
+  const T q = rcp(rL * rR);
+  const T iL = rR * q, iR = rL * q;
   const T mL = uL[in] * iL, mR = uR[in] * iR;
   const T tL = two ? uL[it] * iL : T(0), tR = two ? uR[it] * iR : T(0);
   const T EL = uL[iE], ER = uR[iE];
@@ -362,18 +362,12 @@ __device__ __forceinline__ void hllc(const Prob& P, const T* uL, const T* uR, in
     return;
   }
   const T a = sK - mK, b = sK - ss;
-  T fac, ek, pk;
-  if constexpr (sizeof(T) == 8) {   // FP64: D = 1/(a b) gives 1/a and 1/b with one division
-    const T iK = useL ? iL : iR;
-    const T D = T(1) / (a * b);
-    fac = rK * a * (a * D);
-    ek = EK * iK;
-    pk = pK * iK * (b * D);
-  } else {
-    fac = rK * a / b;
-    ek = EK / rK;
-    pk = pK / (rK * a);
-  }
+  // D = 1/(a b) gives 1/a and 1/b with one reciprocal
+  const T iK = useL ? iL : iR;
+  const T D = rcp(a * b);
+  const T fac = rK * a * (a * D);
+  const T ek = EK * iK;
+  const T pk = pK * iK * (b * D);
   T us[NV];
   us[0] = fac;
   us[in] = fac * ss;
@@ -418,13 +412,13 @@ __device__ __forceinline__ void combine_weights(const Weights<T>& W, const T bet
     const T n1 = W.gam[1] * (x1 + tau4) * (x0 * p23);
     const T n2 = W.gam[2] * (x2 + tau4) * (p01 * x3);
     const T n3 = W.gam[3] * (x3 + tau4) * (p01 * x2);
-    const T inv = T(1) / ((n0 + n1) + (n2 + n3));
+    const T inv = rcp((n0 + n1) + (n2 + n3));
     om[0] = n0 * inv; om[1] = n1 * inv; om[2] = n2 * inv; om[3] = n3 * inv;
   } else {
     T wb[4], ws = T(0);
 #pragma unroll
     for (int l = 0; l < 4; ++l) { wb[l] = W.gam[l] * (T(1) + tau4 / (beta[l] + W.eps)); ws += wb[l]; }
-    const T inv = T(1) / ws;
+    const T inv = rcp(ws);
 #pragma unroll
     for (int l = 0; l < 4; ++l) om[l] = wb[l] * inv;
   }
@@ -456,7 +450,7 @@ __device__ __forceinline__ void recon1d(const Weights<T>& W, const Beta1<T>& B, 
     } else {
       const T wl = T(0.5) * (T(1) + t1 / (bl + W.eps));
       const T wr = T(0.5) * (T(1) + t1 / (br + W.eps));
-      const T inv = T(1) / (wl + wr);
+      const T inv = rcp(wl + wr);
       gg = (wl * inv) * dl + (wr * inv) * dr;
     }
     beta[0] = gg * gg;
@@ -496,7 +490,7 @@ __device__ __forceinline__ void recon2d(const Weights<T>& W, const Beta2<T>& B, 
       const T y0 = b1[0] + W.eps, y1 = b1[1] + W.eps, y2 = b1[2] + W.eps, y3 = b1[3] + W.eps;
       const T p01 = y0 * y1, p23 = y2 * y3;
       const T n[4] = {(y0 + t1) * (y1 * p23), (y1 + t1) * (y0 * p23), (y2 + t1) * (p01 * y3), (y3 + t1) * (p01 * y2)};
-      const T inv = T(1) / ((n[0] + n[1]) + (n[2] + n[3]));
+      const T inv = rcp((n[0] + n[1]) + (n[2] + n[3]));
 #pragma unroll
       for (int k = 0; k < 4; ++k) { gx = fma(n[k], bx[k], gx); gy = fma(n[k], by[k], gy); }
       gx *= inv;
@@ -505,7 +499,7 @@ __device__ __forceinline__ void recon2d(const Weights<T>& W, const Beta2<T>& B, 
       T w[4], wsum = T(0);
 #pragma unroll
       for (int k = 0; k < 4; ++k) { w[k] = T(0.25) * (T(1) + t1 / (b1[k] + W.eps)); wsum += w[k]; }
-      const T inv = T(1) / wsum;
+      const T inv = rcp(wsum);
 #pragma unroll
       for (int k = 0; k < 4; ++k) { gx = fma(w[k] * inv, bx[k], gx); gy = fma(w[k] * inv, by[k], gy); }
     }

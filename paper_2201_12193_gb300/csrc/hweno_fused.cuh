@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 4 : 2)
       for (int m = 0; m < 3; ++m) {
         const long long si = (long long)(v * 3 + m) * P.plane + so;
         rin[m] = S.Uin[si];
-        if (!S.Lout) rn[m] = S.Un[si];
+        if (!S.Lout && S.cA != 0.0) rn[m] = S.Un[si];
       }
       rfn = P.persist && S.maskN && S.maskN[(long long)ju * P.nx + i] != 0;
     }
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 4 : 2)
         for (int k = 0; k < 12; ++k) rinv[bp[k]] = r[k];
       } else {
 #pragma unroll
-        for (int k = 0; k < 12; ++k) rinv[bp[k]] = T(1) / sm.G[s5][0][bp[k]][c];
+        for (int k = 0; k < 12; ++k) rinv[bp[k]] = rcp(sm.G[s5][0][bp[k]][c]);
       }
       T pxl = T(0), pxr = T(0), pyb = T(0), pyt = T(0);
 #pragma unroll
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 4 : 2)
         if constexpr (sizeof(T) == 8) batch_inverse<4, T>(rho, inv);
         else {
 #pragma unroll
-          for (int l = 0; l < 4; ++l) inv[l] = T(1) / rho[l];
+          for (int l = 0; l < 4; ++l) inv[l] = rcp(rho[l]);
         }
 #pragma unroll
         for (int v = 0; v < 4; ++v) Fc[v] = Gc[v] = T(0);
@@ -468,10 +468,12 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 4 : 2)
       const double idx = P.crdx.d, idy = P.crdy.d;
       const T tidx = pc<T>(P.crdx), tidy = pc<T>(P.crdy);
       double L[3];
-      L[0] = -((double)Fp - (double)Fm) * idx - ((double)Gp - (double)Gm) * idy;
-      L[1] = (double)(-(Fp + Fm) * T(0.5) * tidx + Fcv * tidx - (Gpx - Gmx) * tidy);
-      L[2] = (double)(-(Fpe - Fme) * tidx - (Gp + Gm) * T(0.5) * tidy + Gcv * tidy);
+      L[0] = -(to_f64(Fp) - to_f64(Fm)) * idx - (to_f64(Gp) - to_f64(Gm)) * idy;
+      L[1] = to_f64(-(Fp + Fm) * T(0.5) * tidx + Fcv * tidx - (Gpx - Gmx) * tidy);
+      L[2] = to_f64(-(Fpe - Fme) * tidx - (Gp + Gm) * T(0.5) * tidy + Gcv * tidy);
       const bool live = act && i < P.nx;
+      const bool first = S.cA == 0.0;   // the first stage has no U^n term
+      bool finite = true;
       double newavg = 0.0;
       if (live) {
         const long long so = (long long)ju * P.pitch + i;
@@ -486,12 +488,18 @@ __global__ void __launch_bounds__(FZ_NT, sizeof(T) == 4 ? 4 : 2)
             if (S.Umod) S.Umod[si] = uin;
             continue;
           }
-          const double un = (m > 0 && fn) ? S.ModN[(long long)(v * 2 + m - 1) * P.plane + so] : rn[m];
-          const double r = S.cA * un + S.cB * (uin + dt * L[m]);
+          double r;
+          if (first) {   // U^(1) = U' + dt L
+            r = fma(dt, L[m], uin);
+          } else {
+            const double un = (m > 0 && fn) ? S.ModN[(long long)(v * 2 + m - 1) * P.plane + so] : rn[m];
+            r = S.cA * un + S.cB * (uin + dt * L[m]);
+          }
           S.Uout[si] = r;
           if (m == 0) newavg = r;
-          if (!isfinite(r) && ju >= P.jlo && ju < P.jhi) atomicOr(S.status, ST_NONFINITE);
+          finite = finite && ((__double_as_longlong(r) >> 52) & 0x7FF) != 0x7FF;
         }
+        if (!finite && ju >= P.jlo && ju < P.jhi) atomicOr(S.status, ST_NONFINITE);
       }
       // positivity of the new cell average (lane v = 0 gathers the cell's four variables)
       const int base = (tid & 31) & ~3;
