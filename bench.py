@@ -348,7 +348,12 @@ def run_batched(torch, hweno, args, world, rank):
 MLP_FLOP_PER_CELL = 2 * (108 * 64 + 64 * 64 + 64)    # 11,072 multiply-adds per cell
 
 
-KERNEL_SOURCES = ("hweno_2d_kernels.cuh", "hweno_device.cuh", "hweno_parity.h", "hweno_internal.h", "hweno_fused.cuh")
+KERNEL_SOURCES = ("hweno_2d_kernels.cuh", "hweno_device.cuh", "hweno_parity.h", "hweno_internal.h", "hweno_fused.cuh",
+                  "df64.cuh")
+# FP32-bulk update kernel, bytes per cell and launch that its inputs and outputs
+# fix: point values 4 x 16 x 4 B, U^(k) 96 B, U^n 96 B in two stages of three
+# (64 B on average), U^(k+1) 96 B and its float copy 48 B
+UPD32_BYTES_PER_CELL = 256 + 96 + 64 + 96 + 48
 
 
 def source_hash():
@@ -864,6 +869,23 @@ def run_ours(args, world, rank, local):
                              "rel_l1_vs_fp64_after_steps": float(np.abs(a - b).sum() / np.abs(b).sum()),
                              "steps_compared": args.warmup + args.steps,
                              "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof32.items()}}
+        rk_ms, rk_n = prof32["reconstruct"]
+        up_ms, up_n = prof32["update"]
+        if rk_n:
+            ach = _rec_flop_per_cell(4) * cells * rk_n / (rk_ms * 1e-3) / 1e12
+            t = traffic_per_cell("rec2d_fp32")
+            forms["fp32bulk"]["roofline_reconstruct"] = {
+                "bound": "alu", "achieved": ach, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+                "frac": ach / peaks["fp32_tflops"], "peak_source": "FP32 FMA throughput measured in this run (of measured)",
+                "flop_per_cell": _rec_flop_per_cell(4), "avg_ms": rk_ms / rk_n,
+                "traffic": t * cells if t else None}
+        if up_n:
+            gbs = UPD32_BYTES_PER_CELL * cells * up_n / (up_ms * 1e-3) / 1e9
+            t = traffic_per_cell("update2d_fp32")
+            forms["fp32bulk"]["roofline_update"] = {
+                "bound": "hbm", "achieved": gbs, "peak": hbm_gbps, "unit": "GB/s", "frac": gbs / hbm_gbps,
+                "peak_source": hbm_src, "bytes_per_cell": UPD32_BYTES_PER_CELL, "avg_ms": up_ms / up_n,
+                "traffic": t * cells if t else None}
         s32.close()
         sx, msx, profx, _, outx = run_solver(torch, hweno, p, "df64", args.steps, args.warmup, world, profile=True)
         msx = max_over_ranks(msx, world)
