@@ -400,7 +400,9 @@ struct Rk {
 
 // Step 3 for the TXV x TYV tile at (i0, j0): face fluxes into shared memory, then
 // quadrature, L(U) and the Runge-Kutta combination per cell.  tid = ty*TXV + tx.
-template <typename T, int NV, int TXV, int TYV>
+// SOLID: the handle may have a solid block (FP64 2D Euler only); without it the
+// wall-face code is not compiled in (the batched kernel runs at the register limit).
+template <typename T, int NV, int TXV, int TYV, bool SOLID = false>
 __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict__ G, const Rk& S, int i0, int j0,
                                               int tid, T (&xf)[TYV][TXV + 1][4][NV], T (&yf)[TYV + 1][TXV][4][NV]) {
   const int tx = tid % TXV, ty = tid / TXV;
@@ -414,7 +416,7 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
   constexpr int NXP = (TXV + 1) * TYV * 4, NYP = TXV * (TYV + 1) * 4;
   // a tile whose faces all join cells inside the grid (no image, no solid cell):
   // the point values at fixed offsets
-  const bool tin = P.sol_j == 0 && i0 >= 1 && i0 + TXV < P.nx && j0 >= 1 && j0 + TYV < P.ny;
+  const bool tin = (!SOLID || P.sol_j == 0) && i0 >= 1 && i0 + TXV < P.nx && j0 >= 1 && j0 + TYV < P.ny;
   __syncthreads();   // the shared arrays may still be read for a previous tile
   for (int f = tid; f < NXP + NYP; f += TXV * TYV) {
     // the face's GL point q, its slot (c, r) in the tile, its two cells a
@@ -436,10 +438,10 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
       }
     } else {
       if (aJ >= P.ny || aI >= P.nx) continue;
-      const bool sa = P.sol_j > 0 && is_solid(P, aI, aJ), sb = P.sol_j > 0 && is_solid(P, bI, bJ);
+      const bool sa = SOLID && P.sol_j > 0 && is_solid(P, aI, aJ), sb = SOLID && P.sol_j > 0 && is_solid(P, bI, bJ);
       // a face no fluid cell uses (solid on one side, solid or outside on the
       // other) is skipped: only solid cells would read it, and they are not updated
-      if (P.sol_j > 0 && (sa || aI < 0 || aJ < 0) && (sb || bI >= P.nx || bJ >= P.ny)) continue;
+      if (SOLID && P.sol_j > 0 && (sa || aI < 0 || aJ < 0) && (sb || bI >= P.nx || bJ >= P.ny)) continue;
       if (!sa) gl_state<T, NV>(P, G, image(P, aI, aJ), ka, la, uL);
       if (!sb) gl_state<T, NV>(P, G, image(P, bI, bJ), kb, lb, uR);
       // a face shared with a solid cell: the outer state is the reflection of
@@ -459,7 +461,7 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
   }
   __syncthreads();
   if (!live) return;
-  if (P.sol_j > 0 && is_solid(P, i, j)) {   // solid cells are not updated: the state passes through
+  if (SOLID && P.sol_j > 0 && is_solid(P, i, j)) {   // solid cells are not updated: the state passes through
     if (!S.Lout) {
 #pragma unroll 1
       for (int q = 0; q < NV * 3; ++q) {
@@ -581,7 +583,7 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
   }
 }
 
-template <typename T, int NV>
+template <typename T, int NV, bool SOLID = false>
 __global__ void __launch_bounds__(TX * TY, (std::is_same<T, float>::value ? 8 : 3)) update2d_kernel(Prob P, const T* __restrict__ G, Rk S) {
   __shared__ T xf[TY][TX + 1][4][NV];
   __shared__ T yf[TY + 1][TX][4][NV];
@@ -598,7 +600,7 @@ __global__ void __launch_bounds__(TX * TY, (std::is_same<T, float>::value ? 8 : 
       return;
     }
   }
-  update2d_tile<T, NV, TX, TY>(P, G, S, blockIdx.x * TX, blockIdx.y * TY, threadIdx.y * TX + threadIdx.x, xf, yf);
+  update2d_tile<T, NV, TX, TY, SOLID>(P, G, S, blockIdx.x * TX, blockIdx.y * TY, threadIdx.y * TX + threadIdx.x, xf, yf);
 }
 
 }  // namespace
@@ -687,7 +689,12 @@ void stage_t(const Prob& P, const HostTabs& HT, const Weights<T>& W, const Beta2
   Rk r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status, S.dtp,
        std::is_same<T, float>::value ? S.U32out : nullptr};
   if (B.prof) B.prof->begin(3, st);
-  update2d_kernel<T, NV><<<grd, blk, 0, st>>>(P, (const T*)B.G, r);
+  if constexpr (NV == 4 && std::is_same<T, double>::value) {
+    if (P.sol_j > 0) update2d_kernel<T, NV, true><<<grd, blk, 0, st>>>(P, (const T*)B.G, r);
+    else update2d_kernel<T, NV><<<grd, blk, 0, st>>>(P, (const T*)B.G, r);
+  } else {
+    update2d_kernel<T, NV><<<grd, blk, 0, st>>>(P, (const T*)B.G, r);
+  }
   if (B.prof) B.prof->end(st);
 }
 
