@@ -232,9 +232,12 @@ __device__ __forceinline__ void rec2d_cell(const Prob& P, const Weights<T>& W, c
 // rerec (REC_FLAGGED only, may be null) accumulates the number of cells
 // reconstructed a second time.
 // Double-float: 4 resident blocks per SM (at most 128 registers, a few spills)
-// beat 3 (168 registers, none): 7.0 vs 8.3 ms per launch at 2048^2.
+// beat 3 (168 registers, none): 7.0 vs 8.3 ms per launch at 2048^2.  FP32 with
+// the float copy: 8 blocks (64 registers, 164 B of spills) measured 0.545 ms per
+// 2048^2 launch against 0.685 at 4 blocks (119 registers).  FP64 is pipe-bound:
+// 2, 3 or 4 blocks run alike.
 template <typename T, int NV, int MODE, bool FIX = false, bool S32 = false>
-__global__ void __launch_bounds__(RB, (is_df64<T>::value || std::is_same<T, float>::value ? 4 : 1)) rec2d_kernel(Prob P, Weights<T> W, Beta2<T> B, const double* __restrict__ U,
+__global__ void __launch_bounds__(RB, (is_df64<T>::value ? 4 : (std::is_same<T, float>::value ? 8 : 1))) rec2d_kernel(Prob P, Weights<T> W, Beta2<T> B, const double* __restrict__ U,
                                                   const uint8_t* __restrict__ mask, const double* __restrict__ Mod,
                                                   const int* __restrict__ list, const int* __restrict__ count,
                                                   T* __restrict__ G, T* __restrict__ aux,
