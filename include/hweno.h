@@ -326,6 +326,18 @@ hweno_status hweno_set_solid(hweno_t h, int i0, int j1);
  * quadrature sums.  Applies to hweno_step, hweno_advance and hweno_rhs. */
 hweno_status hweno_set_fused(hweno_t h, int on);
 
+/* TMA staging of the FP32-bulk update (off by default): each interior 32 x 4
+ * tile loads its own point values (64 planes) into shared memory with one
+ * cp.async.bulk.tensor completing on an mbarrier (the wait is bounded: past the
+ * limit the step reports HWENO_ETIMEOUT); the one-cell halo, the stage states
+ * and the tiles at the grid's edges read global memory.  The arithmetic is the
+ * same code either way, so results are bitwise the same with on = 0 or 1.  Off
+ * by default because the global-memory kernel, at 8 resident blocks per SM,
+ * measured faster than the staged one at the 4 its shared memory allows.
+ * Single 2D Euler FP32-bulk handles (else ESTATE for on = 1); EINVAL unless on
+ * is 0 or 1. */
+hweno_status hweno_set_tma(hweno_t h, int on);
+
 /* How the first moments modified by eq. (vi) in troubled cells (Step 2.2) are
  * used; the paper does not say.  persist = 1 (default): they replace the
  * stage input, so the Runge-Kutta combination of eq. (Runge-Kutta) takes them

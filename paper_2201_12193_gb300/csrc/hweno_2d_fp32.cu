@@ -8,4 +8,9 @@ void run_stage_2d_fp32(const Prob& P, const HostTabs& T, const Bufs& B, const St
   else stage_t<float, 1>(P, T, T.wf, T.b2f, B, S, st);
 }
 
+bool prepare_update_tma() {
+  static const bool ok = set_update_tma_attribute();
+  return ok;
+}
+
 }  // namespace hw

@@ -401,17 +401,57 @@ struct Rk {
   float* U32out = nullptr;   // FP32 form: the float copy of Uout (the next stage's reconstruction input)
 };
 
+// Where update2d_tile reads point values and stage states: global memory (any
+// tile) or, for an interior tile of the FP32 TMA kernel, the boxes staged in
+// shared memory.  The arithmetic is the same template either way, so both give
+// bitwise the same results.
+template <typename T>
+struct GlobalSrc {
+  static constexpr bool staged = false;
+  const T* __restrict__ G;
+  __device__ __forceinline__ T g(const Prob& P, int v, int p, int i, int j) const {
+    return G[(long long)(v * 16 + p) * P.gplane + goff(P, i, j)];
+  }
+  __device__ __forceinline__ double uin(const Prob& P, const Rk& S, int q, int i, int j) const {
+    return S.Uin[(long long)q * P.plane + (long long)j * P.pitch + i];
+  }
+  __device__ __forceinline__ double un(const Prob& P, const Rk& S, int q, int i, int j) const {
+    return S.Un[(long long)q * P.plane + (long long)j * P.pitch + i];
+  }
+};
+
+// The TMA kernel's shared-memory box (FP32): the tile's own point values,
+// [64 planes][4 rows][32 columns] from cell (i0, j0); the one-cell halo the face
+// fluxes need and the stage states come from global memory.
+constexpr int GBX = 32, GBY = 4;
+struct StagedSrc {
+  static constexpr bool staged = true;
+  const float* gs;
+  const float* __restrict__ G;
+  int i0, j0;
+  __device__ __forceinline__ float g(const Prob& P, int v, int p, int i, int j) const {
+    const int x = i - i0, y = j - j0;
+    if ((unsigned)x < (unsigned)GBX && (unsigned)y < (unsigned)GBY) return gs[((v * 16 + p) * GBY + y) * GBX + x];
+    return G[(long long)(v * 16 + p) * P.gplane + goff(P, i, j)];
+  }
+  __device__ __forceinline__ double uin(const Prob& P, const Rk& S, int q, int i, int j) const {
+    return S.Uin[(long long)q * P.plane + (long long)j * P.pitch + i];
+  }
+  __device__ __forceinline__ double un(const Prob& P, const Rk& S, int q, int i, int j) const {
+    return S.Un[(long long)q * P.plane + (long long)j * P.pitch + i];
+  }
+};
+
 // Step 3 for the TXV x TYV tile at (i0, j0): face fluxes into shared memory, then
 // quadrature, L(U) and the Runge-Kutta combination per cell.  tid = ty*TXV + tx.
 // SOLID: the handle may have a solid block (FP64 2D Euler only); without it the
 // wall-face code is not compiled in (the batched kernel runs at the register limit).
-template <typename T, int NV, int TXV, int TYV, bool SOLID = false>
-__device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict__ G, const Rk& S, int i0, int j0,
+template <typename T, int NV, int TXV, int TYV, bool SOLID = false, typename Src = GlobalSrc<T>>
+__device__ __forceinline__ void update2d_tile(const Prob& P, const Src& src, const Rk& S, int i0, int j0,
                                               int tid, T (&xf)[TYV][TXV + 1][4][NV], T (&yf)[TYV + 1][TXV][4][NV]) {
   const int tx = tid % TXV, ty = tid / TXV;
   const int i = i0 + tx, j = j0 + ty;
   const bool live = i < P.nx && j < P.ny;
-  const Img self{i, j, 1, 1, 0, -1};
   // Every face flux of the tile at one Gauss-Lobatto point per iteration, by one
   // call site, so that a face shared by two tiles gets bitwise the same flux
   // from both (the flux differences then telescope exactly in FP64).
@@ -419,7 +459,7 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
   constexpr int NXP = (TXV + 1) * TYV * 4, NYP = TXV * (TYV + 1) * 4;
   // a tile whose faces all join cells inside the grid (no image, no solid cell):
   // the point values at fixed offsets
-  const bool tin = (!SOLID || P.sol_j == 0) && i0 >= 1 && i0 + TXV < P.nx && j0 >= 1 && j0 + TYV < P.ny;
+  const bool tin = Src::staged || ((!SOLID || P.sol_j == 0) && i0 >= 1 && i0 + TXV < P.nx && j0 >= 1 && j0 + TYV < P.ny);
   __syncthreads();   // the shared arrays may still be read for a previous tile
   for (int f = tid; f < NXP + NYP; f += TXV * TYV) {
     // the face's GL point q, its slot (c, r) in the tile, its two cells a
@@ -433,13 +473,13 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
     T uL[NV], uR[NV];
     bool wall = false;
     if (tin) {
-      const long long oa = goff(P, aI, aJ), ob = goff(P, bI, bJ);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        uL[v] = G[(long long)(v * 16 + ka * 4 + la) * P.gplane + oa];
-        uR[v] = G[(long long)(v * 16 + kb * 4 + lb) * P.gplane + ob];
+        uL[v] = src.g(P, v, ka * 4 + la, aI, aJ);
+        uR[v] = src.g(P, v, kb * 4 + lb, bI, bJ);
       }
-    } else {
+    } else if constexpr (!Src::staged) {
+      const T* __restrict__ G = src.G;
       if (aJ >= P.ny || aI >= P.nx) continue;
       const bool sa = SOLID && P.sol_j > 0 && is_solid(P, aI, aJ), sb = SOLID && P.sol_j > 0 && is_solid(P, bI, bJ);
       // a face no fluid cell uses (solid on one side, solid or outside on the
@@ -505,14 +545,15 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
     // Euler, FP64: the 16 reciprocal densities with one division
     T rho[16], inv[16];
 #pragma unroll
-    for (int p = 0; p < 16; ++p) rho[p] = G[(long long)p * P.gplane + goff(P, i, j)];
+    for (int p = 0; p < 16; ++p) rho[p] = src.g(P, 0, p, i, j);
     batch_inverse_ranged<16, T>(rho, inv);
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         T u[NV], fx[NV], gy[NV];
-        gl_state<T, NV>(P, G, self, k, l, u);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) u[v] = src.g(P, v, k * 4 + l, i, j);
         euler_flux_inv<T, NV>(P, u, inv[k * 4 + l], 0, fx);
         euler_flux_inv<T, NV>(P, u, inv[k * 4 + l], 1, gy);
         const T w = gl_w<T>(k) * gl_w<T>(l);
@@ -525,7 +566,8 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
 #pragma unroll
       for (int l = 0; l < 4; ++l) {
         T u[NV], fx[NV], gy[NV];
-        gl_state<T, NV>(P, G, self, k, l, u);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) u[v] = src.g(P, v, k * 4 + l, i, j);
         phys_flux<T, NV>(P, u, 0, fx);
         phys_flux<T, NV>(P, u, 1, gy);
         const T w = gl_w<T>(k) * gl_w<T>(l);
@@ -557,7 +599,7 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
       const long long si = (long long)(v * 3 + m) * P.plane + so;
-      const double uin = (m > 0 && fk) ? S.Mod[(long long)(v * 2 + m - 1) * P.plane + so] : S.Uin[si];
+      const double uin = (m > 0 && fk) ? S.Mod[(long long)(v * 2 + m - 1) * P.plane + so] : src.uin(P, S, v * 3 + m, i, j);
       if (S.Lout) {
         S.Lout[si] = L[m];
         if (S.Umod) S.Umod[si] = uin;
@@ -567,7 +609,7 @@ __device__ __forceinline__ void update2d_tile(const Prob& P, const T* __restrict
       if (first) {
         r = fma(S.dt, L[m], uin);
       } else {
-        const double un = (m > 0 && fn) ? S.ModN[(long long)(v * 2 + m - 1) * P.plane + so] : S.Un[si];
+        const double un = (m > 0 && fn) ? S.ModN[(long long)(v * 2 + m - 1) * P.plane + so] : src.un(P, S, v * 3 + m, i, j);
         r = S.cA * un + S.cB * (uin + S.dt * L[m]);
       }
       S.Uout[si] = r;
@@ -603,7 +645,92 @@ __global__ void __launch_bounds__(TX * TY, (std::is_same<T, float>::value ? 8 : 
       return;
     }
   }
-  update2d_tile<T, NV, TX, TY, SOLID>(P, G, S, blockIdx.x * TX, blockIdx.y * TY, threadIdx.y * TX + threadIdx.x, xf, yf);
+  update2d_tile<T, NV, TX, TY, SOLID>(P, GlobalSrc<T>{G}, S, blockIdx.x * TX, blockIdx.y * TY,
+                                      threadIdx.y * TX + threadIdx.x, xf, yf);
+}
+
+// ---------------------------------------------------------------- TMA-staged update (FP32 form)
+// An interior tile loads its own point values (a 32 x 4 x 64-plane box from
+// cell (i0, j0), 32 KB) with one cp.async.bulk.tensor into shared memory,
+// completing on an mbarrier; the halo points and the stage states come from
+// global memory, and tiles at the grid's edges take the global-memory path
+// (boundary images).  An option (hweno_set_tma): with 52 KB of shared memory a
+// block, 4 blocks fit an SM against the global kernel's 8, and the global
+// kernel measured faster (1.07 against 1.46 ms per 2048^2 launch; a 40 x 6 box
+// with the halo and both stage states in shared memory, 2 blocks per SM: 1.63).
+constexpr unsigned GBOX_BYTES = GBX * GBY * 64 * 4;
+constexpr unsigned TMA_SMEM = GBOX_BYTES + 128;
+constexpr unsigned long long MBAR_POLL_LIMIT = 1ull << 22;
+static_assert(GBX == TX && GBY == TY, "the box covers one update tile");
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tma_load3d(void* dst, const CUtensorMap* map, int x, int y, int z, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      :: "r"(smem_u32(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(bar) : "memory");
+}
+
+// Phase `parity` of the mbarrier at `bar` completed; at most `limit` polls, false if the wait gave up.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity, unsigned long long limit) {
+  for (unsigned long long k = 0; k < limit; ++k) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__global__ void __launch_bounds__(TX * TY, 4) update2d_tma_kernel(Prob P, const float* __restrict__ G, Rk S,
+                                                                  const __grid_constant__ CUtensorMap tmG) {
+  __shared__ float xf[TY][TX + 1][4][4];
+  __shared__ float yf[TY + 1][TX][4][4];
+  extern __shared__ __align__(128) unsigned char dsm[];
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  if (S.dtp) {
+    S.dt = *S.dtp;
+    if (S.dt < 0.0) {   // a skipped step (block-uniform): the state passes through unchanged
+      const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+      if (i < P.nx && j < P.ny)
+        for (int q = 0; q < 12; ++q) {
+          const long long si = (long long)q * P.plane + (long long)j * P.pitch + i;
+          S.Uout[si] = S.Uin[si];
+          if (S.U32out) S.U32out[si] = f32_rn(S.Uin[si]);
+        }
+      return;
+    }
+  }
+  if (!(i0 >= 1 && i0 + TX < P.nx && j0 >= 1 && j0 + TY < P.ny)) {
+    update2d_tile<float, 4, TX, TY>(P, GlobalSrc<float>{G}, S, i0, j0, tid, xf, yf);
+    return;
+  }
+  float* gs = reinterpret_cast<float*>(dsm);
+  const unsigned bar = smem_u32(dsm + GBOX_BYTES);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(GBOX_BYTES) : "memory");
+    tma_load3d(gs, &tmG, i0, j0, 0, bar);   // i0 is a multiple of 32 floats (16-byte aligned)
+  }
+  if (!mbar_wait(bar, 0, MBAR_POLL_LIMIT)) {
+    // gave up: report, wait (bounded) for the copies still in flight, skip the tile
+    if (tid == 0) atomicOr(S.status, ST_TIMEOUT);
+    mbar_wait(bar, 0, MBAR_POLL_LIMIT);
+    return;
+  }
+  update2d_tile<float, 4, TX, TY, false, StagedSrc>(P, StagedSrc{gs, G, i0, j0}, S, i0, j0, tid, xf, yf);
+}
+
+// The TMA update kernel needs more than 48 KB of dynamic shared memory.
+[[maybe_unused]] bool set_update_tma_attribute() {
+  return cudaFuncSetAttribute(update2d_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TMA_SMEM) ==
+         cudaSuccess;
 }
 
 }  // namespace
@@ -695,6 +822,11 @@ void stage_t(const Prob& P, const HostTabs& HT, const Weights<T>& W, const Beta2
   if constexpr (NV == 4 && std::is_same<T, double>::value) {
     if (P.sol_j > 0) update2d_kernel<T, NV, true><<<grd, blk, 0, st>>>(P, (const T*)B.G, r);
     else update2d_kernel<T, NV><<<grd, blk, 0, st>>>(P, (const T*)B.G, r);
+  } else if constexpr (NV == 4 && std::is_same<T, float>::value) {
+    if (B.tmG && !S.Lout)
+      update2d_tma_kernel<<<grd, blk, TMA_SMEM, st>>>(P, (const float*)B.G, r, *B.tmG);
+    else
+      update2d_kernel<T, NV><<<grd, blk, 0, st>>>(P, (const T*)B.G, r);
   } else {
     update2d_kernel<T, NV><<<grd, blk, 0, st>>>(P, (const T*)B.G, r);
   }
@@ -843,7 +975,8 @@ __global__ void __launch_bounds__(TXV * TYV) batch_stage_kernel(BatchStage A, We
     Rk S{A.Uin + Q.uoff, A.Un + Q.uoff, A.Uout + Q.uoff, A.mask + Q.coff, A.Mod + Q.moff,
          A.maskN ? A.maskN + Q.coff : nullptr, A.ModN ? A.ModN + Q.moff : nullptr, dt, A.cA, A.cB,
          nullptr, nullptr, A.pstatus + p};
-    update2d_tile<T, 4, TXV, TYV>(Q.P, G + Q.goff, S, (t % Q.tiles_x) * TXV, (t / Q.tiles_x) * TYV, tid, xf, yf);
+    update2d_tile<T, 4, TXV, TYV>(Q.P, GlobalSrc<T>{G + Q.goff}, S, (t % Q.tiles_x) * TXV, (t / Q.tiles_x) * TYV, tid,
+                                  xf, yf);
   }
 }
 

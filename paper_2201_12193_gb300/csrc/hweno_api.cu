@@ -24,6 +24,9 @@ struct hweno_s {
   int fp32 = 0;                  // compute precision (hw::PREC_*)
   double* U[3] = {nullptr, nullptr, nullptr};
   float* U32[3] = {nullptr, nullptr, nullptr};   // FP32 form (single 2D handles): float copies of U[k]
+  CUtensorMap tmG{};             // FP32 2D Euler: tensor map of the point values (TMA-staged update)
+  bool tma_ok = false;           // the map is encoded
+  bool tma_on = false;           // the update kernel uses it (hweno_set_tma; off by default)
   int cur = 0, prev = 0;
   bool have_state = false, stepped = false;
   hw::Bufs B{};
@@ -295,6 +298,10 @@ int hweno_version(void) { return VERSION; }
 
 const char* hweno_last_error(hweno_t h) { return h ? h->err.c_str() : "null handle"; }
 
+namespace {
+bool encode_maps(hweno_t h);
+}  // namespace
+
 hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gamma, hweno_t* out) {
   if (!out) return HWENO_EINVAL;
   *out = nullptr;
@@ -388,6 +395,8 @@ hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gam
   for (int k = 0; k < 3; ++k) cudaMemset(h->U[k], 0, sbytes);
   for (int k = 0; k < 3 && shadow; ++k) cudaMemset(h->U32[k], 0, sbytes / 2);
   if (cudaDeviceSynchronize() != cudaSuccess) { free_all(h); delete h; return HWENO_ECUDA; }
+  // FP32 2D Euler: the update can stage interior tiles through TMA (hweno_set_tma; off by default)
+  if (shadow && P.nvar == 4) h->tma_ok = encode_maps(h);
   *out = h;
   return HWENO_OK;
 }
@@ -439,6 +448,37 @@ hweno_status hweno_get_moments(hweno_t h, double* m, size_t count, int on_device
 }
 
 namespace {
+
+// Tensor map of the FP32 update's TMA loads: the point values as a 3D tensor
+// (columns up to the padded pitch, rows, 64 planes), box 32 x 4 x 64 floats (one
+// update tile).  Strides and box rows are multiples of 16 bytes (rows padded to
+// 32 elements).
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool encode_maps(hweno_t h) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    return false;
+  }
+  const EncodeTiled enc = reinterpret_cast<EncodeTiled>(fn);
+  const Prob& P = h->P;
+  const cuuint32_t one[3] = {1, 1, 1};
+  {
+    const cuuint64_t dim[3] = {(cuuint64_t)P.gpitch, (cuuint64_t)P.ny, 64};
+    const cuuint64_t stride[2] = {(cuuint64_t)P.gpitch * 4, (cuuint64_t)P.gplane * 4};
+    const cuuint32_t box[3] = {32, 4, 64};
+    if (enc(&h->tmG, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, h->B.G, dim, stride, box, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+        CUDA_SUCCESS)
+      return false;
+  }
+  return hw::prepare_update_tma();
+}
 
 // Stage k (0, 1, 2) of the SSP-RK3 step from rotation a (eq. (Runge-Kutta)):
 //   U^(1) = U^n' + dt L(U^n');  U^(2) = 3/4 U^n' + 1/4 (U^(1)' + dt L(U^(1)'));
@@ -849,6 +889,17 @@ hweno_status hweno_set_positivity_check(hweno_t h, int on) {
                           h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
   }
+  return HWENO_OK;
+}
+
+hweno_status hweno_set_tma(hweno_t h, int on) {
+  if (!h) return HWENO_EINVAL;
+  if (on != 0 && on != 1) return fail(h, HWENO_EINVAL, "set_tma: on must be 0 or 1");
+  if (on && !h->tma_ok)
+    return fail(h, HWENO_ESTATE, "set_tma: TMA staging is for single 2D Euler FP32-bulk handles");
+  h->tma_on = on != 0;
+  h->B.tmG = h->tma_on ? &h->tmG : nullptr;
+  drop_graphs(h);
   return HWENO_OK;
 }
 

@@ -1,6 +1,7 @@
 // Internal interface between the C ABI (hweno_api.cu) and the kernel files.
 #pragma once
 
+#include <cuda.h>           // CUtensorMap (the type only; maps are encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -77,6 +78,7 @@ struct Bufs {
   int* und;           // cells the learned indicator left to KXRCF (current stage)
   int* und_count;     // [3] their counts per stage
   unsigned long long* rerec;   // [1] cells reconstructed a second time (accumulates), or null
+  const CUtensorMap* tmG = nullptr;   // FP32 2D Euler: tensor map of G for the TMA update kernel, or null
 };
 
 // One evaluation of the spatial operator with the troubled-cell steps and,
@@ -101,6 +103,10 @@ struct StageCall {
   const float* U32in = nullptr;   // FP32 form: float copy of Uin (its reconstruction input), or null
   float* U32out = nullptr;        // FP32 form: float copy of Uout, written by the update
 };
+
+// FP32 form: the TMA update kernel's shared-memory attribute (once per process);
+// false if it cannot be set (the caller then keeps the global-memory kernel).
+bool prepare_update_tma();
 
 void run_stage_1d(const Prob& P, const HostTabs& T, int prec, const Bufs& B, const StageCall& S, cudaStream_t st);
 

@@ -99,6 +99,7 @@ def lib():
         L.hweno_set_positivity_check.argtypes = [H, ctypes.c_int]
         L.hweno_set_persistence.argtypes = [H, ctypes.c_int]
         L.hweno_set_fused.argtypes = [H, ctypes.c_int]
+        L.hweno_set_tma.argtypes = [H, ctypes.c_int]
         L.hweno_set_solid.argtypes = [H, ctypes.c_int, ctypes.c_int]
         L.hweno_set_owned_rows.argtypes = [H, ctypes.c_int, ctypes.c_int]
         L.hweno_stage.argtypes = [H, ctypes.c_int, ctypes.c_double]
@@ -322,6 +323,11 @@ class Solver:
         out = (ctypes.c_double * 2)()
         self._check(lib().hweno_wave_speeds(self._h, out))
         return out[0], out[1]
+
+    def set_tma(self, on=True):
+        """TMA staging of the FP32-bulk update's interior tiles (off by
+        default; bitwise the same results either way)."""
+        self._check(lib().hweno_set_tma(self._h, int(bool(on))))
 
     def set_fused(self, on=True):
         """One fused kernel per Runge-Kutta stage (2D Euler; KXRCF, none or all
