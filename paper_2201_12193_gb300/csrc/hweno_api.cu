@@ -104,6 +104,8 @@ hw::PConst pconst(double v) {
 // The per-precision constants of a problem (after dx, dy and gamma are set).
 void fill_consts(Prob& P) {
   P.cgamma = pconst(P.gamma);
+  P.cgm1 = pconst(P.gamma - 1.0);
+  P.chk = pconst((P.gamma + 1.0) / (2.0 * P.gamma));
   P.cdx = pconst(P.dx);
   P.cdy = pconst(P.dy);
   P.crdx = pconst(1.0 / P.dx);

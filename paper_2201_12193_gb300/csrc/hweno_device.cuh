@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "hweno_parity.h"
 #include "df64.cuh"
 
@@ -66,6 +68,7 @@ struct Prob {
                           //    L only and the combination takes the stage states as they entered
   int fused;              // 2D Euler: one fused kernel per stage where it applies (else the pipeline)
   PConst cgamma, cdx, cdy, crdx, crdy, cdx2;   // gamma, dx, dy, 1/dx, 1/dy, dx^2
+  PConst cgm1, chk;   // gamma - 1 and (gamma + 1) / (2 gamma) of eq. (COEF)
   int sol_i, sol_j;       // solid block (2D Euler, the forward step): cells i >= sol_i, j < sol_j;
                           //    sol_j = 0: none
   int jlo, jhi;           // owned rows [jlo, jhi): the rows a row-slab of a decomposed grid owns (the
@@ -334,17 +337,34 @@ __device__ __forceinline__ void hllc(const Prob& P, const T* uL, const T* uR, in
   const T mL = uL[in] * iL, mR = uR[in] * iR;
   const T tL = two ? uL[it] * iL : T(0), tR = two ? uR[it] * iR : T(0);
   const T EL = uL[iE], ER = uR[iE];
-  const T pL = (g - T(1)) * (EL - T(0.5) * rL * (mL * mL + tL * tL));
-  const T pR = (g - T(1)) * (ER - T(0.5) * rR * (mR * mR + tR * tR));
-  const T cL = sqrt(g * pL * iL), cR = sqrt(g * pR * iR);
+  const T gm1 = pc<T>(P.cgm1);
+  const T pL = gm1 * (EL - T(0.5) * rL * (mL * mL + tL * tL));
+  const T pR = gm1 * (ER - T(0.5) * rR * (mR * mR + tR * tR));
+  const T gL = g * iL, gR = g * iR;
+  const T cL = sqrt(gL * pL), cR = sqrt(gR * pR);
   const T rs = T(0.5) * (rL + rR), cs = T(0.5) * (cL + cR);
   const T crs = cs * rs;
   const T ps = T(0.5) * (pL + pR + (mL - mR) * crs);
   const T ss = T(0.5) * (mL + mR + (pL - pR) / crs);
-  const T k = (g + T(1)) / (T(2) * g);
-  const T coefL = ps <= pL ? T(1) : sqrt(T(1) + k * (ps / pL - T(1)));
-  const T coefR = ps <= pR ? T(1) : sqrt(T(1) + k * (ps / pR - T(1)));
-  const T sL = mL - cL * coefL, sR = mR + cR * coefR;
+  // eq. (COEF): c_K coef_K = sqrt(gamma p_K / rho_K) sqrt(1 + k (p* / p_K - 1)) with
+  // k = (gamma + 1) / (2 gamma) when p* > p_K, else c_K.  FP64 keeps the two roots
+  // (the second only where p* > p_K); FP32 and double-float take one root,
+  // sqrt(gamma / rho_K (p_K + k max(p* - p_K, 0))), without the divisions by p_K
+  // (measured 5 % faster in the double-float update, 1 % slower in FP64).  A
+  // non-finite p* stays non-finite either way (the comparison is written so), and
+  // the branches below then fall through to f_R.
+  const T k = pc<T>(P.chk);
+  T sL, sR;
+  if constexpr (std::is_same<T, double>::value) {
+    const T coefL = ps <= pL ? T(1) : sqrt(T(1) + k * (ps / pL - T(1)));
+    const T coefR = ps <= pR ? T(1) : sqrt(T(1) + k * (ps / pR - T(1)));
+    sL = mL - cL * coefL;
+    sR = mR + cR * coefR;
+  } else {
+    const T dL = ps - pL, dR = ps - pR;
+    sL = mL - sqrt(gL * (pL + k * (dL <= T(0) ? T(0) : dL)));
+    sR = mR + sqrt(gR * (pR + k * (dR <= T(0) ? T(0) : dR)));
+  }
   const bool useL = (!wall && T(0) <= sL) || T(0) <= ss;     // left physical or left star flux
   const T rK = useL ? rL : rR, mK = useL ? mL : mR, tK = useL ? tL : tR;
   const T EK = useL ? EL : ER, pK = useL ? pL : pR, sK = useL ? sL : sR;
