@@ -356,27 +356,35 @@ KERNEL_SOURCES = ("hweno_2d_kernels.cuh", "hweno_device.cuh", "hweno_parity.h", 
 UPD32_BYTES_PER_CELL = 256 + 96 + 64 + 96 + 48
 
 
-def source_hash():
-    """SHA-256 of the 2D kernel sources (a committed ncu figure holds only for them)."""
+# the fused 1D stage kernel's sources (its ncu figures: profiles/dram_traffic_1d.json)
+KERNEL_SOURCES_1D = ("hweno_fused1d.cuh", "hweno_1d.cu", "hweno_device.cuh", "hweno_parity.h", "df64.cuh")
+# fused 1D stage, bytes per cell and launch: U^(k) 48 B, U^n 48 B in two stages
+# of three (32 B on average), U^(k+1) 48 B, the troubled mask 1 B and the
+# previous stage's mask 1 B in two of three
+FUSED1D_BYTES_PER_CELL = 48 + 32 + 48 + 1 + 2.0 / 3.0
+
+
+def source_hash(sources=KERNEL_SOURCES):
+    """SHA-256 of kernel sources (a committed ncu figure holds only for them)."""
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, "paper_2201_12193_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
 
 
-def traffic_per_cell(kernel):
+def traffic_per_cell(kernel, table="dram_traffic.json", sources=KERNEL_SOURCES):
     """DRAM bytes per cell of one launch of `kernel` from the committed ncu
-    figures (profiles/dram_traffic.json), or None when the kernel sources
-    changed since that capture."""
+    figures (profiles/<table>), or None when the kernel sources changed since
+    that capture."""
     try:
-        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", table)) as f:
             d = json.load(f)
     except (OSError, ValueError):
         return None
     k = d.get("kernels", {}).get(kernel)
-    if not k or d.get("source_sha256") != source_hash():
+    if not k or d.get("source_sha256") != source_hash(sources):
         return None
     return float(k["bytes_per_cell"])
 
@@ -413,9 +421,11 @@ def alu_peaks(hweno):
 
 def run_shu_osher(torch, hweno, world):
     """The 1D Shu-Osher problem (N = 4000, transmissive, to t = 1.8, CFL 0.6): a
-    latency-bound run of ~5,800 small steps (192 KB of state).  FP64 timed whole,
+    latency-bound run of ~5,800 small steps (192 KB of state) on the fused 1D
+    stage (the 1D default: one launch per Runge-Kutta stage).  FP64 timed whole,
     device-driven (hweno_advance: dt formed on the device, graph replays of 12
-    steps) against the host-driven loop (hweno_max_dt + hweno_step); the FP32-bulk
+    steps) against the host-driven loop (hweno_max_dt + hweno_step) and against
+    the four-launch pipeline (the same states bit for bit); the FP32-bulk
     and double-float forms run device-driven to the same time, each with the
     relative L1 difference of its final state to the FP64 run's (all moments, and
     cell averages alone) and the troubled cells per stage.  For scale, the same
@@ -425,10 +435,13 @@ def run_shu_osher(torch, hweno, world):
     p = W.shu_osher_1d(4000)
     out = {}
     finals = {}
-    for mode, prec, nx in (("advance", "fp64", 4000), ("host_loop", "fp64", 4000), ("advance_fp32", "fp32", 4000),
-                           ("advance_df64", "df64", 4000), ("advance_n8000", "fp64", 8000)):
+    for mode, prec, nx in (("advance", "fp64", 4000), ("host_loop", "fp64", 4000), ("advance_pipeline", "fp64", 4000),
+                           ("advance_fp32", "fp32", 4000), ("advance_df64", "df64", 4000),
+                           ("advance_n8000", "fp64", 8000)):
         q = p if nx == 4000 else W.shu_osher_1d(nx)
         s = hweno.Solver.from_problem(q, precision=prec)
+        if mode == "advance_pipeline":
+            s.set_fused(False)     # the four-launch stage (the fused stage is the 1D default)
         s.set_stream(torch.cuda.current_stream())
         s.set_moments(torch.from_numpy(q.m).cuda())
         s.run(0.01) if mode == "host_loop" else s.advance(0.01)      # warm-up (graph capture)
@@ -456,12 +469,63 @@ def run_shu_osher(torch, hweno, world):
     fine = finals["advance_n8000"][:, 0, 0]
     coarse = 0.5 * (fine[:, 0::2] + fine[:, 1::2])
     same = bool(np.array_equal(finals["advance"], finals["host_loop"]))
+    same_pipe = bool(np.array_equal(finals["advance"], finals["advance_pipeline"]))
     return {"shu_osher_1d_full_run": {"workload": "1d_euler_shu_osher_4000_to_t1.8", "dtype": "f64",
                                       "value": out["advance"]["value"], "unit": UNIT, "device_driven": out["advance"],
                                       "host_driven": out["host_loop"], "identical_states": same,
+                                      "stage": "fused (one launch per Runge-Kutta stage)",
+                                      "pipeline": out["advance_pipeline"],
+                                      "identical_states_fused_vs_pipeline": same_pipe,
                                       "fp32bulk": out["advance_fp32"], "df64": out["advance_df64"],
                                       "resolution_gap_averages_n4000_vs_n8000": rel(ref[:, 0, 0], coarse),
                                       "n8000_troubled_per_stage": out["advance_n8000"]["troubled_per_stage"]}}
+
+
+def run_shu_osher_long(torch, hweno, world, hbm_gbps, hbm_src, nx=1 << 24):
+    """Shu-Osher data on 2^24 cells (transmissive, CFL 0.6, 805 MB of state per
+    copy, far above L2) in the FP32-bulk form: the fused 1D stage kernel (one
+    launch per Runge-Kutta stage) against HBM.  Its algorithmic bytes per cell
+    and launch are the stage's inputs and outputs (FUSED1D_BYTES_PER_CELL); the
+    duration is the CUDA-event time of its launches on the solver's stream."""
+    from paper_2201_12193_gb300 import workloads as W
+    p = W.shu_osher_1d(nx)
+    s = hweno.Solver.from_problem(p, precision="fp32")
+    s.set_stream(torch.cuda.current_stream())
+    s.set_moments(torch.from_numpy(p.m).cuda())
+    del p
+    dt = s.max_dt(CFL)
+    for _ in range(3):
+        s.step(dt)
+    s.sync()
+    s.profile(True)
+    s.profile_read()
+    steps = 5
+    barrier(world)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        s.step(dt)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    prof = s.profile_read()
+    s.close()
+    f_ms, f_n = prof["fused_stage"]
+    out = {"workload": f"1d_euler_shu_osher_{nx}", "dtype": "f32 (state and RK accumulation f64)",
+           "value": aggregate(nx, 3, steps, world, ms), "unit": UNIT, "ms_per_step": ms / steps,
+           "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}}
+    if f_n:
+        gbs = FUSED1D_BYTES_PER_CELL * nx * f_n / (f_ms * 1e-3) / 1e9
+        t = traffic_per_cell("fused1d_fp32", "dram_traffic_1d.json", KERNEL_SOURCES_1D)
+        out["roofline_fused_stage"] = {
+            "bound": "hbm", "achieved": gbs, "peak": hbm_gbps, "unit": "GB/s", "frac": gbs / hbm_gbps,
+            "peak_source": hbm_src, "bytes_per_cell": FUSED1D_BYTES_PER_CELL, "avg_ms": f_ms / f_n,
+            "traffic": t * nx if t else None,
+            "note": "the FP64 pipe, not HBM, binds: ncu shows it 72 % busy (the Runge-Kutta combination and "
+                    "the flux differences of the average equation stay in FP64)"}
+    return {"shu_osher_1d_long_fp32": out}
 
 
 def run_four_quadrant_full(torch, hweno, world, rank):
@@ -909,6 +973,7 @@ def run_ours(args, world, rank, local):
 
     if not args.no_forms and not args.no_1d:
         forms.update(run_shu_osher(torch, hweno, world))
+        forms.update(run_shu_osher_long(torch, hweno, world, hbm_gbps, hbm_src))
     if args.full_run:
         forms.update(run_four_quadrant_full(torch, hweno, world, rank))
     if args.dmr:

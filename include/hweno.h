@@ -315,15 +315,21 @@ hweno_status hweno_set_positivity_check(hweno_t h, int on);
 hweno_status hweno_set_solid(hweno_t h, int i0, int j1);
 
 /* One fused kernel per Runge-Kutta stage (on = 1) instead of the pipeline of
- * four launches (on = 0, default): Steps 1-3 of Sec. 2.2 (reconstruction,
- * eq. (KXRCF_), eq. (vi), the troubled re-reconstruction, HLLC fluxes,
- * eqs. (integral1)-(integral3), L and eq. (Runge-Kutta)) for a strip of cells
- * in one block, the point values kept in shared memory.  Single 2D Euler
- * handles with the KXRCF, none or all indicator (else ESTATE); sides with
- * fixed states (hweno_set_fixed_state) keep the pipeline.  Boundary images
- * enter as ordinary cells, so cells next to a non-periodic side may differ from
- * the pipeline by rounding; elsewhere the two agree to rounding of the
- * quadrature sums.  Applies to hweno_step, hweno_advance and hweno_rhs. */
+ * four launches (on = 0).  2D (Sec. 2.2; off by default): Steps 1-3
+ * (reconstruction, eq. (KXRCF_), eq. (vi), the troubled re-reconstruction,
+ * HLLC fluxes, eqs. (integral1)-(integral3), L and eq. (Runge-Kutta)) for a
+ * strip of cells in one block, the point values kept in shared memory; single
+ * 2D Euler handles without a solid block; sides with fixed states
+ * (hweno_set_fixed_state) keep the pipeline; boundary images enter as
+ * ordinary cells, so cells next to a non-periodic side may differ from the
+ * pipeline by rounding, elsewhere the two agree to rounding of the quadrature
+ * sums.  1D (Sec. 2.1; ON by default): the same steps for a segment of cells
+ * and a 4-cell halo in shared memory, bitwise the pipeline's states, masks,
+ * KXRCF values and counts (scalar laws and Euler, every side kind and
+ * precision); component-wise reconstruction only (charwise handles keep the
+ * pipeline).  Both: the KXRCF, none or all indicator (else ESTATE; TVB and the
+ * learned indicator keep the pipeline).  Applies to hweno_step, hweno_stage,
+ * hweno_advance and hweno_rhs. */
 hweno_status hweno_set_fused(hweno_t h, int on);
 
 /* TMA staging of the FP32-bulk update (off by default): each interior 32 x 4

@@ -121,6 +121,23 @@ __global__ void __launch_bounds__(RB) rec1d_char_kernel(Prob P, Weights<T> W, Be
 
 // KXRCF face velocity of a cell at its left (side 0) or right (side 1) face,
 // from its own point values: u at the face (scalars, f'(u)) or (rho u)/rho (Euler).
+// KXRCF value of a cell (eq. (KXRCF) with the line integral of
+// eq. (line-integral-average) reduced to the two end points in 1D): the jumps
+// jl, jr of the density at the inflow faces (face velocities vl, vr), over
+// h^{(l+1)/3} (l = 5) times the cell's largest density point value nrm.  The
+// pipeline and the fused stage both call this, so their flags agree bit for bit.
+template <typename T>
+__device__ __forceinline__ T kxrcf1(const Prob& P, T jl, T jr, T vl, T vr, T nrm) {
+  const T s = jl * (vl > T(KX_VDEAD) ? T(1) : T(0)) + jr * (-vr > T(KX_VDEAD) ? T(1) : T(0));
+  return nrm == T(0) ? T(0) : tabs(s) / (T(P.dx * P.dx) * nrm);
+}
+
+// Modified first moment of a troubled cell, eq. (vi): from the neighbours'
+// averages uL, uR and first moments vL, vR (image signs applied).
+__device__ __forceinline__ double mod1(double uL, double uR, double vL, double vR) {
+  return MOD_WU * (uR - uL) + MOD_WV * (vL + vR);
+}
+
 template <typename T, int NV>
 __device__ __forceinline__ T face_vel1(const Prob& P, const T* __restrict__ G, int c, int side) {
   const int p = side ? 3 : 0;
@@ -152,11 +169,10 @@ __global__ void __launch_bounds__(RB) flag1d_kernel(Prob P, Weights<T> W, const 
       const T vr = T(0.5) * (face_vel1<T, NV>(P, G, i, 1) + (R.neg & 2 ? -ar : ar));
       const T jl = G[0 * P.gplane + i] - G[(long long)mpt1(L, 3) * P.gplane + L.i];
       const T jr = G[3 * P.gplane + i] - G[(long long)mpt1(R, 0) * P.gplane + R.i];
-      const T s = jl * (vl > T(KX_VDEAD) ? T(1) : T(0)) + jr * (-vr > T(KX_VDEAD) ? T(1) : T(0));
       T nrm = T(0);
 #pragma unroll
       for (int p = 0; p < 4; ++p) nrm = tmax(nrm, tabs(G[(long long)p * P.gplane + i]));
-      const T a = nrm == T(0) ? T(0) : tabs(s) / (T(P.dx * P.dx) * nrm);   // h^{(l+1)/3}, l = 5
+      const T a = kxrcf1<T>(P, jl, jr, vl, vr, nrm);
       if (aleph) aleph[i] = double(a);
       flag = a > T(1);
     }
@@ -178,7 +194,7 @@ __global__ void __launch_bounds__(RB) flag1d_kernel(Prob P, Weights<T> W, const 
     const int gL = vsign(L, v), gR = vsign(R, v);
     const double uL = gL * U[sidx(P, v, 0, L.i, 0)], uR = gR * U[sidx(P, v, 0, R.i, 0)];
     const double vL = gL * L.sx * U[sidx(P, v, 1, L.i, 0)], vR = gR * R.sx * U[sidx(P, v, 1, R.i, 0)];
-    Mod[(long long)v * P.plane + i] = MOD_WU * (uR - uL) + MOD_WV * (vL + vR);
+    Mod[(long long)v * P.plane + i] = mod1(uL, uR, vL, vR);
   }
 }
 
@@ -198,6 +214,90 @@ __device__ __forceinline__ void gl1(const Prob& P, const T* __restrict__ G, cons
   for (int v = 0; v < NV; ++v) {
     const T x = G[(long long)(v * 4 + p) * P.gplane + m.i];
     u[v] = (m.neg >> v) & 1 ? -x : x;
+  }
+}
+
+// Quadrature of eq. (F): the weighted physical flux at the cell's 4
+// Gauss-Lobatto points u[k] (FP64 Euler: the four reciprocal densities with
+// one division).
+template <typename T, int NV>
+__device__ __forceinline__ void quad1(const Prob& P, const T (&u)[4][NV], T (&F)[NV]) {
+#pragma unroll
+  for (int v = 0; v < NV; ++v) F[v] = T(0);
+  if constexpr (NV == 3 && one_division<T>::value) {
+    T rho[4], inv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) rho[k] = u[k][0];
+    batch_inverse<4, T>(rho, inv);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      T f[NV];
+      euler_flux_inv<T, NV>(P, u[k], inv[k], 0, f);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) F[v] += gl_w<T>(k) * f[v];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      T f[NV];
+      phys_flux<T, NV>(P, u[k], 0, f);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) F[v] += gl_w<T>(k) * f[v];
+    }
+  }
+}
+
+// L(U) of eq. (1D-equ-int-approximation) of cell i from its face fluxes fp
+// (right), fm (left) and quadrature F, and the SSP-RK3 combination of
+// eq. (Runge-Kutta) (or L and the stage input into Lout / Umod).  The average
+// equation is formed in FP64 from the widened face fluxes so that the flux
+// differences telescope in every precision; FP32 values are widened by integer
+// work and the first stage (cA = 0, cB = 1: U^(1) = U + dt L) is one FMA
+// without U^n, so the FP64 pipe carries only the sums.  uin: the cell's stage
+// input, its first moments replaced by those of eq. (vi) when it is flagged
+// and they persist (or Lout asks for them).  Both 1D stage forms call this.
+template <typename T, int NV>
+__device__ __forceinline__ void rk1_cell(const Prob& P, const Rk1& S, int i, const T* fp, const T* fm,
+                                         const T (&F)[NV], const double (&uinc)[2 * NV]) {
+  const double idx = P.crdx.d;
+  const T tidx = pc<T>(P.crdx);
+  const bool fn = P.persist && S.maskN && S.maskN[i] != 0;
+  const bool first = S.cA == 0.0;
+  double newavg[NV];
+  bool finite = true;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double L[2];
+    L[0] = -(to_f64(fp[v]) - to_f64(fm[v])) * idx;
+    L[1] = to_f64(-(fp[v] + fm[v]) * T(0.5) * tidx + F[v] * tidx);
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const long long si = (long long)(v * 2 + m) * P.plane + i;
+      const double uin = uinc[v * 2 + m];
+      if (S.Lout) {
+        S.Lout[si] = L[m];
+        if (S.Umod) S.Umod[si] = uin;
+        continue;
+      }
+      double r;
+      if (first) {
+        r = fma(S.dt, L[m], uin);
+      } else {
+        const double un = (m == 1 && fn) ? S.ModN[(long long)v * P.plane + i] : S.Un[si];
+        r = S.cA * un + S.cB * (uin + S.dt * L[m]);
+      }
+      S.Uout[si] = r;
+      if (m == 0) newavg[v] = r;
+      // non-finite by the exponent field (integer work, no FP64 compare)
+      finite = finite && ((__double_as_longlong(r) >> 52) & 0x7FF) != 0x7FF;
+    }
+  }
+  if (S.Lout) return;
+  if (!finite) atomicOr(S.status, ST_NONFINITE);
+  if (NV == 3) {
+    // rho > 0 and p = (gamma - 1)(E - m^2 / (2 rho)) > 0, the latter as 2 E rho > m^2 (no division)
+    const double rho = newavg[0];
+    if (!(rho > 0.0) || !(2.0 * newavg[NV - 1] * rho > newavg[1] * newavg[1])) atomicOr(S.status, ST_NONPOSITIVE);
   }
 }
 
@@ -229,70 +329,51 @@ __global__ void __launch_bounds__(UB) update1d_kernel(Prob P, const T* __restric
   }
   __syncthreads();
   if (!live) return;
-  T F[NV];
+  T u[4][NV], F[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) F[v] = T(0);
-  if constexpr (NV == 3 && one_division<T>::value) {
-    // Euler, FP64: the four reciprocal densities with one division
-    T rho[4], inv[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) rho[k] = G[(long long)k * P.gplane + i];
-    batch_inverse<4, T>(rho, inv);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {     // eq. (F)
-      T u[NV], f[NV];
-      gl1<T, NV>(P, G, self, k, u);
-      euler_flux_inv<T, NV>(P, u, inv[k], 0, f);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) F[v] += gl_w<T>(k) * f[v];
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {     // eq. (F)
-      T u[NV], f[NV];
-      gl1<T, NV>(P, G, self, k, u);
-      phys_flux<T, NV>(P, u, 0, f);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) F[v] += gl_w<T>(k) * f[v];
-    }
-  }
-  const double idx = P.crdx.d;
-  const T tidx = pc<T>(P.crdx);
+  for (int k = 0; k < 4; ++k) gl1<T, NV>(P, G, self, k, u[k]);
+  quad1<T, NV>(P, u, F);
   // modified first moments in the combination (persist), and always in the Umod output of Lout
   const bool fk = S.mask[i] != 0 && (P.persist || S.Lout);
-  const bool fn = P.persist && S.maskN && S.maskN[i] != 0;
-  double newavg[NV];
+  double uin[2 * NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) {
-    const T fp = fx[t + 1][v], fm = fx[t][v];
-    double L[2];
-    L[0] = -((double)fp - (double)fm) * idx;
-    L[1] = (double)(-(fp + fm) * T(0.5) * tidx + F[v] * tidx);
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      const long long si = (long long)(v * 2 + m) * P.plane + i;
-      const double uin = (m == 1 && fk) ? S.Mod[(long long)v * P.plane + i] : S.Uin[si];
-      if (S.Lout) {
-        S.Lout[si] = L[m];
-        if (S.Umod) S.Umod[si] = uin;
-        continue;
-      }
-      const double un = (m == 1 && fn) ? S.ModN[(long long)v * P.plane + i] : S.Un[si];
-      const double r = S.cA * un + S.cB * (uin + S.dt * L[m]);
-      S.Uout[si] = r;
-      if (m == 0) newavg[v] = r;
-      if (!isfinite(r)) atomicOr(S.status, ST_NONFINITE);
-    }
+    uin[2 * v] = S.Uin[(long long)(2 * v) * P.plane + i];
+    uin[2 * v + 1] = fk ? S.Mod[(long long)v * P.plane + i] : S.Uin[(long long)(2 * v + 1) * P.plane + i];
   }
-  if (!S.Lout && NV == 3) {
-    const double rho = newavg[0];
-    const double p = (P.gamma - 1.0) * (newavg[2] - 0.5 * newavg[1] * newavg[1] / rho);
-    if (!(rho > 0.0) || !(p > 0.0)) atomicOr(S.status, ST_NONPOSITIVE);
-  }
+  rk1_cell<T, NV>(P, S, i, fx[t + 1], fx[t], F, uin);
+}
+
+}  // namespace
+}  // namespace hw
+
+#include "hweno_fused1d.cuh"
+
+namespace hw {
+namespace {
+
+template <typename T, int NV, int SEG, int NT>
+void fused1d_launch(const Prob& P, const Weights<T>& W, const Beta1<T>& Bt, const Rk1& r, const Bufs& B,
+                    const StageCall& S, cudaStream_t st) {
+  constexpr int smem = (int)sizeof(Fused1dSmem<T, NV, SEG>);
+  static const bool attr = smem <= 48 * 1024 ||
+      cudaFuncSetAttribute(fused1d_kernel<T, NV, SEG, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) ==
+          cudaSuccess;
+  (void)attr;
+  fused1d_kernel<T, NV, SEG, NT><<<(P.nx + SEG - 1) / SEG, NT, smem, st>>>(P, W, Bt, r, S.mask, S.Mod, S.aleph,
+                                                                             B.rerec);
 }
 
 template <typename T, int NV>
 void stage_t(const Prob& P, const Weights<T>& W, const Beta1<T>& Bt, const Bufs& B, const StageCall& S, cudaStream_t st) {
+  Rk1 r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status, S.dtp};
+  if (P.fused) {   // the whole stage in one launch (hweno_set_fused)
+    if (B.prof) B.prof->begin(5, st);
+    if (P.nx >= 2 * P.nsm * 250) fused1d_launch<T, NV, 250, 256>(P, W, Bt, r, B, S, st);
+    else fused1d_launch<T, NV, 32, 128>(P, W, Bt, r, B, S, st);
+    if (B.prof) B.prof->end(st);
+    return;
+  }
   int* cnt = B.count + S.stage;
   cudaMemsetAsync(cnt, 0, sizeof(int), st);
   const int blocks = (P.nx + RB - 1) / RB, rblocks = (P.nx * NV + RB - 1) / RB;
@@ -318,7 +399,6 @@ void stage_t(const Prob& P, const Weights<T>& W, const Beta1<T>& Bt, const Bufs&
       rec1d_kernel<T, NV, true><<<rblocks, RB, 0, st>>>(P, W, Bt, S.Uin, S.mask, S.Mod, B.list, cnt, (T*)B.G, B.rerec);
     if (B.prof) B.prof->end(st);
   }
-  Rk1 r{S.Uin, S.Un, S.Uout, S.mask, S.Mod, S.maskN, S.ModN, S.dt, S.cA, S.cB, S.Lout, S.Umod, B.status, S.dtp};
   if (B.prof) B.prof->begin(3, st);
   update1d_kernel<T, NV><<<blocks, UB, 0, st>>>(P, (const T*)B.G, r);
   if (B.prof) B.prof->end(st);

@@ -344,6 +344,9 @@ hweno_status hweno_create(const hweno_grid* grid, const hweno_bc* bc, double gam
   P.persist = 1;
   P.jlo = 0;
   P.jhi = P.ny;
+  // 1D: the fused stage by default where it applies (bitwise the pipeline's states in one launch per stage)
+  P.fused = h->g.dim == 1 && !P.charwise &&
+            (P.indicator == HWENO_IND_NONE || P.indicator == HWENO_IND_KXRCF || P.indicator == HWENO_IND_ALL);
   fill_consts(P);
   cudaDeviceGetAttribute(&P.nsm, cudaDevAttrMultiProcessorCount, h->dev);
   h->fp32 = h->g.precision;
@@ -908,11 +911,13 @@ hweno_status hweno_set_tma(hweno_t h, int on) {
 hweno_status hweno_set_fused(hweno_t h, int on) {
   if (!h) return HWENO_EINVAL;
   if (on != 0 && on != 1) return fail(h, HWENO_EINVAL, "set_fused: on must be 0 or 1");
-  if (on && (h->batch || h->g.dim != 2 || h->g.eq != HWENO_EULER || h->P.sol_j > 0 ||
-             (h->g.indicator != HWENO_IND_NONE && h->g.indicator != HWENO_IND_KXRCF &&
-              h->g.indicator != HWENO_IND_ALL)))
-    return fail(h, HWENO_ESTATE, "set_fused: the fused stage is for single 2D Euler handles with the KXRCF, "
-                                 "none or all indicator");
+  const bool ind_ok = h->g.indicator == HWENO_IND_NONE || h->g.indicator == HWENO_IND_KXRCF ||
+                      h->g.indicator == HWENO_IND_ALL;
+  const bool ok2 = h->g.dim == 2 && h->g.eq == HWENO_EULER && h->P.sol_j == 0;
+  const bool ok1 = h->g.dim == 1 && !h->P.charwise;
+  if (on && (h->batch || !ind_ok || !(ok1 || ok2)))
+    return fail(h, HWENO_ESTATE, "set_fused: the fused stage is for single 1D handles (component-wise) and 2D Euler "
+                                 "handles with the KXRCF, none or all indicator");
   // the fused stage keeps no float copy of the state: renew it when the pipeline takes over
   if (!on && h->P.fused && h->have_state && h->U32[h->cur])
     hw::run_shadow32(h->P, h->U[h->cur], h->U32[h->cur], 0, h->P.ny, h->stream);

@@ -330,8 +330,9 @@ class Solver:
         self._check(lib().hweno_set_tma(self._h, int(bool(on))))
 
     def set_fused(self, on=True):
-        """One fused kernel per Runge-Kutta stage (2D Euler; KXRCF, none or all
-        indicator) instead of the four-launch pipeline."""
+        """One fused kernel per Runge-Kutta stage instead of the four-launch
+        pipeline (KXRCF, none or all indicator): 2D Euler (off by default) and
+        component-wise 1D (on by default, bitwise the pipeline)."""
         self._check(lib().hweno_set_fused(self._h, int(bool(on))))
 
     def set_persistence(self, persist=True):

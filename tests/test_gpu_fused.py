@@ -191,7 +191,7 @@ def test_fused_rerecon_count_equals_the_pipeline():
 
 def test_fused_rejected_where_it_does_not_apply():
     for kw, p in (({"indicator": "tvb", "tvb_m": 1.0}, W.four_quadrant_2d(16, seed=1)),
-                  ({}, W.shu_osher_1d(100)), ({}, W.burgers_2d(16))):
+                  ({"charwise": True}, W.shu_osher_1d(100)), ({}, W.burgers_2d(16))):
         s = hweno.Solver.from_problem(p, **kw)
         with pytest.raises(hweno.HwenoError):
             s.set_fused(True)
