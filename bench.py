@@ -499,6 +499,7 @@ def run_shu_osher_long(torch, hweno, world, hbm_gbps, hbm_src, nx=1 << 24):
     s.sync()
     s.profile(True)
     s.profile_read()
+    s.rerecon_count()
     steps = 5
     barrier(world)
     torch.cuda.synchronize()
@@ -511,10 +512,12 @@ def run_shu_osher_long(torch, hweno, world, hbm_gbps, hbm_src, nx=1 << 24):
     torch.cuda.synchronize()
     ms = max_over_ranks(e0.elapsed_time(e1), world)
     prof = s.profile_read()
+    rer = s.rerecon_count()
     s.close()
     f_ms, f_n = prof["fused_stage"]
     out = {"workload": f"1d_euler_shu_osher_{nx}", "dtype": "f32 (state and RK accumulation f64)",
            "value": aggregate(nx, 3, steps, world, ms), "unit": UNIT, "ms_per_step": ms / steps,
+           "rerecon_cells_per_stage": rer / (3.0 * steps),
            "kernels": {k: {"ms": v[0], "launches": v[1]} for k, v in prof.items() if v[1]}}
     if f_n:
         gbs = FUSED1D_BYTES_PER_CELL * nx * f_n / (f_ms * 1e-3) / 1e9

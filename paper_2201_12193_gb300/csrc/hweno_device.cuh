@@ -66,7 +66,7 @@ struct Prob {
   int persist;            // 1: the first moments modified in troubled cells (eq. (vi)) replace the
                           //    stage input and enter the Runge-Kutta combination; 0: they serve
                           //    L only and the combination takes the stage states as they entered
-  int fused;              // 2D Euler: one fused kernel per stage where it applies (else the pipeline)
+  int fused;              // one fused kernel per stage (1D default; 2D Euler option) instead of the pipeline
   PConst cgamma, cdx, cdy, crdx, crdy, cdx2;   // gamma, dx, dy, 1/dx, 1/dy, dx^2
   PConst cgm1, chk;   // gamma - 1 and (gamma + 1) / (2 gamma) of eq. (COEF)
   int sol_i, sol_j;       // solid block (2D Euler, the forward step): cells i >= sol_i, j < sol_j;
