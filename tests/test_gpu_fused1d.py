@@ -121,6 +121,76 @@ def test_fused1d_large_grid_sampled():
     b.close()
 
 
+def _both(a, b, fn):
+    """fn on both handles: the same status (a rolled-back step included)."""
+    st = []
+    for s in (a, b):
+        try:
+            fn(s)
+            st.append(0)
+        except hweno.HwenoError as e:
+            st.append(e.status)
+    assert st[0] == st[1], st
+    return st[0]
+
+
+@pytest.mark.parametrize("nx", [4, 5, 7, 31, 32, 33, 65, 257])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fused1d_tiny_and_ragged_grids(nx, precision):
+    """The smallest grids (every ghost's image inside a 4-cell grid) and ragged
+    last segments, on every side kind: bitwise the pipeline, failures included."""
+    for make, nopos in ((W.sod_1d, False), (W.blast_wave_1d, True), (W.advection_sin_1d, False),
+                        (W.burgers_1d, False)):
+        p = make(nx)
+        a, b = _pair(p, nopos, precision=precision)
+        for _ in range(3):
+            dt = a.max_dt(0.6)
+            if _both(a, b, lambda s: s.step(dt)):
+                break
+        np.testing.assert_array_equal(a.get_moments(), b.get_moments())
+        np.testing.assert_array_equal(a.troubled_mask(), b.troubled_mask())
+        a.close()
+        b.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_fused1d_modification_in_L_only(precision):
+    """Reading B of the persistence of eq. (vi) (hweno_set_persistence 0): the
+    fused stage equals the pipeline bit for bit."""
+    for p, nopos in ((W.shu_osher_1d(600), False), (W.blast_wave_1d(300), True)):
+        a, b = _pair(p, nopos, precision=precision)
+        for s in (a, b):
+            s.set_persistence(False)
+        for _ in range(6):
+            dt = a.max_dt(0.6)
+            a.step(dt)
+            b.step(dt)
+        np.testing.assert_array_equal(a.get_moments(), b.get_moments())
+        a.close()
+        b.close()
+
+
+@pytest.mark.parametrize("indicator", ["kxrcf", "none", "all"])
+def test_fused1d_rhs_scalar_laws(indicator):
+    """L, the stage input with eq. (vi) applied, masks and KXRCF values of the
+    scalar laws (LLF fluxes, periodic sides) against the pipeline."""
+    for p in (W.advection_sin_1d(300), W.burgers_1d(260)):
+        res = []
+        for fused in (False, True):
+            s = hweno.Solver.from_problem(p, indicator=indicator)
+            s.set_fused(fused)
+            U = torch.from_numpy(p.m).cuda()
+            Um, L = torch.empty_like(U), torch.empty_like(U)
+            mask = torch.empty(p.nx, dtype=torch.uint8, device="cuda")
+            aleph = torch.zeros(p.nx, dtype=torch.float64, device="cuda")
+            s.rhs(U, Um, L, mask, aleph)
+            torch.cuda.synchronize()
+            res.append([x.cpu().numpy() for x in (Um, L, mask, aleph)])
+            s.close()
+        for x, y in zip(*res):
+            np.testing.assert_array_equal(x, y)
+
+
 def test_fused1d_is_the_default():
     """A 1D handle runs the fused stage unless asked otherwise: one launch per
     stage; the characteristic-wise and TVB forms keep the pipeline."""
