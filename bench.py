@@ -540,7 +540,7 @@ def run_four_quadrant_full(torch, hweno, world, rank):
     from paper_2201_12193_gb300 import workloads as W
     rejected = []
     seed = rank
-    out, finals = {}, {}
+    out, finals, reached = {}, {}, {}
 
     def run(p, prec):
         s = hweno.Solver.from_problem(p, precision=prec)
@@ -549,7 +549,14 @@ def run_four_quadrant_full(torch, hweno, world, rank):
             s.set_moments(torch.from_numpy(p.m).cuda())
             s.sync()
             t0 = time.perf_counter()
-            t, n = s.advance(0.25, CFL)
+            try:
+                t, n = s.advance(0.25, CFL)
+            except hweno.HwenoError:
+                try:
+                    reached[prec] = s.time()     # the start of the 12-step replay that failed
+                except hweno.HwenoError:
+                    pass
+                raise
             secs = time.perf_counter() - t0
             finals[prec] = s.get_moments()
             out[prec] = {"value": aggregate(p.nx * p.ny, 3, n, 1, secs * 1e3), "steps": n, "seconds": secs,
@@ -571,7 +578,7 @@ def run_four_quadrant_full(torch, hweno, world, rank):
         try:
             run(p, prec)
         except hweno.HwenoError as e:
-            out[prec] = {"failed": str(e)}
+            out[prec] = {"failed": str(e), "t_reached": reached.get(prec)}
             continue
         out[prec]["rel_l1_to_fp64"] = float(np.abs(finals[prec] - finals["fp64"]).sum()
                                             / np.abs(finals["fp64"]).sum())
