@@ -109,7 +109,7 @@ def test_fused1d_device_driven_run(precision):
 
 
 def test_fused1d_large_grid_sampled():
-    """2^20 cells (4096 blocks): two steps, bitwise the pipeline."""
+    """2^20 cells (4,195 segments of 250 cells): two steps, bitwise the pipeline."""
     p = W.shu_osher_1d(1 << 20)
     a, b = _pair(p, False, precision="fp32")
     for _ in range(2):
