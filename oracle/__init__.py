@@ -113,6 +113,8 @@ def lib():
             _lib.orc_level_matrix.argtypes = [ctypes.c_int, ctypes.c_int, I, I, I, I, I, I, I, D]
             _lib.orc_num_flux.argtypes = [C, D, D, ctypes.c_int, D]
             _lib.orc_phys_flux.argtypes = [C, D, ctypes.c_int, D]
+            _lib.orc_kxrcf_aleph.argtypes = [C, D, ctypes.c_int, ctypes.c_int]
+            _lib.orc_kxrcf_aleph.restype = ctypes.c_double
             _lib.orc_totals.argtypes = [C, D, D]
             _lib.orc_set_beta_source.argtypes = [ctypes.c_int]
             _lib.orc_euler1d_eig.argtypes = [ctypes.c_double, D, D, D]
@@ -253,6 +255,23 @@ def num_flux(cfg: Cfg, uL, uR, direction: int = 0) -> np.ndarray:
     F = np.zeros(nvars(cfg))
     lib().orc_num_flux(ctypes.byref(cfg), _dp(uL), _dp(uR), direction, _dp(F))
     return F
+
+
+def kxrcf_aleph(cfg: Cfg, G, i: int, j: int = 0) -> float:
+    """The KXRCF value of cell (i, j) from given point values G[j][i][var][k][l]
+    (2D; 1D: G[i][var][k], the 4 Gauss-Lobatto points of a cell)."""
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    if cfg.dim == 2:
+        want = (cfg.ny, cfg.nx, nvars(cfg), 4, 4)
+        flat = G.reshape(-1)
+    else:
+        want = (cfg.nx, nvars(cfg), 4)
+        flat = np.zeros((cfg.nx, nvars(cfg), 16))
+        flat[:, :, :4] = G
+        flat = flat.reshape(-1)
+    if G.shape != want:
+        raise ValueError(f"G must have shape {want}")
+    return float(lib().orc_kxrcf_aleph(ctypes.byref(cfg), _dp(flat), int(i), int(j)))
 
 
 def phys_flux(cfg: Cfg, u, direction: int = 0) -> np.ndarray:

@@ -1202,6 +1202,12 @@ void orc_num_flux(const orc_cfg *c, const double *uL, const double *uR, int dir,
 
 void orc_phys_flux(const orc_cfg *c, const double *u, int dir, double *f) { phys_flux(c, u, dir, f); }
 
+/* The KXRCF value of cell (i, j) from given pass-1 point values G, laid out as the
+ * oracle's own buffer: G[((j nx + i) nvars + var) 16 + k 4 + l] (1D: + k) -- a
+ * test entry, so that the indicator's definition can be pinned on point values
+ * chosen by hand rather than on those of the reconstruction. */
+double orc_kxrcf_aleph(const orc_cfg *c, const double *G, int i, int j) { return kxrcf_aleph(c, G, i, j); }
+
 /* 1D Euler eigenvectors used by the characteristic-wise option (R row-major,
  * columns = right eigenvectors; L row-major, rows = left eigenvectors). */
 void orc_euler1d_eig(double gam, const double *u, double *R, double *L) {

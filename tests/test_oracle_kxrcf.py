@@ -155,3 +155,45 @@ def test_2d_single_inflow_face(orc):
 def test_2d_at_rest(orc):
     aleph, mask = _aleph_2d(orc, _xstep(), np.zeros((N2, N2)), np.zeros((N2, N2)))
     assert np.all(aleph == 0.0) and mask.sum() == 0
+
+
+# ---------------------------------------------------------------- the norm over all the cell's points
+# ||rho|| in eq. (KXRCF) / (KXRCF_) is the largest |point value| over all the
+# cell's Gauss-Lobatto points, the interior ones included.  On point values
+# chosen by hand (the oracle's test entry takes them in place of the
+# reconstruction's), a cell whose density peaks at its interior points tells
+# that norm from one over the boundary points only.
+
+def test_norm_counts_the_interior_points_1d():
+    """1D, flow to the right (u = 1 everywhere): the left face is the inflow face,
+    the jump there is 1 - 1.5; the cell's points are (1, 3, 3, 1), so
+    aleph = 0.5 / (h^2 * 3), not 0.5 / (h^2 * 1)."""
+    from oracle import kxrcf_aleph, make_cfg
+    h = 0.1
+    cfg = make_cfg(1, 3, dx=h, eq="euler", bc=("periodic",) * 4)
+    G = np.zeros((3, 3, 4))
+    rho = np.ones((3, 4))
+    rho[1] = (1.0, 3.0, 3.0, 1.0)
+    rho[0, 3] = 1.5
+    G[:, 0, :] = rho
+    G[:, 1, :] = rho          # momentum = rho: velocity 1
+    G[:, 2, :] = 2.5 + 0.5 * rho
+    assert kxrcf_aleph(cfg, G, 1) == pytest.approx(0.5 / (h * h * 3.0), rel=1e-13)
+
+
+def test_norm_counts_the_interior_points_2d():
+    """2D, flow along +x (u = 1, v = 0): only the left face is inflow, with the
+    jump 1 - 1.5 at every point of it; the cell's density is 3 at its four
+    interior points and 1 at the twelve boundary points, so
+    aleph = |dy * (-0.5)| / dy / (h^2 * 3)."""
+    from oracle import kxrcf_aleph, make_cfg
+    h = 0.1
+    cfg = make_cfg(2, 3, 3, dx=h, dy=h, eq="euler", bc=("periodic",) * 4)
+    rho = np.ones((3, 3, 4, 4))               # [j][i][k][l]
+    rho[1, 1, 1:3, 1:3] = 3.0
+    rho[1, 0, 3, :] = 1.5                     # the left neighbour's trace on the shared face
+    G = np.zeros((3, 3, 4, 4, 4))
+    G[:, :, 0] = rho
+    G[:, :, 1] = rho                          # x momentum = rho: u = 1
+    G[:, :, 3] = 2.5 + 0.5 * rho
+    assert kxrcf_aleph(cfg, G, 1, 1) == pytest.approx(0.5 / (h * h * 3.0), rel=1e-13)
