@@ -143,7 +143,9 @@ class Solver:
     "none", "all", "tvb" (with tvb_m) or "mlp" (with set_mlp); bc per side:
     "periodic", "transmissive", "reflective" (Euler) or "inflow" (2D Euler FP64,
     states by set_fixed_state); charwise: characteristic-wise reconstruction
-    (1D Euler)."""
+    (1D Euler).  A 1D handle runs each Runge-Kutta stage as one fused launch
+    unless it is charwise or uses TVB (set_fused(False) selects the four-launch
+    pipeline; both give the same states bit for bit)."""
 
     def __init__(self, dim, nx, ny=1, x0=0.0, x1=1.0, y0=0.0, y1=1.0, eq="euler", adv=(1.0, 0.0),
                  precision="fp64", indicator="kxrcf", gamma_bar=(1.0, 10.0, 100.0, 1000.0), beta_of_q=False,
